@@ -1,0 +1,518 @@
+/*
+ * rlt2_oracle.c -- TEST INFRASTRUCTURE, not part of the product path.
+ *
+ * A plain, slow, single-threaded CPU restatement of the level-2 RLT (RLT2)
+ * dual ascent for the Koopmans-Beckmann QAP (Algorithm 1 of Goncalves,
+ * Pessoa, Drummond, Bentes, Farias, arXiv:1510.02065), in int64.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
+ * load this library.  It shares no code, header, table or helper with the
+ * CUDA library: it is the independent definition the CUDA path is checked
+ * against.
+ *
+ * Storage is the plainest possible: the reduced costs are dense arrays
+ * indexed by the paper's own subscripts,
+ *     b[i][j]               (matrix B, N x N)
+ *     c[i][j][k][n]         (matrix C; only i!=k, j!=n are meaningful)
+ *     d[i][j][k][n][p][q]   (matrix D; only distinct i,k,p and distinct j,n,q)
+ * with every meaningless entry held at 0.
+ *
+ * Readings of passages the paper leaves open (each one is also listed in the
+ * design notes of the repository):
+ *   R1  rows and columns of every submatrix are taken in ascending index order;
+ *   R2  one iteration runs the seven operations in the order of Algorithm 1;
+ *   R3  a cost spread over m rows (Sec. 4.2 divides by N-1 and N-2) is split
+ *       into integers: q = floor(x/m), r = x mod m, and the t-th row
+ *       (ascending, t = 0..m-1) receives q + [t < r].  Every row of the
+ *       submatrix gets the same increment on all its columns, so the cost of
+ *       every feasible solution is kept exactly;
+ *   R4  the transfer between complementary costs (Sec. 4.3) is the equal split
+ *       of the class sum T: the member of lexicographic rank t (t = 0..s-1,
+ *       s = 2 for C, 6 for D) receives floor(T/s) + [t < T mod s];
+ *   R5  the "residual coefficients" of a concentration (Sec. 4.1) are the
+ *       reduced costs M[r][s] - u[r] - v[s] under the duals of the Hungarian
+ *       method below;
+ *   R6  the Hungarian method is the shortest-augmenting-path form with row and
+ *       column potentials: u = v = 0 at the start, rows inserted in ascending
+ *       order, the next column is the unlabelled one of least reduced
+ *       distance with ties going to the smallest column index, a distance
+ *       label (and its predecessor) changes only on a strict improvement.
+ *
+ * Parity pins for every function live in tests/ (N!-enumeration and scipy for
+ * the LAP, brute-force QAP optima, the conservation identity
+ * Q(pi) = LB + sum of reduced costs along pi, non-negativity, monotone LB, and
+ * the Gilmore-Lawler bound in RLT1 mode).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_INF INT64_MAX
+
+typedef struct {
+    int N;
+    int rlt1_only;     /* strong-branching dual of Sec. 6: Algorithm 1 without D */
+    int64_t LB;
+    int64_t iters;
+    int64_t *b, *c, *d;
+    /* work counters of the Hungarian method, summed over all LAPs solved */
+    int64_t laps, steps, relaxations;
+    int64_t max_abs;   /* largest |value| seen in a potential, label or cost */
+} orc_state;
+
+/* ---------------------------------------------------------------- indexing */
+
+static inline size_t ix2(int N, int i, int j) { return (size_t)i * N + j; }
+static inline size_t ix4(int N, int i, int j, int k, int n)
+{
+    return (((size_t)i * N + j) * N + k) * N + n;
+}
+static inline size_t ix6(int N, int i, int j, int k, int n, int p, int q)
+{
+    return (((((size_t)i * N + j) * N + k) * N + n) * N + p) * N + q;
+}
+
+static inline void track(orc_state *st, int64_t x)
+{
+    int64_t a = x < 0 ? -x : x;
+    if (st && a > st->max_abs) st->max_abs = a;
+}
+
+/* ------------------------------------------------------- Hungarian method */
+
+/*
+ * Linear assignment by the Hungarian method (Sec. 4.1 names Munkres' method
+ * for each concentration; the variant is fixed by reading R6).
+ *
+ *   n            size of the square cost matrix M (row-major, n*n, entries >= 0)
+ *   u_out[n]     row potentials, v_out[n] column potentials (may be NULL)
+ *   col_of_row   assignment sigma: row r -> column col_of_row[r] (may be NULL)
+ *   work[3]      += {steps, relaxations, 1} (may be NULL)
+ * Returns S = sum_r M[r][sigma(r)], the optimal assignment cost.
+ *
+ * Column index n is a virtual column that holds the row being inserted.  A
+ * "step" labels one column; a "relaxation" is one evaluation of a reduced
+ * distance M[i0][j] - u[i0] - v[j] for an unlabelled column j.
+ */
+int64_t orc_lap(int n, const int64_t *M, int64_t *u_out, int64_t *v_out,
+                int32_t *col_of_row, int64_t *work, orc_state *st)
+{
+    int64_t *u = calloc((size_t)n + 1, sizeof(int64_t));   /* per row     */
+    int64_t *v = calloc((size_t)n + 1, sizeof(int64_t));   /* per column  */
+    int64_t *dist = malloc(((size_t)n + 1) * sizeof(int64_t));
+    int *row_at = malloc(((size_t)n + 1) * sizeof(int));    /* row matched to column */
+    int *pred = malloc(((size_t)n + 1) * sizeof(int));      /* previous column on path */
+    char *labelled = malloc((size_t)n + 1);
+    int64_t steps = 0, relax = 0;
+
+    for (int j = 0; j <= n; j++) row_at[j] = -1;
+
+    for (int r = 0; r < n; r++) {
+        const int root = n;               /* virtual column carrying row r */
+        row_at[root] = r;
+        for (int j = 0; j <= n; j++) { dist[j] = ORC_INF; labelled[j] = 0; }
+        int col = root;                   /* last labelled column */
+        for (;;) {
+            labelled[col] = 1;
+            const int i0 = row_at[col];   /* its row is scanned once */
+            int64_t delta = ORC_INF;
+            int next = -1;
+            steps++;
+            for (int j = 0; j < n; j++) {
+                if (labelled[j]) continue;
+                relax++;
+                int64_t red = M[(size_t)i0 * n + j] - u[i0] - v[j];
+                track(st, red);
+                if (red < dist[j]) { dist[j] = red; pred[j] = col; }
+                if (dist[j] < delta) { delta = dist[j]; next = j; }
+            }
+            /* move the potentials by delta: labelled columns and their rows
+             * (the tree) keep their reduced costs, the rest get closer */
+            for (int j = 0; j <= n; j++) {
+                if (labelled[j]) {
+                    u[row_at[j]] += delta;
+                    v[j] -= delta;
+                    track(st, u[row_at[j]]);
+                    track(st, v[j]);
+                } else {
+                    dist[j] -= delta;
+                }
+            }
+            col = next;
+            if (row_at[col] < 0) break;   /* free column: augmenting path found */
+        }
+        /* augment: every column on the path takes the row of its predecessor */
+        while (col != root) {
+            int p = pred[col];
+            row_at[col] = row_at[p];
+            col = p;
+        }
+    }
+
+    int64_t S = 0;
+    for (int j = 0; j < n; j++) {
+        int r = row_at[j];
+        S += M[(size_t)r * n + j];
+        if (col_of_row) col_of_row[r] = j;
+    }
+    if (u_out) for (int r = 0; r < n; r++) u_out[r] = u[r];
+    if (v_out) for (int j = 0; j < n; j++) v_out[j] = v[j];
+    if (work) { work[0] += steps; work[1] += relax; work[2] += 1; }
+    if (st) { st->steps += steps; st->relaxations += relax; st->laps += 1; }
+    free(u); free(v); free(dist); free(row_at); free(pred); free(labelled);
+    return S;
+}
+
+/* Batch form for tests: count matrices of n*n, outputs per matrix. */
+void orc_lap_batch(int n, int count, const int64_t *M, int64_t *S,
+                   int64_t *u, int64_t *v, int32_t *col_of_row, int64_t *work)
+{
+    for (int t = 0; t < count; t++)
+        S[t] = orc_lap(n, M + (size_t)t * n * n, u ? u + (size_t)t * n : NULL,
+                       v ? v + (size_t)t * n : NULL,
+                       col_of_row ? col_of_row + (size_t)t * n : NULL,
+                       work ? work + (size_t)t * 3 : NULL, NULL);
+}
+
+/* ------------------------------------------------------------ state setup */
+
+/*
+ * Initialisation of Algorithm 1: LB <- lb_const, b_ij <- linear cost (B_lin,
+ * or 0), c_ijkn <- f_ik * d_jn for i != k and j != n, d <- 0.
+ * F, D: N x N row-major flow and distance matrices (Eq. (1)).
+ */
+orc_state *orc_create(int N, const int32_t *F, const int32_t *Dist,
+                      const int64_t *B_lin, int64_t lb_const, int rlt1_only)
+{
+    if (N < 3) return NULL;
+    orc_state *st = calloc(1, sizeof(orc_state));
+    st->N = N;
+    st->rlt1_only = rlt1_only;
+    st->LB = lb_const;
+    size_t n2 = (size_t)N * N, n4 = n2 * n2;
+    st->b = calloc(n2, sizeof(int64_t));
+    st->c = calloc(n4, sizeof(int64_t));
+    if (!rlt1_only) st->d = calloc(n4 * n2, sizeof(int64_t));
+    if (!st->b || !st->c || (!rlt1_only && !st->d)) {
+        free(st->b); free(st->c); free(st->d); free(st);
+        return NULL;
+    }
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+            st->b[ix2(N, i, j)] = B_lin ? B_lin[ix2(N, i, j)] : 0;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+            for (int k = 0; k < N; k++)
+                for (int n = 0; n < N; n++)
+                    if (k != i && n != j)
+                        st->c[ix4(N, i, j, k, n)] =
+                            (int64_t)F[ix2(N, i, k)] * (int64_t)Dist[ix2(N, j, n)];
+    return st;
+}
+
+void orc_destroy(orc_state *st)
+{
+    if (!st) return;
+    free(st->b); free(st->c); free(st->d); free(st);
+}
+
+/* -------------------------------------------------------- cost spreading */
+
+/* The t-th of m rows receives floor(x/m) + [t < x mod m]  (reading R3). */
+static inline int64_t row_share(int64_t x, int m, int t)
+{
+    return x / m + (t < x % m ? 1 : 0);
+}
+
+/*
+ * Costs spreading from B to C (Sec. 4.2): b_ij is spread over the N-1 rows
+ * k != i of the submatrix C_ij, every c_ijkn (n != j) of a row receiving that
+ * row's share; then b_ij = 0.
+ */
+void orc_spread_B_to_C(orc_state *st)
+{
+    const int N = st->N, m = N - 1;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            int64_t x = st->b[ix2(N, i, j)];
+            int t = 0;
+            for (int k = 0; k < N; k++) {
+                if (k == i) continue;
+                int64_t sh = row_share(x, m, t++);
+                for (int n = 0; n < N; n++)
+                    if (n != j) st->c[ix4(N, i, j, k, n)] += sh;
+            }
+            st->b[ix2(N, i, j)] = 0;
+        }
+}
+
+/*
+ * Costs spreading from C to D (Sec. 4.2): c_ijkn is spread over the N-2 rows
+ * p not in {i,k} of the submatrix D_ijkn, every d_ijknpq (q not in {j,n}) of
+ * a row receiving that row's share; then c_ijkn = 0.
+ * Only first indices i in [i_lo, i_hi) are processed (the whole operation is
+ * [0, N)); the range exists so that a time-bounded sample can be measured.
+ */
+void orc_spread_C_to_D_range(orc_state *st, int i_lo, int i_hi)
+{
+    const int N = st->N, m = N - 2;
+    for (int i = i_lo; i < i_hi; i++)
+        for (int j = 0; j < N; j++)
+            for (int k = 0; k < N; k++) {
+                if (k == i) continue;
+                for (int n = 0; n < N; n++) {
+                    if (n == j) continue;
+                    int64_t x = st->c[ix4(N, i, j, k, n)];
+                    int t = 0;
+                    for (int p = 0; p < N; p++) {
+                        if (p == i || p == k) continue;
+                        int64_t sh = row_share(x, m, t++);
+                        for (int q = 0; q < N; q++)
+                            if (q != j && q != n) st->d[ix6(N, i, j, k, n, p, q)] += sh;
+                    }
+                    st->c[ix4(N, i, j, k, n)] = 0;
+                }
+            }
+}
+
+void orc_spread_C_to_D(orc_state *st) { orc_spread_C_to_D_range(st, 0, st->N); }
+
+/* ------------------------------------------- complementary cost transfer */
+
+/*
+ * Transfer between complementary costs of D (Sec. 4.3, the six coefficients of
+ * Eq. (11)).  A class is an unordered set of three pairs (i,j),(k,n),(p,q)
+ * with distinct facilities and distinct locations; it is visited once, with
+ * its facilities sorted i < k < p.  Its six members, in lexicographic order of
+ * their index 6-tuples (the facilities are distinct, so the order is decided
+ * by the first two facilities), are
+ *   d_ijknpq < d_ijpqkn < d_knijpq < d_knpqij < d_pqijkn < d_pqknij.
+ * The class sum T is re-split equally (reading R4).
+ * Only smallest facilities i in [i_lo, i_hi) are processed.
+ */
+void orc_complementary_D_range(orc_state *st, int i_lo, int i_hi)
+{
+    const int N = st->N;
+    int64_t *d = st->d;
+    for (int i = i_lo; i < i_hi; i++)
+        for (int k = i + 1; k < N; k++)
+            for (int p = k + 1; p < N; p++)
+                for (int j = 0; j < N; j++)
+                    for (int n = 0; n < N; n++) {
+                        if (n == j) continue;
+                        for (int q = 0; q < N; q++) {
+                            if (q == j || q == n) continue;
+                            size_t mem[6] = {
+                                ix6(N, i, j, k, n, p, q), ix6(N, i, j, p, q, k, n),
+                                ix6(N, k, n, i, j, p, q), ix6(N, k, n, p, q, i, j),
+                                ix6(N, p, q, i, j, k, n), ix6(N, p, q, k, n, i, j)};
+                            int64_t T = 0;
+                            for (int t = 0; t < 6; t++) T += d[mem[t]];
+                            track(st, T);
+                            for (int t = 0; t < 6; t++) d[mem[t]] = T / 6 + (t < T % 6 ? 1 : 0);
+                        }
+                    }
+}
+
+void orc_complementary_D(orc_state *st) { orc_complementary_D_range(st, 0, st->N); }
+
+/*
+ * Transfer between complementary costs of C (Sec. 4.3, Eq. (10)): the pair
+ * c_ijkn, c_knij with i < k (the first in lexicographic order) is re-split
+ * equally, the first member taking the odd unit (reading R4).
+ */
+void orc_complementary_C(orc_state *st)
+{
+    const int N = st->N;
+    for (int i = 0; i < N; i++)
+        for (int k = i + 1; k < N; k++)
+            for (int j = 0; j < N; j++)
+                for (int n = 0; n < N; n++) {
+                    if (n == j) continue;
+                    int64_t T = st->c[ix4(N, i, j, k, n)] + st->c[ix4(N, k, n, i, j)];
+                    st->c[ix4(N, i, j, k, n)] = T / 2 + T % 2;
+                    st->c[ix4(N, k, n, i, j)] = T / 2;
+                }
+}
+
+/* ------------------------------------------------------ cost concentration */
+
+/*
+ * Cost concentration from D to C (Sec. 4.1): for each (i,j,k,n) with i != k,
+ * j != n, M_rs = d_ijkn p_r q_s over the (N-2) x (N-2) submatrix D_ijkn
+ * (p_r: r-th row not in {i,k}, q_s: s-th column not in {j,n}); S = LAP(M) is
+ * added to c_ijkn and D_ijkn is replaced by M's residual coefficients
+ * (reading R5).  Only first indices i in [i_lo, i_hi) are processed.
+ */
+void orc_concentrate_D_to_C_range(orc_state *st, int i_lo, int i_hi)
+{
+    const int N = st->N, m = N - 2;
+    int64_t *M = malloc((size_t)m * m * sizeof(int64_t));
+    int64_t *u = malloc((size_t)m * sizeof(int64_t));
+    int64_t *v = malloc((size_t)m * sizeof(int64_t));
+    int rows[64], cols[64];
+    for (int i = i_lo; i < i_hi; i++)
+        for (int j = 0; j < N; j++)
+            for (int k = 0; k < N; k++) {
+                if (k == i) continue;
+                for (int n = 0; n < N; n++) {
+                    if (n == j) continue;
+                    int r = 0, s = 0;
+                    for (int p = 0; p < N; p++) if (p != i && p != k) rows[r++] = p;
+                    for (int q = 0; q < N; q++) if (q != j && q != n) cols[s++] = q;
+                    for (r = 0; r < m; r++)
+                        for (s = 0; s < m; s++)
+                            M[r * m + s] = st->d[ix6(N, i, j, k, n, rows[r], cols[s])];
+                    int64_t S = orc_lap(m, M, u, v, NULL, NULL, st);
+                    st->c[ix4(N, i, j, k, n)] += S;
+                    for (r = 0; r < m; r++)
+                        for (s = 0; s < m; s++)
+                            st->d[ix6(N, i, j, k, n, rows[r], cols[s])] = M[r * m + s] - u[r] - v[s];
+                }
+            }
+    free(M); free(u); free(v);
+}
+
+void orc_concentrate_D_to_C(orc_state *st) { orc_concentrate_D_to_C_range(st, 0, st->N); }
+
+/*
+ * Cost concentration from C to B (Sec. 4.1): for each (i,j), the
+ * (N-1) x (N-1) submatrix C_ij (rows k != i, columns n != j); b_ij += S and
+ * C_ij is replaced by its residual coefficients.
+ */
+void orc_concentrate_C_to_B(orc_state *st)
+{
+    const int N = st->N, m = N - 1;
+    int64_t *M = malloc((size_t)m * m * sizeof(int64_t));
+    int64_t *u = malloc((size_t)m * sizeof(int64_t));
+    int64_t *v = malloc((size_t)m * sizeof(int64_t));
+    int rows[64], cols[64];
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            int r = 0, s = 0;
+            for (int k = 0; k < N; k++) if (k != i) rows[r++] = k;
+            for (int n = 0; n < N; n++) if (n != j) cols[s++] = n;
+            for (r = 0; r < m; r++)
+                for (s = 0; s < m; s++)
+                    M[r * m + s] = st->c[ix4(N, i, j, rows[r], cols[s])];
+            int64_t S = orc_lap(m, M, u, v, NULL, NULL, st);
+            st->b[ix2(N, i, j)] += S;
+            for (r = 0; r < m; r++)
+                for (s = 0; s < m; s++)
+                    st->c[ix4(N, i, j, rows[r], cols[s])] = M[r * m + s] - u[r] - v[s];
+        }
+    free(M); free(u); free(v);
+}
+
+/*
+ * Cost concentration from B to LB (Sec. 4.1): S = LAP(B) is the increment
+ * LB' of Algorithm 1; B is replaced by its residual coefficients.
+ */
+int64_t orc_concentrate_B_to_LB(orc_state *st)
+{
+    const int N = st->N;
+    int64_t *u = malloc((size_t)N * sizeof(int64_t));
+    int64_t *v = malloc((size_t)N * sizeof(int64_t));
+    int64_t *M = malloc((size_t)N * N * sizeof(int64_t));
+    memcpy(M, st->b, (size_t)N * N * sizeof(int64_t));
+    int64_t S = orc_lap(N, M, u, v, NULL, NULL, st);
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+            st->b[ix2(N, i, j)] = M[i * N + j] - u[i] - v[j];
+    free(u); free(v); free(M);
+    return S;
+}
+
+/* -------------------------------------------------------------- Algorithm 1 */
+
+/*
+ * One pass of the loop of Algorithm 1 (reading R2): spread B->C, spread C->D,
+ * complementary D, concentrate D->C, complementary C, concentrate C->B,
+ * concentrate B->LB, LB += LB'.  In RLT1 mode (Sec. 6, strong branching) the
+ * three operations on D are skipped.  Returns LB after the pass.
+ */
+int64_t orc_iterate(orc_state *st)
+{
+    orc_spread_B_to_C(st);
+    if (!st->rlt1_only) {
+        orc_spread_C_to_D(st);
+        orc_complementary_D(st);
+        orc_concentrate_D_to_C(st);
+    }
+    orc_complementary_C(st);
+    orc_concentrate_C_to_B(st);
+    st->LB += orc_concentrate_B_to_LB(st);
+    st->iters++;
+    return st->LB;
+}
+
+/* Run k passes; hist (may be NULL) receives LB after each. */
+void orc_run(orc_state *st, int k, int64_t *hist)
+{
+    for (int t = 0; t < k; t++) {
+        int64_t lb = orc_iterate(st);
+        if (hist) hist[t] = lb;
+    }
+}
+
+/* ----------------------------------------------------------------- access */
+
+int orc_N(const orc_state *st) { return st->N; }
+int64_t orc_LB(const orc_state *st) { return st->LB; }
+int64_t *orc_b(orc_state *st) { return st->b; }
+int64_t *orc_c(orc_state *st) { return st->c; }
+int64_t *orc_d(orc_state *st) { return st->d; }
+void orc_work(const orc_state *st, int64_t *out4)
+{
+    out4[0] = st->laps; out4[1] = st->steps; out4[2] = st->relaxations; out4[3] = st->max_abs;
+}
+
+/* ----------------------------------------------- branch-and-bound subproblem */
+
+/*
+ * Residual instance of a branch-and-bound node (Sec. 6): facilities fac[t] are
+ * fixed to locations loc[t], t < kfix.  The free facilities and free locations
+ * are renumbered in ascending order (N' = N - kfix).  For any completion pi',
+ *   Q(full pi) = const + sum_x Blin[x][pi'(x)] + sum_{x != y} F'[x][y] D'[pi'(x)][pi'(y)]
+ * with
+ *   F'[x][y]  = F[fx][fy],  D'[x][y] = D[lx][ly],
+ *   Blin[x][y] = sum_t F[fx][a_t] D[ly][l_t] + F[a_t][fx] D[l_t][ly],
+ *   const     = sum_{t != t'} F[a_t][a_t'] D[l_t][l_t'].
+ * Outputs: Fp, Dp (N'*N' int32), Blin (N'*N' int64), *cst.  Returns N'.
+ */
+int orc_subproblem(int N, const int32_t *F, const int32_t *Dist, int kfix,
+                   const int32_t *fac, const int32_t *loc,
+                   int32_t *Fp, int32_t *Dp, int64_t *Blin, int64_t *cst)
+{
+    int ff[64], fl[64], nf = 0, nl = 0;
+    for (int a = 0; a < N; a++) {
+        int fixed = 0;
+        for (int t = 0; t < kfix; t++) if (fac[t] == a) fixed = 1;
+        if (!fixed) ff[nf++] = a;
+    }
+    for (int l = 0; l < N; l++) {
+        int fixed = 0;
+        for (int t = 0; t < kfix; t++) if (loc[t] == l) fixed = 1;
+        if (!fixed) fl[nl++] = l;
+    }
+    const int Np = nf;
+    for (int x = 0; x < Np; x++)
+        for (int y = 0; y < Np; y++) {
+            Fp[x * Np + y] = F[ix2(N, ff[x], ff[y])];
+            Dp[x * Np + y] = Dist[ix2(N, fl[x], fl[y])];
+            int64_t s = 0;
+            for (int t = 0; t < kfix; t++)
+                s += (int64_t)F[ix2(N, ff[x], fac[t])] * Dist[ix2(N, fl[y], loc[t])] +
+                     (int64_t)F[ix2(N, fac[t], ff[x])] * Dist[ix2(N, loc[t], fl[y])];
+            Blin[x * Np + y] = s;
+        }
+    int64_t c0 = 0;
+    for (int t = 0; t < kfix; t++)
+        for (int t2 = 0; t2 < kfix; t2++)
+            if (t != t2) c0 += (int64_t)F[ix2(N, fac[t], fac[t2])] * Dist[ix2(N, loc[t], loc[t2])];
+    *cst = c0;
+    return Np;
+}
+
+/* LB <- LB + x (the last line of the loop of Algorithm 1, for step-wise use). */
+void orc_add_LB(orc_state *st, int64_t x) { st->LB += x; }
