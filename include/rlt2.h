@@ -1,0 +1,185 @@
+/*
+ * rlt2.h -- C ABI of the GB300 (sm_103a) level-2 RLT dual-ascent library.
+ *
+ * The library computes the RLT2 dual-ascent lower bound of the Koopmans-
+ * Beckmann quadratic assignment problem (QAP), Algorithm 1 of Goncalves,
+ * Pessoa, Drummond, Bentes, Farias, "Solving the Quadratic Assignment Problem
+ * on heterogeneous environment (CPUs and GPUs) with the application of Level 2
+ * Reformulation and Linearization Technique" (arXiv:1510.02065).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns RLT2_OK (0) or a negative RLT2_E_* code;
+ *    rlt2_strerror() names it.  No function aborts the process.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory on the current device.  Inputs are copied or only read;
+ *    the caller keeps ownership of every buffer it passes.  A context owns
+ *    all the device memory it allocates and frees it in rlt2_destroy().
+ *  - Indices are 0-based.  Matrices are row-major int32.
+ *  - A context is not thread-safe; distinct contexts are independent and
+ *    may run on distinct streams concurrently.
+ *  - Arithmetic is exact: reduced costs, potentials and LAP values are
+ *    integers (int32 on the device, guarded against overflow at creation);
+ *    the bound LB is carried in int64 and also reported as a double.
+ *
+ * Notation (Sec. 3, Eq. (5)): x_ij / b_ij is the assignment variable and its
+ * reduced cost (matrix B, N x N); x'_ijkn / c_ijkn the pair variable and its
+ * reduced cost (matrix C); x''_ijknpq / d_ijknpq the triple variable and its
+ * reduced cost (matrix D).  The exported layouts are compact:
+ *   x: b[i][j]                          N*N entries
+ *   y: c[i][j][k'][n']                  N*N*(N-1)*(N-1) entries, k' = rank of k
+ *                                       among the facilities != i, n' = rank of n
+ *                                       among the locations != j
+ *   z: d[i][j][k'][n'][r][s]            y's count * (N-2)*(N-2) entries, r = rank
+ *                                       of p among the facilities not in {i,k},
+ *                                       s = rank of q among the locations not in {j,n}
+ * A "tile" is the (N-2) x (N-2) submatrix D_ijkn of Sec. 4.1; tile index
+ * t = ((i*N + j)*(N-1) + k')*(N-1) + n'.
+ */
+#ifndef RLT2_H
+#define RLT2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RLT2_OK            0
+#define RLT2_E_INVAL      -1   /* bad argument: null pointer, N out of range, negative entry */
+#define RLT2_E_OOM        -2   /* device or host allocation failed                            */
+#define RLT2_E_OVERFLOW   -3   /* costs too large for exact int32 arithmetic (see rlt2_create) */
+#define RLT2_E_CUDA       -4   /* a CUDA runtime call failed                                  */
+#define RLT2_E_TIMEOUT    -5   /* a bounded device-side wait gave up                          */
+#define RLT2_E_STATE      -6   /* call out of order (e.g. history capacity exhausted)         */
+#define RLT2_E_INTERNAL   -7   /* a kernel's internal consistency check failed (a bug)        */
+
+#define RLT2_MIN_N         3
+#define RLT2_MAX_N        64   /* the LAP kernels hold at most 64 columns per warp */
+#define RLT2_LAP_MAX_ENTRY 536870911  /* 2^29 - 1: largest LAP cost the int32 kernels accept */
+
+/* Options of a dual-ascent context.  Zero-initialise, or call rlt2_default_opts. */
+typedef struct {
+    int rlt1_only;        /* 1: Algorithm 1 without the three operations on D
+                             (the strong-branching dual of Sec. 6); default 0 */
+    int use_graph;        /* 1 (default): each pass is one captured CUDA graph   */
+    int profile;          /* 1: record CUDA events around every stage of every
+                             pass (see rlt2_stage_times); default 0           */
+    int max_iters;        /* capacity of the on-device LB history; default 65536 */
+    double ub;            /* UB of Algorithm 1 (stop once LB >= UB); <= 0: none  */
+    double min_progress;  /* K of Algorithm 1: stop once LB'/UB < K; 0: never     */
+    void *stream;         /* cudaStream_t to run on; NULL = the legacy default stream */
+} rlt2_opts;
+
+typedef struct rlt2_ctx rlt2_ctx;
+
+void rlt2_default_opts(rlt2_opts *opts);
+const char *rlt2_strerror(int code);
+
+/*
+ * Create a dual-ascent context for one QAP instance and initialise it as
+ * Algorithm 1 does: LB <- lb_const, b_ij <- B_lin[i][j] (or 0), c_ijkn <- F_ik
+ * * D_jn for i != k and j != n, d <- 0.
+ *   F, D      host, N x N int32 flow and distance matrices (Eq. (1)); entries
+ *             must be >= 0; the diagonals are ignored (only i != k enters).
+ *   N         RLT2_MIN_N .. RLT2_MAX_N.
+ *   B_lin     host, N x N int32 linear costs b_ij (a branch-and-bound node's
+ *             residual instance), or NULL for none.  Entries >= 0.
+ *   lb_const  constant part of the objective (0 at the root).
+ *   opts      options, or NULL for the defaults.
+ *   out       receives the context.
+ * Errors: RLT2_E_INVAL, RLT2_E_OVERFLOW when U = sum_{i!=k} F_ik * max_{j!=n}
+ * D_jn + sum_i max_j B_lin[i][j] exceeds RLT2_LAP_MAX_ENTRY (every reduced
+ * cost, class sum and Hungarian potential is then bounded by 3U and fits
+ * int32), RLT2_E_OOM, RLT2_E_CUDA.  Device memory: about 4 B * N^2 (N-1)^2
+ * (N-2)^2 for D plus 12 B * N^2 (N-1)^2.
+ */
+int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
+                int64_t lb_const, const rlt2_opts *opts, rlt2_ctx **out);
+
+/* Release every resource of ctx (NULL is allowed). */
+void rlt2_destroy(rlt2_ctx *ctx);
+
+/*
+ * Enqueue k passes of the loop of Algorithm 1 on the context's stream:
+ * spread B->C and C->D with the transfer between complementary costs of D
+ * (one fused pass over D), concentration D->C (N^2 (N-1)^2 Hungarian LAPs of
+ * size N-2, Sec. 4.1), transfer between complementary costs of C fused into
+ * concentration C->B (N^2 LAPs of size N-1), concentration B->LB (one LAP of
+ * size N) and LB <- LB + LB'.  Returns without waiting for the GPU.  Passes
+ * after the stopping rule of Algorithm 1 fired (opts.ub / opts.min_progress)
+ * do nothing.  Errors: RLT2_E_INVAL (k < 0), RLT2_E_STATE (history full),
+ * RLT2_E_CUDA.
+ */
+int rlt2_iterate(rlt2_ctx *ctx, int k);
+
+/*
+ * Wait for the context's stream and read the bound.
+ *   lb        (may be NULL) LB as a double
+ *   lb_exact  (may be NULL) LB as an exact int64
+ *   iters     (may be NULL) passes completed so far
+ * Errors: RLT2_E_TIMEOUT if a device-side wait gave up, RLT2_E_CUDA.
+ */
+int rlt2_bound(rlt2_ctx *ctx, double *lb, int64_t *lb_exact, int *iters);
+
+/* LB after each completed pass, oldest first: up to cap values into host
+ * buffer out; *count receives the number written. */
+int rlt2_bound_history(rlt2_ctx *ctx, int64_t *out, int cap, int *count);
+
+/*
+ * Copy the current reduced costs to host memory in the compact layouts above.
+ *   level 0: x (B), count N*N;  1: y (C), count N^2 (N-1)^2;
+ *   2: z (D), count N^2 (N-1)^2 (N-2)^2.
+ * Synchronises the context's stream.  Errors: RLT2_E_INVAL on a wrong count.
+ */
+int rlt2_get_state(rlt2_ctx *ctx, int level, int32_t *host_buf, size_t count);
+
+/*
+ * Cumulative work of the Hungarian method in this context (synchronises):
+ * out[0] LAPs solved, out[1] steps (columns labelled), out[2] relaxations
+ * (reduced distances evaluated for unlabelled columns), out[3] steps of the
+ * D->C concentrations alone.
+ */
+int rlt2_work(rlt2_ctx *ctx, int64_t out[4]);
+
+/*
+ * Stage times recorded while opts.profile was set (synchronises): out[s] =
+ * total milliseconds of stage s over all profiled passes, s = 0 fused
+ * spread/complementary pass over D, 1 concentration D->C, 2 complementary C +
+ * concentration C->B, 3 concentration B->LB; *passes = passes recorded.
+ * rlt2_reset_stage_times() clears the totals.
+ */
+int rlt2_stage_times(rlt2_ctx *ctx, double out[4], int *passes);
+int rlt2_reset_stage_times(rlt2_ctx *ctx);
+
+/* Device pointer of the context's stream-ordered state (for the Python binding's
+ * zero-copy views): which 0 = x, 1 = y (C), 2 = z (tile-padded: row stride
+ * rlt2_row_stride(N)).  Returns NULL on error. */
+void *rlt2_device_state(rlt2_ctx *ctx, int which);
+int rlt2_row_stride(int N);
+
+/*
+ * Batched linear assignment with the library's Hungarian kernel (the LAP of
+ * Sec. 4.1, solved by the method the dual ascent uses).  count independent
+ * n x n problems, one warp each.
+ *   M       device, count * n * n int32, row-major, entries in
+ *           [0, RLT2_LAP_MAX_ENTRY]
+ *   n       1 .. 64;  count >= 0
+ *   S       device, count int64: optimal cost (-1 for a matrix with an entry
+ *           out of range)
+ *   assign  device, count * n int32: column of each row (may be NULL)
+ *   u, v    device, count * n int32: row and column potentials; M - u - v
+ *           is >= 0 and 0 on the assignment (each may be NULL)
+ *   work    device, count * 2 int64: steps, relaxations (may be NULL)
+ *   stream  cudaStream_t or NULL.
+ * Synchronises the stream.  Errors: RLT2_E_INVAL (bad n/count/pointer or an
+ * entry out of range: every other problem is still solved), RLT2_E_CUDA.
+ */
+int rlt2_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
+                   int32_t *u, int32_t *v, int64_t *work, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLT2_H */

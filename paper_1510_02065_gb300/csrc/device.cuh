@@ -1,0 +1,302 @@
+// device.cuh -- device-side building blocks of the RLT2 library (sm_103a).
+//
+//  * bounded mbarrier waits and 1-D bulk copies global -> shared (the TMA
+//    engine's cp.async.bulk), used to stage LAP tiles;
+//  * warp_hungarian<NS, PACK>: the Hungarian method of the cost concentration
+//    (Sec. 4.1), one warp per linear assignment problem.
+#pragma once
+#include <climits>
+#include <cstdint>
+
+namespace rlt2 {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kInf = INT_MAX;
+
+// bits of the device status word
+constexpr int kDevTimeout = 1;
+constexpr int kDevRange = 2;
+constexpr int kDevInternal = 4;   // an invariant of the Hungarian method failed
+
+// Iteration bound of every spin on an mbarrier.  try_wait suspends the thread
+// for a while on each call, so the bound is far above any real wait.
+constexpr unsigned kSpinLimit = 1u << 22;
+
+struct DevStatus {
+    int err;                     // kDev* bits
+    int pad;
+    unsigned long long laps;     // LAPs solved
+    unsigned long long steps;    // columns labelled (all concentrations)
+    unsigned long long relax;    // reduced distances evaluated
+    unsigned long long dsteps;   // steps of the D->C concentrations
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Arrive on bar expecting `bytes` of asynchronous transactions, then start a
+// bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, unsigned bytes,
+                                          uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Wait for the phase of parity `parity` of bar to complete; false after
+// kSpinLimit unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------ register slots
+// A column c of a LAP lives in lane c % 32, slot c / 32 (NS slots per lane).
+// Slot selection by a warp-uniform runtime index without local memory.
+
+template <int NS, typename T>
+__device__ __forceinline__ T pick(const T (&a)[NS], int s)
+{
+    if constexpr (NS == 1) return a[0];
+    else return s ? a[1] : a[0];
+}
+
+template <int NS, typename T>
+__device__ __forceinline__ void put(T (&a)[NS], int s, T x)
+{
+    if constexpr (NS == 1) a[0] = x;
+    else {
+        if (s) a[1] = x;
+        else a[0] = x;
+    }
+}
+
+__device__ __forceinline__ long long warp_sum64(long long x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+// ------------------------------------------------------- Hungarian method
+//
+// Shortest-augmenting-path Hungarian method with row and column potentials,
+// rows inserted in ascending order from u = v = 0; the next column labelled is
+// the unlabelled one of least reduced distance, ties to the smallest column;
+// a distance label and its predecessor change only on a strict improvement.
+//
+// Warp mapping: lane c % 32, slot c / 32 owns column c: its potential v, the
+// row matched to it (rowOf) and that row's potential (uM), its distance label
+// and predecessor column (way).  Each step relaxes the newly reached row
+// against every column at once and takes the argmin with one warp reduction.
+//
+// Potentials are updated lazily.  Within the insertion of one row, let D be
+// the running sum of the step minima.  A column labelled when the sum was
+// dlab ends the phase with v -= Dend - dlab and its row with u += Dend - dlab;
+// unlabelled columns keep v; the new row gets u = Dend.  Distance labels are
+// stored plus the D of their last update, so the per-step update of every
+// label disappears.  In exact integer arithmetic this takes the same decisions
+// and ends with the same (u, v, assignment) as updating every potential at
+// every step.
+//
+// PACK: when every key is below 2^25 the key and its column are packed into
+// one 32-bit value (key * 64 + column) and one reduction yields both the
+// minimum and the smallest column attaining it.
+//
+// Value range: with entries in [0, A], |u|, |v| <= A and every key <= 3A, so
+// A <= 2^29 - 1 fits int32 (PACK needs 3A < 2^25).
+//
+// M: shared memory, row r at M + r * ld, columns 0..n-1 (n <= 32 * NS).
+//
+// Every loop is bounded: a phase labels at most r + 1 columns and an
+// augmenting path is at most that long.  If an invariant fails (it cannot in
+// exact arithmetic) the function stops and returns false instead of spinning.
+template <int NS, bool PACK>
+__device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld, int n,
+                                               int (&rowOf)[NS], int (&uM)[NS], int (&v)[NS],
+                                               long long &steps_out, long long &relax_out)
+{
+    const int lane = threadIdx.x & 31;
+    bool valid[NS], used[NS];
+    int dist[NS], way[NS], dlab[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        valid[s] = lane + 32 * s < n;
+        rowOf[s] = -1;
+        uM[s] = 0;
+        v[s] = 0;
+        way[s] = -1;
+        dlab[s] = 0;
+    }
+    long long steps = 0, relax = 0;
+
+    for (int r = 0; r < n; ++r) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            used[s] = !valid[s];
+            dist[s] = kInf;
+        }
+        int i0 = r;        // row scanned at this step
+        int j0 = -1;       // column through which i0 was reached (-1: the new row)
+        int c0 = 0;        // u(i0) - D before this step
+        int K = 0, jf = 0, Dend = 0;
+        for (;;) {
+            if (++K > r + 1) return false;
+            const int *Mrow = M + i0 * ld + lane;
+            int key[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                if (!used[s]) {
+                    const int cand = Mrow[32 * s] - v[s] - c0;
+                    if (cand < dist[s]) {
+                        dist[s] = cand;
+                        way[s] = j0;
+                    }
+                }
+                key[s] = used[s] ? kInf : dist[s];
+            }
+            int Dk, j1;
+            if constexpr (PACK) {
+                int pk = used[0] ? kInf : (key[0] << 6) | lane;
+                if constexpr (NS == 2) {
+                    const int p1 = used[1] ? kInf : (key[1] << 6) | (lane + 32);
+                    pk = min(pk, p1);
+                }
+                const int m = __reduce_min_sync(kFull, pk);
+                Dk = m >> 6;
+                j1 = m & 63;
+            } else {
+                int lmin = key[0];
+                if constexpr (NS == 2) lmin = min(lmin, key[1]);
+                Dk = __reduce_min_sync(kFull, lmin);
+                const unsigned b0 = __ballot_sync(kFull, key[0] == Dk);
+                if constexpr (NS == 1) {
+                    j1 = __ffs(b0) - 1;
+                } else {
+                    const unsigned b1 = __ballot_sync(kFull, key[1] == Dk);
+                    j1 = b0 ? __ffs(b0) - 1 : 31 + __ffs(b1);
+                }
+            }
+            const int src = j1 & 31, sl = j1 >> 5;
+            const int rj = __shfl_sync(kFull, pick<NS>(rowOf, sl), src);
+            const int uj = __shfl_sync(kFull, pick<NS>(uM, sl), src);
+            if (rj < 0) {  // free column: augmenting path found
+                jf = j1;
+                Dend = Dk;
+                break;
+            }
+            if (lane == src) {
+                put<NS>(used, sl, true);
+                put<NS>(dlab, sl, Dk);
+            }
+            i0 = rj;
+            j0 = j1;
+            c0 = uj - Dk;
+        }
+        steps += K;
+        relax += (long long)K * n - (long long)K * (K - 1) / 2;
+
+        // lazy potential updates of the columns labelled in this phase
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (used[s] && valid[s]) {
+                const int dd = Dend - dlab[s];
+                v[s] -= dd;
+                uM[s] += dd;
+            }
+        }
+        // augment: each column on the path takes the row of its predecessor
+        int c = jf;
+        for (int hop = 0;; ++hop) {
+            if (hop > K) return false;
+            const int cs = c >> 5, cl = c & 31;
+            const int w = __shfl_sync(kFull, pick<NS>(way, cs), cl);
+            int nr = r, nu = Dend;
+            const int ws = (w < 0 ? 0 : w) >> 5, wl = (w < 0 ? 0 : w) & 31;
+            const int pr = __shfl_sync(kFull, pick<NS>(rowOf, ws), wl);
+            const int pu = __shfl_sync(kFull, pick<NS>(uM, ws), wl);
+            if (w >= 0) {
+                nr = pr;
+                nu = pu;
+            }
+            if (lane == cl) {
+                put<NS>(rowOf, cs, nr);
+                put<NS>(uM, cs, nu);
+            }
+            if (w < 0) break;
+            c = w;
+        }
+    }
+    steps_out += steps;
+    relax_out += relax;
+    return true;
+}
+
+// S = sum of the row and column potentials = cost of the assignment.
+template <int NS>
+__device__ __forceinline__ long long lap_value(int n, const int (&uM)[NS], const int (&v)[NS])
+{
+    const int lane = threadIdx.x & 31;
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+        if (lane + 32 * k < n) s += (long long)uM[k] + v[k];
+    return warp_sum64(s);
+}
+
+// Row potentials by row index into shared uRow[n] (and the column of each row
+// into colOf[n] when non-null); the caller syncs the warp afterwards.
+template <int NS>
+__device__ __forceinline__ void scatter_rows(int n, const int (&rowOf)[NS], const int (&uM)[NS],
+                                             int *uRow, int *colOf)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const int c = lane + 32 * k;
+        if (c < n && rowOf[k] >= 0 && rowOf[k] < n) {
+            uRow[rowOf[k]] = uM[k];
+            if (colOf) colOf[rowOf[k]] = c;
+        }
+    }
+}
+
+}  // namespace rlt2

@@ -1,0 +1,368 @@
+// lap_kernels.cu -- the cost concentrations of Algorithm 1 (Sec. 4.1) on sm_103a.
+//
+//   dlap_kernel   concentration D -> C: one Hungarian LAP of size N-2 per tile
+//                 D_ijkn; tiles are streamed into shared memory by 1-D bulk
+//                 copies (cp.async.bulk, double-buffered per warp, work taken
+//                 from a global counter); the residual tile is written back in
+//                 place and S goes to yS.
+//   clap_kernel   transfer between complementary costs of C fused with the
+//                 concentration C -> B (N^2 LAPs of size N-1).
+//   xlap_kernel   concentration B -> LB (one LAP of size N), LB += LB', history,
+//                 stopping rule of Algorithm 1.
+//   lap_batch_kernel  the same Hungarian on caller-supplied matrices.
+#include "device.cuh"
+#include "kernels.h"
+
+namespace rlt2 {
+
+constexpr int kDlapWarps = 4;
+constexpr int kClapWarps = 4;
+constexpr int kBatchWarps = 4;
+
+// ------------------------------------------------------------ D -> C sweep
+
+template <int NS, bool PACK>
+__global__ void __launch_bounds__(kDlapWarps * 32)
+    dlap_kernel(PassState p, int n, int RS, long long ntiles)
+{
+    if (*p.stop) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int TS = n * RS;
+    const unsigned bytes = (unsigned)TS * 4u;
+    int *bufs = reinterpret_cast<int *>(smem) + (size_t)warp * 2 * TS;
+    unsigned char *tail = smem + (size_t)kDlapWarps * 2 * TS * 4;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tail) + warp * 2;
+    int *uRow = reinterpret_cast<int *>(tail + kDlapWarps * 16) + warp * 64;
+
+    if (lane == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    auto grab = [&]() -> long long {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(p.counter, 1u);
+        return (long long)__shfl_sync(kFull, t, 0);
+    };
+
+    long long t = grab();
+    if (t < ntiles && lane == 0) bulk_load(bufs, p.z + t * TS, bytes, &bars[0]);
+    unsigned parity = 0;  // bit b: parity of the next completion of bars[b]
+    int cur = 0;
+    long long steps = 0, relax = 0, laps = 0;
+    while (t < ntiles) {
+        const long long tn = grab();
+        const bool pref = tn < ntiles;
+        if (pref && lane == 0) {
+            fence_proxy_async_smem();
+            bulk_load(bufs + (cur ^ 1) * TS, p.z + tn * TS, bytes, &bars[cur ^ 1]);
+        }
+        const bool got = __all_sync(kFull, mbar_wait(&bars[cur], (parity >> cur) & 1u));
+        if (!got) {
+            // give up: record it, let the copies in flight land (bounded), leave
+            if (lane == 0) atomicOr(&p.status->err, kDevTimeout);
+            mbar_wait(&bars[cur], (parity >> cur) & 1u);
+            if (pref) mbar_wait(&bars[cur ^ 1], (parity >> (cur ^ 1)) & 1u);
+            __syncwarp();
+            return;
+        }
+        parity ^= 1u << cur;
+        const int *buf = bufs + cur * TS;
+
+        int rowOf[NS], uM[NS], v[NS];
+        if (!warp_hungarian<NS, PACK>(buf, RS, n, rowOf, uM, v, steps, relax) && lane == 0)
+            atomicOr(&p.status->err, kDevInternal);
+        scatter_rows<NS>(n, rowOf, uM, uRow, nullptr);
+        __syncwarp();
+        int *g = p.z + t * TS;
+        for (int r = 0; r < n; ++r) {
+            const int ur = uRow[r];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int c = lane + 32 * s;
+                if (c < RS) g[r * RS + c] = c < n ? buf[r * RS + c] - ur - v[s] : 0;
+            }
+        }
+        const long long S = lap_value<NS>(n, uM, v);
+        if (lane == 0) p.yS[t] = (int)S;
+        ++laps;
+        __syncwarp();
+        t = tn;
+        cur ^= 1;
+    }
+    if (lane == 0 && laps) {
+        atomicAdd(&p.status->laps, (unsigned long long)laps);
+        atomicAdd(&p.status->steps, (unsigned long long)steps);
+        atomicAdd(&p.status->dsteps, (unsigned long long)steps);
+        atomicAdd(&p.status->relax, (unsigned long long)relax);
+    }
+}
+
+// -------------------------------------------- complementary C + C -> B
+
+// In RLT1 mode the input of C -> B is C plus the spread of B (no D in between);
+// this kernel writes it to yS so that the fused transfer reads one buffer.
+__global__ void spread_x_to_y_kernel(PassState p, int N)
+{
+    if (*p.stop) return;
+    const int m = N - 1;
+    const long long tiles = (long long)N * N * m * m;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tiles;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int kk = (int)((t / m) % m);
+        const int ij = (int)(t / ((long long)m * m));
+        const int b = p.x[ij];
+        p.yS[t] = p.yC[t] + b / m + (kk < b % m ? 1 : 0);
+    }
+}
+
+template <int NS, bool PACK>
+__global__ void __launch_bounds__(kClapWarps * 32) clap_kernel(PassState p, int N)
+{
+    if (*p.stop) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = N - 1;
+    int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * (m * m + 64);
+    int *uRow = buf + m * m;
+    long long steps = 0, relax = 0, laps = 0;
+    for (int prob = blockIdx.x * kClapWarps + warp; prob < N * N; prob += gridDim.x * kClapWarps) {
+        const int i = prob / N, j = prob % N;
+        const long long base = (long long)prob * m * m;
+        // transfer between the complementary pair {c_ijkn, c_knij} (Eq. (10)):
+        // the lexicographically first member (i < k) takes the odd unit
+        for (int e = lane; e < m * m; e += 32) {
+            const int kk = e / m, nn = e % m;
+            const int k = kk + (kk >= i), n = nn + (nn >= j);
+            const int i2 = i - (i > k), j2 = j - (j > n);
+            const long long t2 = ((long long)(k * N + n) * m + i2) * m + j2;
+            const int T = p.yS[base + e] + p.yS[t2];
+            buf[e] = i < k ? T - T / 2 : T / 2;
+        }
+        __syncwarp();
+        int rowOf[NS], uM[NS], v[NS];
+        if (!warp_hungarian<NS, PACK>(buf, m, m, rowOf, uM, v, steps, relax) && lane == 0)
+            atomicOr(&p.status->err, kDevInternal);
+        scatter_rows<NS>(m, rowOf, uM, uRow, nullptr);
+        __syncwarp();
+        for (int r = 0; r < m; ++r) {
+            const int ur = uRow[r];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int c = lane + 32 * s;
+                if (c < m) p.yC[base + r * m + c] = buf[r * m + c] - ur - v[s];
+            }
+        }
+        const long long S = lap_value<NS>(m, uM, v);
+        if (lane == 0) p.x[prob] = (int)S;
+        ++laps;
+        __syncwarp();
+    }
+    if (lane == 0 && laps) {
+        atomicAdd(&p.status->laps, (unsigned long long)laps);
+        atomicAdd(&p.status->steps, (unsigned long long)steps);
+        atomicAdd(&p.status->relax, (unsigned long long)relax);
+    }
+}
+
+// ------------------------------------------------------------- B -> LB
+
+template <int NS, bool PACK>
+__global__ void __launch_bounds__(32) xlap_kernel(PassState p, int N)
+{
+    if (*p.stop) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    int *buf = reinterpret_cast<int *>(smem);
+    int *uRow = buf + N * N;
+    for (int e = lane; e < N * N; e += 32) buf[e] = p.x[e];
+    __syncwarp();
+    long long steps = 0, relax = 0;
+    int rowOf[NS], uM[NS], v[NS];
+    if (!warp_hungarian<NS, PACK>(buf, N, N, rowOf, uM, v, steps, relax) && lane == 0)
+        atomicOr(&p.status->err, kDevInternal);
+    scatter_rows<NS>(N, rowOf, uM, uRow, nullptr);
+    __syncwarp();
+    for (int r = 0; r < N; ++r) {
+        const int ur = uRow[r];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int c = lane + 32 * s;
+            if (c < N) p.x[r * N + c] = buf[r * N + c] - ur - v[s];
+        }
+    }
+    const long long S = lap_value<NS>(N, uM, v);
+    if (lane == 0) {
+        const long long lb = *p.LB + S;
+        *p.LB = lb;
+        const int it = *p.iter;
+        if (it < p.hist_cap) p.hist[it] = lb;
+        *p.iter = it + 1;
+        // stopping rule of Algorithm 1: continue while progress >= K and LB < UB
+        if (p.ub > 0.0) {
+            if ((double)lb >= p.ub) *p.stop = 1;
+            if (p.min_progress > 0.0 && (double)S / p.ub < p.min_progress) *p.stop = 1;
+        }
+        atomicAdd(&p.status->laps, 1ull);
+        atomicAdd(&p.status->steps, (unsigned long long)steps);
+        atomicAdd(&p.status->relax, (unsigned long long)relax);
+    }
+}
+
+// ------------------------------------------------------------- LAP batch
+
+template <int NS>
+__global__ void __launch_bounds__(kBatchWarps * 32)
+    lap_batch_kernel(const int32_t *__restrict__ M, int n, int count, int64_t *S, int32_t *assign,
+                     int32_t *uo, int32_t *vo, int64_t *work, DevStatus *status)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * (n * n + 128);
+    int *uRow = buf + n * n;
+    int *colOf = uRow + 64;
+    for (int prob = blockIdx.x * kBatchWarps + warp; prob < count; prob += gridDim.x * kBatchWarps) {
+        const int32_t *src = M + (size_t)prob * n * n;
+        int mx = 0, bad = 0;
+        for (int e = lane; e < n * n; e += 32) {
+            const int a = src[e];
+            buf[e] = a;
+            mx = max(mx, a);
+            bad |= (a < 0) | (a > 536870911);
+        }
+        bad = __any_sync(kFull, bad);
+        mx = __reduce_max_sync(kFull, mx);
+        __syncwarp();
+        if (bad) {
+            if (lane == 0) {
+                S[prob] = -1;
+                atomicOr(&status->err, kDevRange);
+            }
+            continue;
+        }
+        long long steps = 0, relax = 0;
+        int rowOf[NS], uM[NS], v[NS];
+        const bool fine = mx < (1 << 25) / 3
+                              ? warp_hungarian<NS, true>(buf, n, n, rowOf, uM, v, steps, relax)
+                              : warp_hungarian<NS, false>(buf, n, n, rowOf, uM, v, steps, relax);
+        if (!fine && lane == 0) atomicOr(&status->err, kDevInternal);
+        scatter_rows<NS>(n, rowOf, uM, uRow, colOf);
+        __syncwarp();
+        const long long s = lap_value<NS>(n, uM, v);
+        for (int e = lane; e < n; e += 32) {
+            if (assign) assign[(size_t)prob * n + e] = colOf[e];
+            if (uo) uo[(size_t)prob * n + e] = uRow[e];
+        }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const int c = lane + 32 * k;
+            if (vo && c < n) vo[(size_t)prob * n + c] = v[k];
+        }
+        if (lane == 0) {
+            S[prob] = s;
+            if (work) {
+                work[2 * (size_t)prob] = steps;
+                work[2 * (size_t)prob + 1] = relax;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <int NS, bool PACK>
+static cudaError_t dlap_go(const Geom &g, const PassState &p, int sm_count, cudaStream_t s)
+{
+    const size_t smem = (size_t)kDlapWarps * (2 * (size_t)g.TS * 4 + 16 + 256);
+    auto k = dlap_kernel<NS, PACK>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDlapWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)per_sm * sm_count;
+    const long long need = (g.tiles + kDlapWarps - 1) / kDlapWarps;
+    if (grid > need) grid = need;
+    k<<<(unsigned)grid, kDlapWarps * 32, smem, s>>>(p, g.n, g.RS, g.tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dlap(const Geom &g, const PassState &p, int sm_count, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    if (g.n <= 32) return p.pack ? dlap_go<1, true>(g, p, sm_count, s) : dlap_go<1, false>(g, p, sm_count, s);
+    return p.pack ? dlap_go<2, true>(g, p, sm_count, s) : dlap_go<2, false>(g, p, sm_count, s);
+}
+
+template <int NS, bool PACK>
+static cudaError_t clap_go(const Geom &g, const PassState &p, cudaStream_t s)
+{
+    const int m = g.N - 1;
+    const size_t smem = (size_t)kClapWarps * (m * m + 64) * 4;
+    auto k = clap_kernel<NS, PACK>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int probs = g.N * g.N;
+    const int grid = (probs + kClapWarps - 1) / kClapWarps;
+    k<<<grid, kClapWarps * 32, smem, s>>>(p, g.N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clap(const Geom &g, const PassState &p, cudaStream_t s)
+{
+    if (p.rlt1_only) {
+        const long long tiles = g.tiles;
+        int grid = (int)((tiles + 255) / 256);
+        if (grid > 4096) grid = 4096;
+        spread_x_to_y_kernel<<<grid, 256, 0, s>>>(p, g.N);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (g.N - 1 <= 32) return p.pack ? clap_go<1, true>(g, p, s) : clap_go<1, false>(g, p, s);
+    return p.pack ? clap_go<2, true>(g, p, s) : clap_go<2, false>(g, p, s);
+}
+
+template <int NS, bool PACK>
+static cudaError_t xlap_go(const Geom &g, const PassState &p, cudaStream_t s)
+{
+    const size_t smem = (size_t)(g.N * g.N + 64) * 4;
+    xlap_kernel<NS, PACK><<<1, 32, smem, s>>>(p, g.N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xlap(const Geom &g, const PassState &p, cudaStream_t s)
+{
+    if (g.N <= 32) return p.pack ? xlap_go<1, true>(g, p, s) : xlap_go<1, false>(g, p, s);
+    return p.pack ? xlap_go<2, true>(g, p, s) : xlap_go<2, false>(g, p, s);
+}
+
+template <int NS>
+static cudaError_t batch_go(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
+                            int32_t *u, int32_t *v, int64_t *work, DevStatus *status, cudaStream_t s)
+{
+    const size_t smem = (size_t)kBatchWarps * ((size_t)n * n + 128) * 4;
+    auto k = lap_batch_kernel<NS>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int grid = (count + kBatchWarps - 1) / kBatchWarps;
+    if (grid > 65535) grid = 65535;
+    k<<<grid, kBatchWarps * 32, smem, s>>>(M, n, count, S, assign, u, v, work, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
+                             int32_t *u, int32_t *v, int64_t *work, DevStatus *status,
+                             cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    if (n <= 32) return batch_go<1>(M, n, count, S, assign, u, v, work, status, s);
+    return batch_go<2>(M, n, count, S, assign, u, v, work, status, s);
+}
+
+}  // namespace rlt2

@@ -1,0 +1,251 @@
+"""Thin Python binding of the C ABI in include/rlt2.h (argument marshalling only).
+
+Every function carries the name of the C entry point it calls.  Host arrays
+are numpy; device buffers are passed as integer addresses (e.g. a torch CUDA
+tensor's ``data_ptr()``) and streams as ``cudaStream_t`` integers (e.g.
+``torch.cuda.current_stream().cuda_stream``).  All computation happens in
+librlt2.so; there is no fallback: if the library is not built, importing the
+binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librlt2.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rlt2.h")
+
+RLT2_OK = 0
+RLT2_E_INVAL = -1
+RLT2_E_OOM = -2
+RLT2_E_OVERFLOW = -3
+RLT2_E_CUDA = -4
+RLT2_E_TIMEOUT = -5
+RLT2_E_STATE = -6
+RLT2_E_INTERNAL = -7
+RLT2_MIN_N = 3
+RLT2_MAX_N = 64
+RLT2_LAP_MAX_ENTRY = 536870911
+
+
+class Rlt2Error(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, rlt2_strerror(code), code))
+
+
+class rlt2_opts(C.Structure):
+    _fields_ = [("rlt1_only", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
+                ("max_iters", C.c_int), ("ub", C.c_double), ("min_progress", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+_lib = None
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+_dblp = C.POINTER(C.c_double)
+_intp = C.POINTER(C.c_int)
+_vp = C.c_void_p
+
+
+def lib():
+    """Load librlt2.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("librlt2.so is not built (%s); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    sig = {
+        "rlt2_default_opts": (None, [C.POINTER(rlt2_opts)]),
+        "rlt2_strerror": (C.c_char_p, [C.c_int]),
+        "rlt2_create": (C.c_int, [_i32p, _i32p, C.c_int, _i32p, C.c_int64,
+                                  C.POINTER(rlt2_opts), C.POINTER(_vp)]),
+        "rlt2_destroy": (None, [_vp]),
+        "rlt2_iterate": (C.c_int, [_vp, C.c_int]),
+        "rlt2_bound": (C.c_int, [_vp, _dblp, _i64p, _intp]),
+        "rlt2_bound_history": (C.c_int, [_vp, _i64p, C.c_int, _intp]),
+        "rlt2_get_state": (C.c_int, [_vp, C.c_int, _i32p, C.c_size_t]),
+        "rlt2_work": (C.c_int, [_vp, _i64p]),
+        "rlt2_stage_times": (C.c_int, [_vp, _dblp, _intp]),
+        "rlt2_reset_stage_times": (C.c_int, [_vp]),
+        "rlt2_device_state": (_vp, [_vp, C.c_int]),
+        "rlt2_row_stride": (C.c_int, [C.c_int]),
+        "rlt2_lap_batch": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_symbols():
+    """Names of the functions include/rlt2.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rlt2_[a-z0-9_]+)\s*\(", text)))
+
+
+def _chk(rc, where):
+    if rc != RLT2_OK:
+        raise Rlt2Error(rc, where)
+
+
+def _p32(a):
+    return a.ctypes.data_as(_i32p)
+
+
+def _p64(a):
+    return a.ctypes.data_as(_i64p)
+
+
+# ---------------------------------------------------------------- C names
+
+def rlt2_strerror(code: int) -> str:
+    return lib().rlt2_strerror(int(code)).decode()
+
+
+def rlt2_default_opts() -> rlt2_opts:
+    o = rlt2_opts()
+    lib().rlt2_default_opts(C.byref(o))
+    return o
+
+
+def rlt2_create(F, D, N=None, B_lin=None, lb_const=0, opts=None):
+    """Returns a context handle (int).  F, D (and B_lin): host N x N int32."""
+    F = np.ascontiguousarray(F, np.int32)
+    D = np.ascontiguousarray(D, np.int32)
+    N = F.shape[0] if N is None else int(N)
+    bl = None
+    if B_lin is not None:
+        B_lin = np.ascontiguousarray(B_lin, np.int32)
+        bl = _p32(B_lin)
+    ctx = _vp()
+    rc = lib().rlt2_create(_p32(F), _p32(D), N, bl, int(lb_const),
+                           C.byref(opts) if opts is not None else None, C.byref(ctx))
+    _chk(rc, "rlt2_create")
+    return ctx.value
+
+
+def rlt2_destroy(ctx):
+    lib().rlt2_destroy(_vp(ctx))
+
+
+def rlt2_iterate(ctx, k: int):
+    _chk(lib().rlt2_iterate(_vp(ctx), int(k)), "rlt2_iterate")
+
+
+def rlt2_bound(ctx):
+    """-> (LB as float, LB as exact int, passes completed)"""
+    lb = C.c_double()
+    ex = C.c_int64()
+    it = C.c_int()
+    _chk(lib().rlt2_bound(_vp(ctx), C.byref(lb), C.byref(ex), C.byref(it)), "rlt2_bound")
+    return lb.value, ex.value, it.value
+
+
+def rlt2_bound_history(ctx, cap: int):
+    out = np.zeros(max(cap, 0), np.int64)
+    cnt = C.c_int()
+    _chk(lib().rlt2_bound_history(_vp(ctx), _p64(out), int(cap), C.byref(cnt)), "rlt2_bound_history")
+    return out[:cnt.value]
+
+
+def rlt2_get_state(ctx, level: int, N: int):
+    counts = {0: N * N, 1: N * N * (N - 1) ** 2, 2: N * N * (N - 1) ** 2 * (N - 2) ** 2}
+    out = np.empty(counts[level], np.int32)
+    _chk(lib().rlt2_get_state(_vp(ctx), int(level), _p32(out), out.size), "rlt2_get_state")
+    return out
+
+
+def rlt2_work(ctx):
+    out = np.zeros(4, np.int64)
+    _chk(lib().rlt2_work(_vp(ctx), _p64(out)), "rlt2_work")
+    return dict(laps=int(out[0]), steps=int(out[1]), relaxations=int(out[2]), d_steps=int(out[3]))
+
+
+def rlt2_stage_times(ctx):
+    out = (C.c_double * 4)()
+    n = C.c_int()
+    _chk(lib().rlt2_stage_times(_vp(ctx), out, C.byref(n)), "rlt2_stage_times")
+    return list(out), n.value
+
+
+def rlt2_reset_stage_times(ctx):
+    _chk(lib().rlt2_reset_stage_times(_vp(ctx)), "rlt2_reset_stage_times")
+
+
+def rlt2_device_state(ctx, which: int) -> int:
+    return lib().rlt2_device_state(_vp(ctx), int(which)) or 0
+
+
+def rlt2_row_stride(N: int) -> int:
+    return lib().rlt2_row_stride(int(N))
+
+
+def rlt2_lap_batch(M_ptr, n, count, S_ptr, assign_ptr=0, u_ptr=0, v_ptr=0, work_ptr=0, stream=0):
+    """Device addresses in, device addresses out (see rlt2.h).  Returns the C code."""
+    return lib().rlt2_lap_batch(_vp(M_ptr or None), int(n), int(count), _vp(S_ptr or None),
+                                _vp(assign_ptr or None), _vp(u_ptr or None), _vp(v_ptr or None),
+                                _vp(work_ptr or None), _vp(stream or None))
+
+
+# ------------------------------------------------------------ convenience
+
+class Context:
+    """Owning wrapper of an rlt2_ctx (same calls, released on close/exit)."""
+
+    def __init__(self, F, D, B_lin=None, lb_const=0, rlt1_only=False, use_graph=True,
+                 profile=False, max_iters=65536, ub=0.0, min_progress=0.0, stream=0):
+        o = rlt2_default_opts()
+        o.rlt1_only = int(rlt1_only)
+        o.use_graph = int(use_graph)
+        o.profile = int(profile)
+        o.max_iters = int(max_iters)
+        o.ub = float(ub)
+        o.min_progress = float(min_progress)
+        o.stream = stream or None
+        self.N = int(np.asarray(F).shape[0])
+        self.ctx = rlt2_create(F, D, self.N, B_lin, lb_const, o)
+
+    def iterate(self, k=1):
+        rlt2_iterate(self.ctx, k)
+
+    def bound(self):
+        return rlt2_bound(self.ctx)
+
+    def history(self, cap=None):
+        return rlt2_bound_history(self.ctx, cap if cap is not None else 65536)
+
+    def state(self, level):
+        return rlt2_get_state(self.ctx, level, self.N)
+
+    def work(self):
+        return rlt2_work(self.ctx)
+
+    def stage_times(self):
+        return rlt2_stage_times(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            rlt2_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

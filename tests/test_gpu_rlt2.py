@@ -1,0 +1,235 @@
+"""Parity of the CUDA dual ascent (rlt2_create / rlt2_iterate) with the oracle.
+
+* full state (B, C, D in the compact layouts) and LB after every pass, bit for
+  bit, on the 8- and 12-facility workloads and on small ragged cases (N = 3..7,
+  asymmetric costs, linear terms, constants);
+* the 20-facility workload: two passes against the live oracle, then all 200
+  passes against the stored LB history and state hashes written by
+  tests/golden/make_golden.py (oracle only);
+* RLT1 mode (no D) up to N = 40, which exercises two column slots per lane in
+  the C -> B and B -> LB kernels;
+* the stopping rule of Algorithm 1;
+* the 30-facility headline workload in the launch configuration the benchmark
+  times: the first pass against the oracle, later passes through properties
+  that hold at any size (conservation on sampled permutations, non-negative
+  reduced costs, monotone LB).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1510_02065_gb300 import instances as I
+from paper_1510_02065_gb300 import rlt2
+from tests.layout import compact_y, compact_z, state_hash
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_02065_gb300 import build
+    build.build()
+    rlt2.lib()
+    return t
+
+
+def assert_same_state(ctx, st, where=""):
+    N = st.N
+    x, y = ctx.state(0), ctx.state(1)
+    assert (x == st.b.reshape(-1)).all(), "B differs " + where
+    assert (y == compact_y(st.c)).all(), "C differs " + where
+    if st.d is not None:
+        z = ctx.state(2).reshape(-1, N - 2, N - 2)
+        zo = compact_z(st.d)
+        bad = np.nonzero(z != zo)
+        assert bad[0].size == 0, "D differs %s at %d entries, first tile %s" % (
+            where, bad[0].size, bad[0][:3])
+    assert ctx.bound()[1] == st.LB, where
+
+
+@pytest.mark.parametrize("name", ["uniform_n8", "grid_n12"])
+def test_full_state_every_pass(gpu, orc, name):
+    F, D, iters = I.instance(name)
+    st = orc.State(F, D)
+    with rlt2.Context(F, D) as ctx:
+        assert_same_state(ctx, st, "at init")
+        for t in range(iters):
+            ctx.iterate(1)
+            st.iterate()
+            assert_same_state(ctx, st, "after pass %d" % (t + 1))
+        gold = json.load(open(os.path.join(GOLDEN, "lb_%s.json" % name)))
+        assert list(ctx.history()) == gold["lb"]
+        w = ctx.work()
+        ow = st.work()
+        assert (w["laps"], w["steps"], w["relaxations"]) == (ow["laps"], ow["steps"], ow["relaxations"])
+
+
+@pytest.mark.parametrize("N,seed", [(3, 0), (4, 1), (5, 2), (6, 3), (7, 4)])
+def test_small_ragged_asymmetric_with_linear_term(gpu, orc, N, seed):
+    rng = np.random.default_rng(seed)
+    F = rng.integers(0, 12, size=(N, N)).astype(np.int32)
+    D = rng.integers(0, 12, size=(N, N)).astype(np.int32)
+    Bl = rng.integers(0, 40, size=(N, N)).astype(np.int32)
+    st = orc.State(F, D, B_lin=Bl, lb_const=123)
+    with rlt2.Context(F, D, B_lin=Bl, lb_const=123, use_graph=(seed % 2 == 0)) as ctx:
+        assert_same_state(ctx, st, "at init")
+        for t in range(8):
+            ctx.iterate(1)
+            st.iterate()
+            assert_same_state(ctx, st, "after pass %d" % (t + 1))
+
+
+def test_subproblem_node(gpu, orc):
+    F, D = I.clustered_euclid(14, seed=5)
+    fac = np.array([3, 9, 0], np.int32)
+    loc = np.array([7, 1, 12], np.int32)
+    Fp, Dp, Bl, cst = orc.subproblem(F, D, fac, loc)
+    st = orc.State(Fp, Dp, B_lin=Bl, lb_const=cst)
+    with rlt2.Context(Fp, Dp, B_lin=Bl.astype(np.int32), lb_const=cst) as ctx:
+        ctx.iterate(6)
+        ref = st.run(6)
+        assert list(ctx.history()) == list(ref)
+        assert_same_state(ctx, st, "after 6 passes")
+
+
+def test_graph_nograph_profile_agree(gpu, orc):
+    F, D = I.uniform_symmetric(9, seed=7)
+    hs = []
+    for kw in (dict(use_graph=True), dict(use_graph=False), dict(profile=True)):
+        with rlt2.Context(F, D, **kw) as ctx:
+            ctx.iterate(5)
+            hs.append(list(ctx.history()))
+            if kw.get("profile"):
+                ms, passes = ctx.stage_times()
+                assert passes == 5 and all(m >= 0 for m in ms) and ms[1] > 0
+    assert hs[0] == hs[1] == hs[2] == list(orc.State(F, D).run(5))
+
+
+def test_clustered_n20_against_oracle_and_golden(gpu, orc):
+    F, D, iters = I.instance("clustered_n20")
+    gold = json.load(open(os.path.join(GOLDEN, "lb_clustered_n20.json")))
+    st = orc.State(F, D)
+    with rlt2.Context(F, D) as ctx:
+        for t in range(2):
+            ctx.iterate(1)
+            st.iterate()
+            assert_same_state(ctx, st, "after pass %d" % (t + 1))
+        done = 2
+        for t in sorted(int(k) for k in gold["hash"]):
+            if t <= done:
+                continue
+            ctx.iterate(t - done)
+            done = t
+            h = gold["hash"][str(t)]
+            N = 20
+            assert state_hash(ctx.state(0)) == h["x"], "B hash after pass %d" % t
+            assert state_hash(ctx.state(1)) == h["y"], "C hash after pass %d" % t
+            assert state_hash(ctx.state(2).reshape(-1, N - 2, N - 2)) == h["z"], "D hash after %d" % t
+        assert done == iters
+        assert list(ctx.history()) == gold["lb"]
+
+
+@pytest.mark.parametrize("N", [12, 20, 33, 34, 40])
+def test_rlt1_mode(gpu, orc, N):
+    F, D = I.clustered_euclid(N, seed=N)
+    st = orc.State(F, D, rlt1_only=True)
+    with rlt2.Context(F, D, rlt1_only=True) as ctx:
+        for t in range(4):
+            ctx.iterate(1)
+            st.iterate()
+            x, y = ctx.state(0), ctx.state(1)
+            assert (x == st.b.reshape(-1)).all()
+            assert (y == compact_y(st.c)).all()
+            assert ctx.bound()[1] == st.LB
+
+
+def test_stopping_rule(gpu, orc):
+    F, D, _ = I.instance("uniform_n8")
+    ref = orc.State(F, D).run(50)
+    # UB reached: stop right after the pass whose LB attains it
+    with rlt2.Context(F, D, ub=float(ref[2])) as ctx:
+        ctx.iterate(20)
+        lb, ex, it = ctx.bound()
+        assert it == 3 and ex == ref[2]
+    # progress below K (LB' / UB < K)
+    ub = 690.0
+    K = 0.005
+    inc = np.diff(np.concatenate([[0], ref]))
+    first = int(np.nonzero(inc / ub < K)[0][0])
+    with rlt2.Context(F, D, ub=ub, min_progress=K) as ctx:
+        ctx.iterate(40)
+        lb, ex, it = ctx.bound()
+        assert it == first + 1 and ex == ref[first]
+
+
+def _conservation_sample(F, D, N, LB, x, y, z, perms):
+    """max |Q(pi) - (LB + reduced costs along pi)| over the sampled permutations."""
+    m, n = N - 1, N - 2
+    F64, D64 = F.astype(np.int64), D.astype(np.int64)
+    idx = np.arange(N)
+    worst = 0
+    I3, K3, P3 = np.meshgrid(idx, idx, idx, indexing="ij")
+    ok = (I3 != K3) & (I3 != P3) & (K3 != P3)
+    I3, K3, P3 = I3[ok], K3[ok], P3[ok]
+    I2, K2 = np.meshgrid(idx, idx, indexing="ij")
+    o2 = I2 != K2
+    I2, K2 = I2[o2], K2[o2]
+    for pi in perms:
+        Q = int((F64 * D64[np.ix_(pi, pi)]).sum() - (np.diag(F64) * np.diag(D64)[pi]).sum())
+        tot = int(LB) + int(x.reshape(N, N)[idx, pi].sum())
+        J2, N2 = pi[I2], pi[K2]
+        t2 = ((I2 * N + J2) * m + (K2 - (K2 > I2))) * m + (N2 - (N2 > J2))
+        tot += int(y[t2].astype(np.int64).sum())
+        J, Nn, Q3 = pi[I3], pi[K3], pi[P3]
+        t = ((I3 * N + J) * m + (K3 - (K3 > I3))) * m + (Nn - (Nn > J))
+        r = P3 - (P3 > I3) - (P3 > K3)
+        s = Q3 - (Q3 > J) - (Q3 > Nn)
+        tot += int(z[(t * n + r) * n + s].astype(np.int64).sum())
+        worst = max(worst, abs(Q - tot))
+    return worst
+
+
+@pytest.mark.slow
+def test_headline_n30(gpu, orc):
+    F, D, _ = I.instance("clustered_n30")
+    N = 30
+    rng = np.random.default_rng(30)
+    perms = [rng.permutation(N) for _ in range(100)]
+    st = orc.State(F, D)
+    with rlt2.Context(F, D) as ctx:
+        ctx.iterate(1)
+        st.iterate()
+        # first pass against the oracle: LB, all of B and C, 10^6 sampled D entries
+        assert ctx.bound()[1] == st.LB
+        assert (ctx.state(0) == st.b.reshape(-1)).all()
+        assert (ctx.state(1) == compact_y(st.c)).all()
+        z = ctx.state(2)
+        i, j, k, n = [a.astype(np.int64) for a in __import__("tests.layout", fromlist=["x"]).tile_indices(N)]
+        sel = rng.integers(0, len(i), size=200000)
+        rr = rng.integers(0, N - 2, size=sel.size)
+        ss = rng.integers(0, N - 2, size=sel.size)
+        lo, hi = np.minimum(i[sel], k[sel]), np.maximum(i[sel], k[sel])
+        p = rr + (rr >= lo)
+        p = p + (p >= hi)
+        lo, hi = np.minimum(j[sel], n[sel]), np.maximum(j[sel], n[sel])
+        q = ss + (ss >= lo)
+        q = q + (q >= hi)
+        ref = st.d[i[sel], j[sel], k[sel], n[sel], p, q]
+        got = z[(sel * (N - 2) + rr) * (N - 2) + ss]
+        assert (got == ref).all()
+        st.close()
+        # later passes: properties that hold at any size
+        hist = [ctx.bound()[1]]
+        for t in range(3):
+            ctx.iterate(1)
+            hist.append(ctx.bound()[1])
+        x, y, z = ctx.state(0), ctx.state(1), ctx.state(2)
+        assert x.min() >= 0 and y.min() >= 0 and z.min() >= 0
+        assert all(a <= b for a, b in zip(hist, hist[1:]))
+        assert _conservation_sample(F, D, N, hist[-1], x, y, z, perms) == 0
