@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the RLT2 dual ascent on GB300: passes (iterations) per second.
+
+One step = one pass of the loop of Algorithm 1 (fused spread/complementary pass
+over D, N^2 (N-1)^2 D->C Hungarian LAPs, complementary C + C->B, B->LB) on the
+30-facility clustered workload (the paper's QAPLIB shapes stand-in; synthetic
+data).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank bounds its own replica of
+the workload (independent instances, no collective on the data path): weak
+scaling; the reported value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RLT2 dual-ascent iters/sec at N=30"
+OPS_PER_RELAXATION = 9   # textbook int ops of one relaxation
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clustered_n30")
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of oracle work for the cpu_baseline sample (0: skip)")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------- CPU oracle
+
+def oracle_sample(F, D, budget_s, steps=None):
+    """Time the CPU oracle (single thread) on a bounded sample of one pass.
+
+    The fused spread/complementary operations and the C/B concentrations are
+    timed in full; the D->C concentration (the bulk of a pass) is timed on
+    facility slices i (the tiles D_ijkn with that first facility), each on the
+    true pass-1 input (the slice is restored after timing), and extrapolated
+    to all N slices.  With `steps`, returns one extrapolated pass time per step
+    (one slice each) instead.
+    """
+    from oracle import oracle as O
+    N = F.shape[0]
+    st = O.State(F, D)
+    t0 = time.perf_counter()
+    st.spread_B_to_C()
+    st.spread_C_to_D()
+    st.complementary_D()
+    t_sc = time.perf_counter() - t0
+    d, c = st.d, st.c
+    slice_times = []
+    per_step = []
+    k = 0
+    tb = time.perf_counter()
+    while True:
+        i = k % N
+        dsave, csave = d[i].copy(), c[i].copy()
+        t1 = time.perf_counter()
+        st.concentrate_D_to_C_range(i, i + 1)
+        dt = time.perf_counter() - t1
+        d[i] = dsave
+        c[i] = csave
+        slice_times.append(dt)
+        per_step.append(dt)
+        k += 1
+        if steps is not None:
+            if k >= steps:
+                break
+        elif time.perf_counter() - tb >= budget_s and k >= 2:
+            break
+    # the C/B operations of the pass on the true state after D->C is not
+    # available without the full concentration; time them on the current state
+    t2 = time.perf_counter()
+    st.complementary_C()
+    st.concentrate_C_to_B()
+    st.add_LB(st.concentrate_B_to_LB())
+    t_cb = time.perf_counter() - t2
+    st.close()
+    rest = t_sc + t_cb
+    if steps is not None:
+        return [N * s + rest for s in per_step], rest
+    t_pass = N * float(np.mean(slice_times)) + rest
+    return t_pass, len(slice_times), rest
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle as it stands, one sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1510_02065_gb300 import instances
+    F, D, _ = instances.instance(args.workload)
+    N = F.shape[0]
+    t0 = time.perf_counter()
+    times, rest = oracle_sample(F, D, 0, steps=args.warmup + args.steps)
+    wall = time.perf_counter() - t0
+    timed = times[args.warmup:]
+    t_pass = float(np.mean(timed))
+    value = 1.0 / t_pass
+    sample = ("each step: D->C concentration of one facility slice (N*(N-1)^2 = %d LAPs of size %d, "
+              "true pass-1 input) x N slices, plus the pass's spread, complementary and C/B "
+              "operations timed once (%.1f s); single thread" % (N * (N - 1) ** 2, N - 2, rest))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * t_pass, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "seed": 0},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1510_02065_gb300 import build, instances, rlt2
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if not os.path.exists(rlt2.LIB_PATH):
+        build.build()
+    rlt2.lib()
+
+    F, D, _ = instances.instance(args.workload)
+    N = F.shape[0]
+    K, W = args.steps, args.warmup
+    stream = torch.cuda.current_stream()
+    peaks, peaks_kind = load_peaks()
+    props = torch.cuda.get_device_properties(local)
+
+    ctx = rlt2.Context(F, D, profile=True, use_graph=True, max_iters=K + W + 16,
+                       stream=stream.cuda_stream)
+    ctx.iterate(W)
+    torch.cuda.synchronize()
+    rlt2.rlt2_reset_stage_times(ctx.ctx)
+    w0 = ctx.work()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.iterate(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stage_ms, passes = ctx.stage_times()
+    w1 = ctx.work()
+    lb, lb_exact, iters = ctx.bound()
+    ctx.close()
+
+    ms_per_step = ms / K
+    value = world * K / (ms / 1000.0)
+    laps_per_pass = (w1["laps"] - w0["laps"]) / K
+    d_relax = (w1["d_relaxations"] - w0["d_relaxations"]) / K
+    d_steps = (w1["d_steps"] - w0["d_steps"]) / K
+    d_laps = (w1["d_laps"] - w0["d_laps"]) / K
+    t_p1 = stage_ms[0] / passes
+    t_dlap = stage_ms[1] / passes
+    t_clap = stage_ms[2] / passes
+    t_xlap = stage_ms[3] / passes
+
+    # roofline of the dominant kernel (D -> C concentration): integer ALU bound
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12   # Tops/s int32
+    achieved = OPS_PER_RELAXATION * d_relax / (t_dlap / 1e3) / 1e12
+    n_tiles = N * N * (N - 1) ** 2
+    m = N - 2
+    z_bytes = n_tiles * m * m * 4
+    dlap_hbm_gbs = 2 * z_bytes / (t_dlap / 1e3) / 1e9
+    p1_bytes = 2 * z_bytes + n_tiles * 4 + N * N * 4
+    p1_gbs = p1_bytes / (t_p1 / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "dlap_traffic.json")
+    if os.path.exists(prof):
+        try:
+            info = json.load(open(prof))
+            if info.get("workload") == args.workload and info.get("kernel_rev") == "v1":
+                traffic = info.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "seed": 0, "tiles": n_tiles,
+                   "laps_per_iter": int(round(laps_per_pass)), "z_bytes": z_bytes,
+                   "l2": "inputs larger than L2 (D store %.2f GB)" % (z_bytes / 1e9),
+                   "parallelism": "replicas x%d" % world if world > 1 else "1 GPU"},
+        "laps_per_s": world * laps_per_pass * K / (ms / 1000.0),
+        "bound": {"LB": lb_exact, "iterations": iters},
+        "stages_ms": {"spread_complementary_D": t_p1, "concentrate_D_to_C": t_dlap,
+                      "complementary_C_concentrate_C_to_B": t_clap, "concentrate_B_to_LB": t_xlap},
+        "roofline": {"bound": "alu", "kernel": "dlap_kernel (concentration D->C)",
+                     "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                     "frac": achieved / alu_peak, "traffic": traffic,
+                     "peak_kind": "%d SMs x 128 int32 lanes x %.0f MHz (%s sm_max)" % (
+                         props.multi_processor_count, sm_max, peaks_kind),
+                     "work": {"laps": d_laps, "steps": d_steps, "relaxations": d_relax,
+                              "ops_per_relaxation": OPS_PER_RELAXATION},
+                     "hbm_gbs": dlap_hbm_gbs},
+        "p1_roofline": {"bound": "hbm", "kernel": "p1_kernel (spread + complementary D)",
+                        "achieved": p1_gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                        "frac": p1_gbs / float(peaks["hbm_gbs"]), "bytes_per_launch": p1_bytes,
+                        "peak_kind": peaks_kind},
+        "gpu_launches": 4 * K,
+        "clocks": clk,
+    }
+
+    # end to end through the public API with host buffers: create (H2D of F, D
+    # from pinned memory), then every step one pass and a D2H read of the bound
+    if not args.no_e2e:
+        Fp = torch.from_numpy(F).pin_memory().numpy()
+        Dp = torch.from_numpy(D).pin_memory().numpy()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = rlt2.Context(Fp, Dp, max_iters=K + 4, stream=stream.cuda_stream)
+        for _ in range(K):
+            c2.iterate(1)
+            c2.bound()
+        c2.close()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        line["e2e"] = {"value": world * K / e2e_s, "unit": "iters/s",
+                       "h2d_bytes_per_step": 2 * N * N * 4 / K, "d2h_bytes_per_step": 12,
+                       "includes": "rlt2_create (alloc, H2D, init) + per step rlt2_iterate(1) + "
+                                   "rlt2_bound + rlt2_destroy"}
+
+    if rank == 0 and world == 1 and args.cpu_budget > 0:
+        t_pass, nslices, rest = oracle_sample(F, D, args.cpu_budget)
+        line["cpu_baseline"] = {
+            "value": 1.0 / t_pass, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": "pass 1: spread/complementary and C/B operations in full (%.1f s), D->C "
+                      "concentration on %d facility slices of %d LAPs each, extrapolated to %d "
+                      "slices; single-threaded C oracle" % (rest, nslices, N * (N - 1) ** 2, N)}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -69,7 +69,8 @@ typedef struct {
     int max_iters;        /* capacity of the on-device LB history; default 65536 */
     double ub;            /* UB of Algorithm 1 (stop once LB >= UB); <= 0: none  */
     double min_progress;  /* K of Algorithm 1: stop once LB'/UB < K; 0: never     */
-    void *stream;         /* cudaStream_t to run on; NULL = the legacy default stream */
+    void *stream;         /* cudaStream_t to run on; NULL = a non-blocking stream
+                             created for (and owned by) the context              */
 } rlt2_opts;
 
 typedef struct rlt2_ctx rlt2_ctx;
@@ -138,13 +139,14 @@ int rlt2_get_state(rlt2_ctx *ctx, int level, int32_t *host_buf, size_t count);
 /*
  * Cumulative work of the Hungarian method in this context (synchronises):
  * out[0] LAPs solved, out[1] steps (columns labelled), out[2] relaxations
- * (reduced distances evaluated for unlabelled columns), out[3] steps of the
- * D->C concentrations alone.
+ * (reduced distances evaluated for unlabelled columns), out[3..5] the same
+ * three counts for the D->C concentrations alone.
  */
-int rlt2_work(rlt2_ctx *ctx, int64_t out[4]);
+int rlt2_work(rlt2_ctx *ctx, int64_t out[6]);
 
 /*
- * Stage times recorded while opts.profile was set (synchronises): out[s] =
+ * Stage times recorded while opts.profile was set (synchronises; with
+ * use_graph the captured pass carries the event records): out[s] =
  * total milliseconds of stage s over all profiled passes, s = 0 fused
  * spread/complementary pass over D, 1 concentration D->C, 2 complementary C +
  * concentration C->B, 3 concentration B->LB; *passes = passes recorded.

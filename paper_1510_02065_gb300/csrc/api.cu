@@ -31,9 +31,12 @@ struct rlt2_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int enqueued = 0;
-    // profiling: 5 events per pass
+    // profiling: 5 events per pass; in graph mode the captured pass holds 5
+    // event-record nodes that are pointed at the next 5 events before each launch
     std::vector<cudaEvent_t> events;
     size_t ev_used = 0;
+    cudaEvent_t tmpl[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraphNode_t evnode[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 static int cuda_code(cudaError_t e)
@@ -83,6 +86,8 @@ static void free_ctx(rlt2_ctx *c)
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->tmpl)
+        if (e) cudaEventDestroy(e);
     cudaFree(c->z);
     cudaFree(c->yS);
     cudaFree(c->yC);
@@ -230,30 +235,54 @@ static cudaError_t enqueue_pass(rlt2_ctx *c, cudaEvent_t *ev)
     const Geom &g = c->g;
     const PassState &p = c->ps;
     cudaError_t e;
-    if (ev) cudaEventRecord(ev[0], c->stream);
+    auto mark = [&](int s) {
+        return ev ? cudaEventRecordWithFlags(ev[s], c->stream, cudaEventRecordExternal) : cudaSuccess;
+    };
+    if ((e = mark(0)) != cudaSuccess) return e;
     if (!c->opts.rlt1_only) {
         if ((e = launch_p1(g, p, c->triples, c->ntriples, c->stream)) != cudaSuccess) return e;
-        if (ev) cudaEventRecord(ev[1], c->stream);
+        if ((e = mark(1)) != cudaSuccess) return e;
         if ((e = launch_dlap(g, p, c->sm_count, c->stream)) != cudaSuccess) return e;
-    } else if (ev) {
-        cudaEventRecord(ev[1], c->stream);
+    } else if ((e = mark(1)) != cudaSuccess) {
+        return e;
     }
-    if (ev) cudaEventRecord(ev[2], c->stream);
+    if ((e = mark(2)) != cudaSuccess) return e;
     if ((e = launch_clap(g, p, c->stream)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[3], c->stream);
+    if ((e = mark(3)) != cudaSuccess) return e;
     if ((e = launch_xlap(g, p, c->stream)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[4], c->stream);
-    return cudaSuccess;
+    return mark(4);
 }
 
 static cudaError_t build_graph(rlt2_ctx *c)
 {
-    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    const bool prof = c->opts.profile != 0;
+    cudaError_t e;
+    if (prof)
+        for (auto &t : c->tmpl)
+            if (!t && (e = cudaEventCreate(&t)) != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaError_t e2 = enqueue_pass(c, nullptr);
+    cudaError_t e2 = enqueue_pass(c, prof ? c->tmpl : nullptr);
     e = cudaStreamEndCapture(c->stream, &c->graph);
     if (e2 != cudaSuccess) return e2;
     if (e != cudaSuccess) return e;
+    if (prof) {
+        size_t nn = 0;
+        if ((e = cudaGraphGetNodes(c->graph, nullptr, &nn)) != cudaSuccess) return e;
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if ((e = cudaGraphGetNodes(c->graph, nodes.data(), &nn)) != cudaSuccess) return e;
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            if ((e = cudaGraphNodeGetType(nd, &ty)) != cudaSuccess) return e;
+            if (ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            if ((e = cudaGraphEventRecordNodeGetEvent(nd, &ev)) != cudaSuccess) return e;
+            for (int s = 0; s < 5; s++)
+                if (ev == c->tmpl[s]) c->evnode[s] = nd;
+        }
+        for (int s = 0; s < 5; s++)
+            if (!c->evnode[s]) return cudaErrorInvalidValue;
+    }
     return cudaGraphInstantiate(&c->gexec, c->graph, 0);
 }
 
@@ -262,19 +291,24 @@ int rlt2_iterate(rlt2_ctx *c, int k)
     if (!c || k < 0) return RLT2_E_INVAL;
     if ((long long)c->enqueued + k > c->opts.max_iters) return RLT2_E_STATE;
     for (int t = 0; t < k; t++) {
+        cudaEvent_t *ev = nullptr;
         if (c->opts.profile) {
             while (c->events.size() < c->ev_used + 5) {
-                cudaEvent_t ev;
-                CK(cudaEventCreate(&ev));
-                c->events.push_back(ev);
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                c->events.push_back(e);
             }
-            CK(enqueue_pass(c, &c->events[c->ev_used]));
+            ev = &c->events[c->ev_used];
             c->ev_used += 5;
-        } else if (c->opts.use_graph) {
+        }
+        if (c->opts.use_graph) {
             if (!c->gexec) CK(build_graph(c));
+            if (ev)
+                for (int s = 0; s < 5; s++)
+                    CK(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->evnode[s], ev[s]));
             CK(cudaGraphLaunch(c->gexec, c->stream));
         } else {
-            CK(enqueue_pass(c, nullptr));
+            CK(enqueue_pass(c, ev));
         }
         c->enqueued++;
     }
@@ -339,7 +373,7 @@ int rlt2_get_state(rlt2_ctx *c, int level, int32_t *host, size_t count)
     return RLT2_OK;
 }
 
-int rlt2_work(rlt2_ctx *c, int64_t out[4])
+int rlt2_work(rlt2_ctx *c, int64_t out[6])
 {
     if (!c || !out) return RLT2_E_INVAL;
     DevStatus s;
@@ -348,7 +382,9 @@ int rlt2_work(rlt2_ctx *c, int64_t out[4])
     out[0] = (int64_t)s.laps;
     out[1] = (int64_t)s.steps;
     out[2] = (int64_t)s.relax;
-    out[3] = (int64_t)s.dsteps;
+    out[3] = (int64_t)s.dlaps;
+    out[4] = (int64_t)s.dsteps;
+    out[5] = (int64_t)s.drelax;
     return RLT2_OK;
 }
 

@@ -28,7 +28,9 @@ struct DevStatus {
     unsigned long long laps;     // LAPs solved
     unsigned long long steps;    // columns labelled (all concentrations)
     unsigned long long relax;    // reduced distances evaluated
-    unsigned long long dsteps;   // steps of the D->C concentrations
+    unsigned long long dlaps;    // LAPs of the D->C concentrations
+    unsigned long long dsteps;   // their steps
+    unsigned long long drelax;   // their relaxations
 };
 
 // ---------------------------------------------------------------- PTX helpers

@@ -96,8 +96,10 @@ __global__ void __launch_bounds__(kDlapWarps * 32)
     if (lane == 0 && laps) {
         atomicAdd(&p.status->laps, (unsigned long long)laps);
         atomicAdd(&p.status->steps, (unsigned long long)steps);
-        atomicAdd(&p.status->dsteps, (unsigned long long)steps);
         atomicAdd(&p.status->relax, (unsigned long long)relax);
+        atomicAdd(&p.status->dlaps, (unsigned long long)laps);
+        atomicAdd(&p.status->dsteps, (unsigned long long)steps);
+        atomicAdd(&p.status->drelax, (unsigned long long)relax);
     }
 }
 
@@ -292,10 +294,9 @@ static cudaError_t dlap_go(const Geom &g, const PassState &p, int sm_count, cuda
     return cudaGetLastError();
 }
 
+// The work counter is reset by the fused pass over D, which precedes this kernel.
 cudaError_t launch_dlap(const Geom &g, const PassState &p, int sm_count, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
     if (g.n <= 32) return p.pack ? dlap_go<1, true>(g, p, sm_count, s) : dlap_go<1, false>(g, p, sm_count, s);
     return p.pack ? dlap_go<2, true>(g, p, sm_count, s) : dlap_go<2, false>(g, p, sm_count, s);
 }

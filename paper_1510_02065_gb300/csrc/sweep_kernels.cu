@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(kP1Threads)
     p1_kernel(PassState p, int N, int RS, const int4 *__restrict__ triples, int nchunks)
 {
     if (*p.stop) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.counter = 0;  // work counter of the D -> C sweep
     extern __shared__ __align__(16) int sm[];
     const P1Layout L = p1_layout(N, JC);
     const int n = L.n, m = L.m;

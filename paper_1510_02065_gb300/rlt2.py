@@ -166,9 +166,10 @@ def rlt2_get_state(ctx, level: int, N: int):
 
 
 def rlt2_work(ctx):
-    out = np.zeros(4, np.int64)
+    out = np.zeros(6, np.int64)
     _chk(lib().rlt2_work(_vp(ctx), _p64(out)), "rlt2_work")
-    return dict(laps=int(out[0]), steps=int(out[1]), relaxations=int(out[2]), d_steps=int(out[3]))
+    return dict(laps=int(out[0]), steps=int(out[1]), relaxations=int(out[2]),
+                d_laps=int(out[3]), d_steps=int(out[4]), d_relaxations=int(out[5]))
 
 
 def rlt2_stage_times(ctx):

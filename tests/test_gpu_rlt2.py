@@ -101,14 +101,15 @@ def test_subproblem_node(gpu, orc):
 def test_graph_nograph_profile_agree(gpu, orc):
     F, D = I.uniform_symmetric(9, seed=7)
     hs = []
-    for kw in (dict(use_graph=True), dict(use_graph=False), dict(profile=True)):
+    for kw in (dict(use_graph=True), dict(use_graph=False), dict(profile=True),
+               dict(profile=True, use_graph=False)):
         with rlt2.Context(F, D, **kw) as ctx:
             ctx.iterate(5)
             hs.append(list(ctx.history()))
             if kw.get("profile"):
                 ms, passes = ctx.stage_times()
                 assert passes == 5 and all(m >= 0 for m in ms) and ms[1] > 0
-    assert hs[0] == hs[1] == hs[2] == list(orc.State(F, D).run(5))
+    assert hs[0] == hs[1] == hs[2] == hs[3] == list(orc.State(F, D).run(5))
 
 
 def test_clustered_n20_against_oracle_and_golden(gpu, orc):
