@@ -64,8 +64,9 @@ typedef struct {
     int rlt1_only;        /* 1: Algorithm 1 without the three operations on D
                              (the strong-branching dual of Sec. 6); default 0 */
     int use_graph;        /* 1 (default): each pass is one captured CUDA graph   */
-    int profile;          /* 1: record CUDA events around every stage of every
-                             pass (see rlt2_stage_times); default 0           */
+    int profile;          /* 1: launch every stage of every pass directly on the
+                             stream with CUDA events between the stages (no
+                             graph; see rlt2_stage_times); default 0          */
     int max_iters;        /* capacity of the on-device LB history; default 65536 */
     double ub;            /* UB of Algorithm 1 (stop once LB >= UB); <= 0: none  */
     double min_progress;  /* K of Algorithm 1: stop once LB'/UB < K; 0: never     */
@@ -145,8 +146,7 @@ int rlt2_get_state(rlt2_ctx *ctx, int level, int32_t *host_buf, size_t count);
 int rlt2_work(rlt2_ctx *ctx, int64_t out[6]);
 
 /*
- * Stage times recorded while opts.profile was set (synchronises; with
- * use_graph the captured pass carries the event records): out[s] =
+ * Stage times recorded while opts.profile was set (synchronises): out[s] =
  * total milliseconds of stage s over all profiled passes, s = 0 fused
  * spread/complementary pass over D, 1 concentration D->C, 2 complementary C +
  * concentration C->B, 3 concentration B->LB; *passes = passes recorded.

@@ -31,12 +31,9 @@ struct rlt2_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int enqueued = 0;
-    // profiling: 5 events per pass; in graph mode the captured pass holds 5
-    // event-record nodes that are pointed at the next 5 events before each launch
+    // profiling: 5 events per pass, recorded on the stream between the stages
     std::vector<cudaEvent_t> events;
     size_t ev_used = 0;
-    cudaEvent_t tmpl[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    cudaGraphNode_t evnode[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 static int cuda_code(cudaError_t e)
@@ -86,8 +83,6 @@ static void free_ctx(rlt2_ctx *c)
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
-    for (cudaEvent_t e : c->tmpl)
-        if (e) cudaEventDestroy(e);
     cudaFree(c->z);
     cudaFree(c->yS);
     cudaFree(c->yC);
@@ -235,9 +230,7 @@ static cudaError_t enqueue_pass(rlt2_ctx *c, cudaEvent_t *ev)
     const Geom &g = c->g;
     const PassState &p = c->ps;
     cudaError_t e;
-    auto mark = [&](int s) {
-        return ev ? cudaEventRecordWithFlags(ev[s], c->stream, cudaEventRecordExternal) : cudaSuccess;
-    };
+    auto mark = [&](int s) { return ev ? cudaEventRecord(ev[s], c->stream) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
     if (!c->opts.rlt1_only) {
         if ((e = launch_p1(g, p, c->triples, c->ntriples, c->stream)) != cudaSuccess) return e;
@@ -255,34 +248,12 @@ static cudaError_t enqueue_pass(rlt2_ctx *c, cudaEvent_t *ev)
 
 static cudaError_t build_graph(rlt2_ctx *c)
 {
-    const bool prof = c->opts.profile != 0;
-    cudaError_t e;
-    if (prof)
-        for (auto &t : c->tmpl)
-            if (!t && (e = cudaEventCreate(&t)) != cudaSuccess) return e;
-    e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaError_t e2 = enqueue_pass(c, prof ? c->tmpl : nullptr);
+    cudaError_t e2 = enqueue_pass(c, nullptr);
     e = cudaStreamEndCapture(c->stream, &c->graph);
     if (e2 != cudaSuccess) return e2;
     if (e != cudaSuccess) return e;
-    if (prof) {
-        size_t nn = 0;
-        if ((e = cudaGraphGetNodes(c->graph, nullptr, &nn)) != cudaSuccess) return e;
-        std::vector<cudaGraphNode_t> nodes(nn);
-        if ((e = cudaGraphGetNodes(c->graph, nodes.data(), &nn)) != cudaSuccess) return e;
-        for (cudaGraphNode_t nd : nodes) {
-            cudaGraphNodeType ty;
-            if ((e = cudaGraphNodeGetType(nd, &ty)) != cudaSuccess) return e;
-            if (ty != cudaGraphNodeTypeEventRecord) continue;
-            cudaEvent_t ev;
-            if ((e = cudaGraphEventRecordNodeGetEvent(nd, &ev)) != cudaSuccess) return e;
-            for (int s = 0; s < 5; s++)
-                if (ev == c->tmpl[s]) c->evnode[s] = nd;
-        }
-        for (int s = 0; s < 5; s++)
-            if (!c->evnode[s]) return cudaErrorInvalidValue;
-    }
     return cudaGraphInstantiate(&c->gexec, c->graph, 0);
 }
 
@@ -301,14 +272,11 @@ int rlt2_iterate(rlt2_ctx *c, int k)
             ev = &c->events[c->ev_used];
             c->ev_used += 5;
         }
-        if (c->opts.use_graph) {
+        if (c->opts.use_graph && !ev) {
             if (!c->gexec) CK(build_graph(c));
-            if (ev)
-                for (int s = 0; s < 5; s++)
-                    CK(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->evnode[s], ev[s]));
             CK(cudaGraphLaunch(c->gexec, c->stream));
         } else {
-            CK(enqueue_pass(c, ev));
+            CK(enqueue_pass(c, ev));   // profiling launches stage by stage
         }
         c->enqueued++;
     }
