@@ -210,7 +210,9 @@ def main():
     F, D, _ = instances.instance(args.workload)
     N = F.shape[0]
     K, W = args.steps, args.warmup
-    stream = torch.cuda.current_stream()
+    # a stream of our own: the library launches on it and the events time it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     peaks, peaks_kind = load_peaks()
     props = torch.cuda.get_device_properties(local)
 

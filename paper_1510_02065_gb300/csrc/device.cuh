@@ -71,6 +71,75 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, 
         : "memory");
 }
 
+// Arrive on bar (count 1 of its expected arrivals) announcing `bytes` of
+// asynchronous transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy (no arrive) of `bytes` global -> shared, completing on bar.
+__device__ __forceinline__ void bulk_load_tx(void *dst_smem, const void *src_gmem, unsigned bytes,
+                                             uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bulk copy shared -> global (bulk-group completion).
+__device__ __forceinline__ void bulk_store(void *dst_gmem, const void *src_smem, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_addr(src_smem)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until every committed bulk store has finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_all()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// 4-byte asynchronous copy global -> shared (cp.async), and its completion.
+__device__ __forceinline__ void cp_async4(void *dst_smem, const void *src_gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst_smem)), "l"(src_gmem)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Exact unsigned division of x < 2^31 by a runtime divisor d >= 1:
+// q = (umulhi(x, mul) + x) >> shift with shift = ceil(log2 d) and
+// mul = ceil(2^(32+shift) / d) - 2^32 (0 when d is a power of two).
+struct FastDiv {
+    unsigned mul, shift, d;
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    FastDiv f;
+    f.d = d;
+    unsigned l = 0;
+    while ((1ull << l) < d) l++;
+    f.shift = l;
+    f.mul = ((1ull << l) == d) ? 0u
+                               : (unsigned)((1ull << (32 + l)) / d + 1 - (1ull << 32));
+    return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned x, const FastDiv &f)
+{
+    return (__umulhi(x, f.mul) + x) >> f.shift;
+}
+
 // Wait for the phase of parity `parity` of bar to complete; false after
 // kSpinLimit unsuccessful polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
@@ -148,17 +217,20 @@ __device__ __forceinline__ long long warp_sum64(long long x)
 //
 // M: shared memory, row r at M + r * ld, columns 0..n-1 (n <= 32 * NS).
 //
-// Every loop is bounded: a phase labels at most r + 1 columns and an
-// augmenting path is at most that long.  If an invariant fails (it cannot in
-// exact arithmetic) the function stops and returns false instead of spinning.
+// Every loop is bounded: a phase ends at the latest when every column is
+// labelled, and an augmenting path is at most as long as the phase.  If an
+// invariant fails (it cannot in exact arithmetic) the function stops and
+// returns false instead of spinning.
 template <int NS, bool PACK>
 __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld, int n,
                                                int (&rowOf)[NS], int (&uM)[NS], int (&v)[NS],
                                                long long &steps_out, long long &relax_out)
 {
+    constexpr unsigned kDone = 0xffffffffu;  // key of a labelled (or absent) column
     const int lane = threadIdx.x & 31;
-    bool valid[NS], used[NS];
-    int dist[NS], way[NS], dlab[NS];
+    bool valid[NS];
+    int way[NS], dlab[NS];
+    unsigned key[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         valid[s] = lane + 32 * s < n;
@@ -171,80 +243,77 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
     long long steps = 0, relax = 0;
 
     for (int r = 0; r < n; ++r) {
+        // key = distance label (+ D of its last update), packed with the column
+        // when PACK; kDone marks labelled columns: as a signed value it is below
+        // every candidate, so no relaxation touches it, and as an unsigned value
+        // it is above every key, so no reduction picks it.
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            used[s] = !valid[s];
-            dist[s] = kInf;
-        }
-        int i0 = r;        // row scanned at this step
-        int j0 = -1;       // column through which i0 was reached (-1: the new row)
-        int c0 = 0;        // u(i0) - D before this step
-        int K = 0, jf = 0, Dend = 0;
+        for (int s = 0; s < NS; ++s) key[s] = valid[s] ? 0x7fffffffu : kDone;
+        int i0 = r;   // row scanned at this step
+        int j0 = -1;  // column through which i0 was reached (-1: the new row)
+        int c0 = 0;   // u(i0) - D before this step
+        unsigned mm;
+        int Dk, j1;
         for (;;) {
-            if (++K > r + 1) return false;
             const int *Mrow = M + i0 * ld + lane;
-            int key[NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                if (!used[s]) {
+                if (valid[s]) {
                     const int cand = Mrow[32 * s] - v[s] - c0;
-                    if (cand < dist[s]) {
-                        dist[s] = cand;
+                    const unsigned ck = PACK ? ((unsigned)cand << 6) | (unsigned)(lane + 32 * s)
+                                             : (unsigned)cand;
+                    if ((int)ck < (int)key[s]) {
+                        key[s] = ck;
                         way[s] = j0;
                     }
                 }
-                key[s] = used[s] ? kInf : dist[s];
             }
-            int Dk, j1;
+            unsigned lmin = key[0];
+            if constexpr (NS == 2) lmin = min(lmin, key[1]);
+            mm = __reduce_min_sync(kFull, lmin);
             if constexpr (PACK) {
-                int pk = used[0] ? kInf : (key[0] << 6) | lane;
-                if constexpr (NS == 2) {
-                    const int p1 = used[1] ? kInf : (key[1] << 6) | (lane + 32);
-                    pk = min(pk, p1);
-                }
-                const int m = __reduce_min_sync(kFull, pk);
-                Dk = m >> 6;
-                j1 = m & 63;
+                Dk = (int)(mm >> 6);
+                j1 = (int)(mm & 63u);
             } else {
-                int lmin = key[0];
-                if constexpr (NS == 2) lmin = min(lmin, key[1]);
-                Dk = __reduce_min_sync(kFull, lmin);
-                const unsigned b0 = __ballot_sync(kFull, key[0] == Dk);
+                Dk = (int)mm;
+                const unsigned b0 = __ballot_sync(kFull, key[0] == mm);
                 if constexpr (NS == 1) {
                     j1 = __ffs(b0) - 1;
                 } else {
-                    const unsigned b1 = __ballot_sync(kFull, key[1] == Dk);
+                    const unsigned b1 = __ballot_sync(kFull, key[1] == mm);
                     j1 = b0 ? __ffs(b0) - 1 : 31 + __ffs(b1);
                 }
             }
             const int src = j1 & 31, sl = j1 >> 5;
             const int rj = __shfl_sync(kFull, pick<NS>(rowOf, sl), src);
             const int uj = __shfl_sync(kFull, pick<NS>(uM, sl), src);
-            if (rj < 0) {  // free column: augmenting path found
-                jf = j1;
-                Dend = Dk;
-                break;
-            }
+            if (rj < 0 || mm == kDone) break;  // free column: augmenting path found
             if (lane == src) {
-                put<NS>(used, sl, true);
+                put<NS>(key, sl, kDone);
                 put<NS>(dlab, sl, Dk);
             }
             i0 = rj;
             j0 = j1;
             c0 = uj - Dk;
         }
-        steps += K;
-        relax += (long long)K * n - (long long)K * (K - 1) / 2;
+        if (mm == kDone) return false;  // every column labelled: cannot happen
+        const int jf = j1, Dend = Dk;
 
         // lazy potential updates of the columns labelled in this phase
+        int K = 1;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            if (used[s] && valid[s]) {
+            const bool lab = valid[s] && key[s] == kDone;
+            K += __popc(__ballot_sync(kFull, lab));
+            if (lab) {
                 const int dd = Dend - dlab[s];
                 v[s] -= dd;
                 uM[s] += dd;
             }
         }
+        steps += K;
+        relax += (long long)K * n - (long long)K * (K - 1) / 2;
+
         // augment: each column on the path takes the row of its predecessor
         int c = jf;
         for (int hop = 0;; ++hop) {

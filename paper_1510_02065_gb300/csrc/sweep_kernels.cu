@@ -25,6 +25,7 @@
 namespace rlt2 {
 
 constexpr int kP1Threads = 512;
+constexpr int kP1Warps = kP1Threads / 32;
 
 __device__ __forceinline__ int tidx_n(int N, int a, int b, int c, int d)
 {
@@ -32,11 +33,11 @@ __device__ __forceinline__ int tidx_n(int N, int a, int b, int c, int d)
     return ((a * N + b) * m + (c - (c > a))) * m + (d - (d > b));
 }
 
-// t-th of m shares of x (reading of Sec. 4.2 in integers)
-__device__ __forceinline__ int share(int x, int m, int t)
+// t-th of m shares of x >= 0 (reading of Sec. 4.2 in integers); fm divides by m
+__device__ __forceinline__ int share(int x, const FastDiv &fm, int t)
 {
-    const int q = x / m;
-    return q + (t < x - q * m ? 1 : 0);
+    const int q = (int)fdiv((unsigned)x, fm);
+    return q + (t < x - q * (int)fm.d ? 1 : 0);
 }
 
 // r-th element of [0, N) without a and b (a != b)
@@ -48,30 +49,33 @@ __device__ __forceinline__ int skip2(int r, int a, int b)
     return r;
 }
 
+// Shared-memory layout of one work unit (offsets in ints).  Full tile rows
+// (kinds 1, 3, 2, 5) keep the global row stride RS so that they move by bulk
+// copies; the JC-column pieces of kinds 4 and 6 use an odd row pitch.
 struct P1Layout {
-    int n, m, n2, JCp, P4;
-    int A1, A3, A2, A5, A4, A6, H1, H2, H3, H5, H4, H6, total;
+    int n, m, JCp, P4;
+    int BAR, A1, A3, A2, A5, A4, A6, H1, H3, H2, H5, H4, H6, total;
 };
 
-__host__ __device__ inline P1Layout p1_layout(int N, int JC)
+__host__ __device__ inline P1Layout p1_layout(int N, int JC, int RS)
 {
     P1Layout L;
     L.n = N - 2;
     L.m = N - 1;
-    L.n2 = L.n | 1;
     L.JCp = JC | 1;
     L.P4 = L.m * L.JCp;
     if (!(L.P4 & 1)) L.P4 += 1;
     int o = 0;
-    L.A1 = o; o += JC * L.m * L.n;
-    L.A3 = o; o += JC * L.m * L.n;
-    L.A2 = o; o += JC * L.m * L.n2;
-    L.A5 = o; o += JC * L.m * L.n2;
+    L.BAR = o; o += 4;  // one mbarrier, 16-byte slot
+    L.A1 = o; o += JC * L.m * RS;
+    L.A3 = o; o += JC * L.m * RS;
+    L.A2 = o; o += JC * L.m * RS;
+    L.A5 = o; o += JC * L.m * RS;
     L.A4 = o; o += N * L.P4;
     L.A6 = o; o += N * L.P4;
     L.H1 = o; o += JC * L.m;
-    L.H2 = o; o += JC * L.m;
     L.H3 = o; o += JC * L.m;
+    L.H2 = o; o += JC * L.m;
     L.H5 = o; o += JC * L.m;
     L.H4 = o; o += N * L.m;
     L.H6 = o; o += N * L.m;
@@ -79,7 +83,11 @@ __host__ __device__ inline P1Layout p1_layout(int N, int JC)
     return L;
 }
 
-size_t p1_smem_bytes(int N, int JC) { return (size_t)p1_layout(N, JC).total * 4; }
+size_t p1_smem_bytes(int N, int JC)
+{
+    const int RS = (N - 2 + 3) & ~3;
+    return (size_t)p1_layout(N, JC, RS).total * 4;
+}
 
 int p1_chunk(int N)
 {
@@ -87,16 +95,29 @@ int p1_chunk(int N)
     return 1;
 }
 
+// Tile and tile row of the full rows: kind q (0: kind 1, 1: kind 3, 2: kind 2,
+// 3: kind 5), location j of the smallest facility, other location l.
+__device__ __forceinline__ void full_row(int q, int N, int i, int k, int pp, int j, int l, int &t,
+                                         int &row)
+{
+    if (q == 0) { t = tidx_n(N, i, j, k, l); row = pp - 2; }        // d_ijklpq: tile (i,j,k,l), row p
+    else if (q == 1) { t = tidx_n(N, k, l, i, j); row = pp - 2; }   // d_klijpq: tile (k,l,i,j), row p
+    else if (q == 2) { t = tidx_n(N, i, j, pp, l); row = k - 1; }   // d_ijplkn: tile (i,j,p,l), row k
+    else { t = tidx_n(N, pp, l, i, j); row = k - 1; }               // d_plijkn: tile (p,l,i,j), row k
+}
+
 template <int JC>
-__global__ void __launch_bounds__(kP1Threads)
-    p1_kernel(PassState p, int N, int RS, const int4 *__restrict__ triples, int nchunks)
+__global__ void __launch_bounds__(kP1Threads, 2)
+    p1_kernel(PassState p, int N, int RS, const int4 *__restrict__ triples, int nchunks,
+              FastDiv fm, FastDiv fn)
 {
     if (*p.stop) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.counter = 0;  // work counter of the D -> C sweep
-    extern __shared__ __align__(16) int sm[];
-    const P1Layout L = p1_layout(N, JC);
+    extern __shared__ __align__(128) int sm[];
+    const P1Layout L = p1_layout(N, JC, RS);
     const int n = L.n, m = L.m;
-    const int TS = n * RS;
+    const size_t TS = (size_t)n * RS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int4 tr = triples[blockIdx.x / nchunks];
     const int i = tr.x, k = tr.y, pp = tr.z;
     const int j0 = (blockIdx.x % nchunks) * JC;
@@ -104,135 +125,157 @@ __global__ void __launch_bounds__(kP1Threads)
     const int *__restrict__ yC = p.yC;
     const int *__restrict__ xb = p.x;
     int *__restrict__ z = p.z;
-    const int RV = RS >> 2;  // int4 per tile row
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.BAR);
+    const unsigned rowBytes = (unsigned)RS * 4u;
 
-    // ---- shares of the staged rows (c' of the tile, spread over its rows)
-    // kinds 1,3,2,5: jc*m rows each
-    for (int e = threadIdx.x; e < 4 * jc * m; e += blockDim.x) {
-        const int kind = e / (jc * m), rr = e % (jc * m);
-        const int jj = rr / m, o = rr % m, j = j0 + jj;
-        const int l = o + (o >= j);  // n (kinds 1,3) or q (kinds 2,5)
-        int t, b, bk, row, h;
-        if (kind == 0) {         // kind 1: tile (i,j,k,l) row p
-            t = tidx_n(N, i, j, k, l); b = xb[i * N + j]; bk = k - 1; row = pp - 2; h = L.H1;
-        } else if (kind == 1) {  // kind 3: tile (k,l,i,j) row p
-            t = tidx_n(N, k, l, i, j); b = xb[k * N + l]; bk = i; row = pp - 2; h = L.H3;
-        } else if (kind == 2) {  // kind 2: tile (i,j,p,l) row k
-            t = tidx_n(N, i, j, pp, l); b = xb[i * N + j]; bk = pp - 1; row = k - 1; h = L.H2;
-        } else {                 // kind 5: tile (p,l,i,j) row k
-            t = tidx_n(N, pp, l, i, j); b = xb[pp * N + l]; bk = i; row = k - 1; h = L.H5;
-        }
-        const int c1 = yC[t] + share(b, m, bk);
-        sm[h + rr] = share(c1, n, row);
-    }
-    // kinds 4,6: N*m rows each
-    for (int e = threadIdx.x; e < 2 * N * m; e += blockDim.x) {
-        const int kind = e / (N * m), rr = e % (N * m);
-        const int a = rr / m, o = rr % m;
-        const int l = o + (o >= a);
-        int t, c1;
-        if (kind == 0) {  // kind 4: tile (k,a,p,l) row i
-            t = tidx_n(N, k, a, pp, l);
-            c1 = yC[t] + share(xb[k * N + a], m, pp - 1);
-            sm[L.H4 + rr] = share(c1, n, i);
-        } else {          // kind 6: tile (p,a,k,l) row i
-            t = tidx_n(N, pp, a, k, l);
-            c1 = yC[t] + share(xb[pp * N + a], m, k);
-            sm[L.H6 + rr] = share(c1, n, i);
-        }
-    }
-
-    // ---- stage the tile rows
-    for (int e = threadIdx.x; e < 4 * jc * m * RV; e += blockDim.x) {
-        const int kind = e / (jc * m * RV), rem = e % (jc * m * RV);
-        const int rr = rem / RV, part = rem % RV;
-        const int jj = rr / m, o = rr % m, j = j0 + jj;
-        const int l = o + (o >= j);
-        int t, row, base, ld;
-        if (kind == 0) { t = tidx_n(N, i, j, k, l); row = pp - 2; base = L.A1; ld = n; }
-        else if (kind == 1) { t = tidx_n(N, k, l, i, j); row = pp - 2; base = L.A3; ld = n; }
-        else if (kind == 2) { t = tidx_n(N, i, j, pp, l); row = k - 1; base = L.A2; ld = L.n2; }
-        else { t = tidx_n(N, pp, l, i, j); row = k - 1; base = L.A5; ld = L.n2; }
-        const int4 w = *reinterpret_cast<const int4 *>(z + (size_t)t * TS + row * RS + 4 * part);
-        int *dst = sm + base + rr * ld + 4 * part;
-        const int c = 4 * part;
-        if (c + 0 < n) dst[0] = w.x;
-        if (c + 1 < n) dst[1] = w.y;
-        if (c + 2 < n) dst[2] = w.z;
-        if (c + 3 < n) dst[3] = w.w;
-    }
-    for (int e = threadIdx.x; e < 2 * N * m * jc; e += blockDim.x) {
-        const int kind = e / (N * m * jc), rem = e % (N * m * jc);
-        const int a = rem / (m * jc), o = (rem / jc) % m, jj = rem % jc, j = j0 + jj;
-        const int l = o + (o >= a);
-        if (j == a || j == l) continue;
-        const int col = j - (j > a) - (j > l);
-        int t, base;
-        if (kind == 0) { t = tidx_n(N, k, a, pp, l); base = L.A4; }
-        else { t = tidx_n(N, pp, a, k, l); base = L.A6; }
-        sm[base + a * L.P4 + o * L.JCp + jj] = z[(size_t)t * TS + i * RS + col];
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 4 * 32);
+        fence_mbar_init();
     }
     __syncthreads();
 
-    // ---- split every class {(i,j),(k,nn),(p,qq)}, j in the chunk
-    for (int e = threadIdx.x; e < jc * m * n; e += blockDim.x) {
-        const int jj = e / (m * n), o = (e / n) % m, s = e % n;
+    // ---- issue every load: full rows by bulk copies (warps 0-3, one kind
+    // each), the JC-column pieces of kinds 4 and 6 by 4-byte cp.async
+    if (warp < 4) {
+        const int q = warp;
+        const int ab = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
+        const int mine = lane < m ? (m - 1 - lane) / 32 + 1 : 0;
+        mbar_arrive_expect_tx(bar, (unsigned)(jc * mine) * rowBytes);
+        for (int jj = 0; jj < jc; ++jj) {
+            const int j = j0 + jj;
+            for (int o = lane; o < m; o += 32) {
+                const int l = o + (o >= j);
+                int t, row;
+                full_row(q, N, i, k, pp, j, l, t, row);
+                bulk_load_tx(sm + ab + (jj * m + o) * RS, z + t * TS + row * RS, rowBytes, bar);
+            }
+        }
+    } else {
+        const int tw = (warp - 4) * 32 + lane, nt = (kP1Warps - 4) * 32;
+        for (int e = tw; e < 2 * N * m * JC; e += nt) {
+            const int jj = e % JC, ro = e / JC;           // JC is a power of two
+            const int kind = ro >= N * m;
+            const int r2 = ro - kind * N * m;
+            const int a = (int)fdiv((unsigned)r2, fm), o = r2 - a * m;
+            const int j = j0 + jj;
+            const int l = o + (o >= a);
+            if (jj >= jc || j == a || j == l) continue;
+            const int col = j - (j > a) - (j > l);
+            // kind 4: d_kapl(i)(j) in tile (k,a,p,l) row i; kind 6: tile (p,a,k,l) row i
+            const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
+            int *dst = sm + (kind ? L.A6 : L.A4) + a * L.P4 + o * L.JCp + jj;
+            cp_async4(dst, z + t * TS + (size_t)i * RS + col);
+        }
+    }
+
+    // ---- shares of the staged rows while the copies fly: the cost c' of the
+    // tile (c plus the share of b of its row in C) spread over the tile's rows
+    for (int q = warp; q < 4 * JC + 2 * N; q += kP1Warps) {
+        if (q < 4 * JC) {
+            const int kind = q / JC, jj = q % JC, j = j0 + jj;
+            if (jj >= jc) continue;
+            const int hb = kind == 0 ? L.H1 : kind == 1 ? L.H3 : kind == 2 ? L.H2 : L.H5;
+            for (int o = lane; o < m; o += 32) {
+                const int l = o + (o >= j);
+                int t, row, b, bk;
+                full_row(kind, N, i, k, pp, j, l, t, row);
+                if (kind == 0) { b = xb[i * N + j]; bk = k - 1; }       // b_ij over rows k != i
+                else if (kind == 1) { b = xb[k * N + l]; bk = i; }      // b_kl over rows i != k
+                else if (kind == 2) { b = xb[i * N + j]; bk = pp - 1; } // b_ij, row p
+                else { b = xb[pp * N + l]; bk = i; }                   // b_pl, row i
+                const int c1 = yC[t] + share(b, fm, bk);
+                sm[hb + jj * m + o] = share(c1, fn, row);
+            }
+        } else {
+            const int q2 = q - 4 * JC;
+            const int kind = q2 >= N, a = q2 - kind * N;
+            for (int o = lane; o < m; o += 32) {
+                const int l = o + (o >= a);
+                if (!kind) {  // kind 4: tile (k,a,p,l): b_ka over rows p != k, tile row i
+                    const int t = tidx_n(N, k, a, pp, l);
+                    const int c1 = yC[t] + share(xb[k * N + a], fm, pp - 1);
+                    sm[L.H4 + a * m + o] = share(c1, fn, i);
+                } else {      // kind 6: tile (p,a,k,l): b_pa over rows k != p, tile row i
+                    const int t = tidx_n(N, pp, a, k, l);
+                    const int c1 = yC[t] + share(xb[pp * N + a], fm, k);
+                    sm[L.H6 + a * m + o] = share(c1, fn, i);
+                }
+            }
+        }
+    }
+
+    cp_async_wait_all();
+    const bool ok = __syncthreads_and(mbar_wait(bar, 0));
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(&p.status->err, kDevTimeout);
+        mbar_wait(bar, 0);   // let the copies in flight land (bounded), then leave
+        return;
+    }
+
+    // ---- split every class {(i,j),(k,nn),(p,qq)}, j in the chunk: one warp
+    // per (j, nn), lanes over the column s of qq in the kind-1 row
+    for (int jj = 0; jj < jc; ++jj) {
         const int j = j0 + jj;
-        const int nn = o + (o >= j);
-        const int qq = skip2(s, j, nn);
-        const int q1 = qq - (qq > j);
-        const int s2 = nn - (nn > j) - (nn > qq);
-        const int q4 = qq - (qq > nn);
-        const int n6 = nn - (nn > qq);
-        int *a1 = sm + L.A1 + (jj * m + o) * n + s;
-        int *a3 = sm + L.A3 + (jj * m + o) * n + s;
-        int *a2 = sm + L.A2 + (jj * m + q1) * L.n2 + s2;
-        int *a5 = sm + L.A5 + (jj * m + q1) * L.n2 + s2;
-        int *a4 = sm + L.A4 + nn * L.P4 + q4 * L.JCp + jj;
-        int *a6 = sm + L.A6 + qq * L.P4 + n6 * L.JCp + jj;
-        const int T = *a1 + sm[L.H1 + jj * m + o] + *a2 + sm[L.H2 + jj * m + q1] +
-                      *a3 + sm[L.H3 + jj * m + o] + *a4 + sm[L.H4 + nn * m + q4] +
-                      *a5 + sm[L.H5 + jj * m + q1] + *a6 + sm[L.H6 + qq * m + n6];
-        const int q6 = T / 6, rm = T - 6 * q6;
-        *a1 = q6 + (0 < rm);
-        *a2 = q6 + (1 < rm);
-        *a3 = q6 + (2 < rm);
-        *a4 = q6 + (3 < rm);
-        *a5 = q6 + (4 < rm);
-        *a6 = q6 + (5 < rm);
+        for (int o = warp; o < m; o += kP1Warps) {
+            const int nn = o + (o >= j);
+            const int h1 = sm[L.H1 + jj * m + o], h3 = sm[L.H3 + jj * m + o];
+            int *r1 = sm + L.A1 + (jj * m + o) * RS;
+            int *r3 = sm + L.A3 + (jj * m + o) * RS;
+            for (int s = lane; s < n; s += 32) {
+                const int qq = skip2(s, j, nn);
+                const int q1 = qq - (qq > j);          // rank of qq among locations != j
+                const int s2 = o - (nn > qq);          // column of nn in tiles (.,j,.,qq)/(.,qq,.,j)
+                const int q4 = qq - (qq > nn);         // rank of qq among locations != nn
+                const int n6 = nn - (nn > qq);         // rank of nn among locations != qq
+                int *a2 = sm + L.A2 + (jj * m + q1) * RS + s2;
+                int *a5 = sm + L.A5 + (jj * m + q1) * RS + s2;
+                int *a4 = sm + L.A4 + nn * L.P4 + q4 * L.JCp + jj;
+                int *a6 = sm + L.A6 + qq * L.P4 + n6 * L.JCp + jj;
+                const int T = r1[s] + h1 + *a2 + sm[L.H2 + jj * m + q1] + r3[s] + h3 +
+                              *a4 + sm[L.H4 + nn * m + q4] + *a5 + sm[L.H5 + jj * m + q1] +
+                              *a6 + sm[L.H6 + qq * m + n6];
+                const int q6 = T / 6, rm = T - 6 * q6;
+                r1[s] = q6 + (0 < rm);   // ranks: d_ijknpq 0, d_ijpqkn 1, d_knijpq 2,
+                *a2 = q6 + (1 < rm);     //        d_knpqij 3, d_pqijkn 4, d_pqknij 5
+                r3[s] = q6 + (2 < rm);
+                *a4 = q6 + (3 < rm);
+                *a5 = q6 + (4 < rm);
+                *a6 = q6 + (5 < rm);
+            }
+        }
     }
+    fence_proxy_async_smem();
     __syncthreads();
 
-    // ---- write back
-    for (int e = threadIdx.x; e < 4 * jc * m * RV; e += blockDim.x) {
-        const int kind = e / (jc * m * RV), rem = e % (jc * m * RV);
-        const int rr = rem / RV, part = rem % RV;
-        const int jj = rr / m, o = rr % m, j = j0 + jj;
-        const int l = o + (o >= j);
-        int t, row, base, ld;
-        if (kind == 0) { t = tidx_n(N, i, j, k, l); row = pp - 2; base = L.A1; ld = n; }
-        else if (kind == 1) { t = tidx_n(N, k, l, i, j); row = pp - 2; base = L.A3; ld = n; }
-        else if (kind == 2) { t = tidx_n(N, i, j, pp, l); row = k - 1; base = L.A2; ld = L.n2; }
-        else { t = tidx_n(N, pp, l, i, j); row = k - 1; base = L.A5; ld = L.n2; }
-        const int *src = sm + base + rr * ld + 4 * part;
-        const int c = 4 * part;
-        int4 w;
-        w.x = c + 0 < n ? src[0] : 0;
-        w.y = c + 1 < n ? src[1] : 0;
-        w.z = c + 2 < n ? src[2] : 0;
-        w.w = c + 3 < n ? src[3] : 0;
-        *reinterpret_cast<int4 *>(z + (size_t)t * TS + row * RS + c) = w;
-    }
-    for (int e = threadIdx.x; e < 2 * N * m * jc; e += blockDim.x) {
-        const int kind = e / (N * m * jc), rem = e % (N * m * jc);
-        const int a = rem / (m * jc), o = (rem / jc) % m, jj = rem % jc, j = j0 + jj;
-        const int l = o + (o >= a);
-        if (j == a || j == l) continue;
-        const int col = j - (j > a) - (j > l);
-        int t, base;
-        if (kind == 0) { t = tidx_n(N, k, a, pp, l); base = L.A4; }
-        else { t = tidx_n(N, pp, a, k, l); base = L.A6; }
-        z[(size_t)t * TS + i * RS + col] = sm[base + a * L.P4 + o * L.JCp + jj];
+    // ---- write back: full rows by bulk stores, column pieces by plain stores
+    if (warp < 4) {
+        const int q = warp;
+        const int ab = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
+        for (int jj = 0; jj < jc; ++jj) {
+            const int j = j0 + jj;
+            for (int o = lane; o < m; o += 32) {
+                const int l = o + (o >= j);
+                int t, row;
+                full_row(q, N, i, k, pp, j, l, t, row);
+                bulk_store(z + t * TS + row * RS, sm + ab + (jj * m + o) * RS, rowBytes);
+            }
+        }
+        bulk_commit();
+        bulk_wait_read_all();
+    } else {
+        const int tw = (warp - 4) * 32 + lane, nt = (kP1Warps - 4) * 32;
+        for (int e = tw; e < 2 * N * m * JC; e += nt) {
+            const int jj = e % JC, ro = e / JC;
+            const int kind = ro >= N * m;
+            const int r2 = ro - kind * N * m;
+            const int a = (int)fdiv((unsigned)r2, fm), o = r2 - a * m;
+            const int j = j0 + jj;
+            const int l = o + (o >= a);
+            if (jj >= jc || j == a || j == l) continue;
+            const int col = j - (j > a) - (j > l);
+            const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
+            z[t * TS + (size_t)i * RS + col] = sm[(kind ? L.A6 : L.A4) + a * L.P4 + o * L.JCp + jj];
+        }
     }
 }
 
@@ -286,7 +329,8 @@ static cudaError_t p1_go(const Geom &g, const PassState &p, const int4 *triples,
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nchunks = (g.N + JC - 1) / JC;
-    k<<<ntriples * nchunks, kP1Threads, smem, s>>>(p, g.N, g.RS, triples, nchunks);
+    k<<<ntriples * nchunks, kP1Threads, smem, s>>>(p, g.N, g.RS, triples, nchunks,
+                                                    make_fastdiv(g.N - 1), make_fastdiv(g.N - 2));
     return cudaGetLastError();
 }
 
