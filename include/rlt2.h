@@ -105,8 +105,8 @@ void rlt2_destroy(rlt2_ctx *ctx);
 
 /*
  * Enqueue k passes of the loop of Algorithm 1 on the context's stream:
- * spread B->C and C->D with the transfer between complementary costs of D
- * (one fused pass over D), concentration D->C (N^2 (N-1)^2 Hungarian LAPs of
+ * spread B->C (a pass over C), spread C->D with the transfer between
+ * complementary costs of D (one fused pass over D), concentration D->C (N^2 (N-1)^2 Hungarian LAPs of
  * size N-2, Sec. 4.1), transfer between complementary costs of C fused into
  * concentration C->B (N^2 LAPs of size N-1), concentration B->LB (one LAP of
  * size N) and LB <- LB + LB'.  Returns without waiting for the GPU.  Passes
@@ -147,8 +147,8 @@ int rlt2_work(rlt2_ctx *ctx, int64_t out[6]);
 
 /*
  * Stage times recorded while opts.profile was set (synchronises): out[s] =
- * total milliseconds of stage s over all profiled passes, s = 0 fused
- * spread/complementary pass over D, 1 concentration D->C, 2 complementary C +
+ * total milliseconds of stage s over all profiled passes, s = 0 spread B->C
+ * and the fused spread/complementary pass over D, 1 concentration D->C, 2 complementary C +
  * concentration C->B, 3 concentration B->LB; *passes = passes recorded.
  * rlt2_reset_stage_times() clears the totals.
  */

@@ -49,6 +49,7 @@ struct PassState {
 
 cudaError_t launch_init(const Geom &g, const PassState &p, const int32_t *F, const int32_t *D,
                         const int32_t *Blin, long long lb_const, cudaStream_t s);
+cudaError_t launch_spread_x(const Geom &g, const PassState &p, cudaStream_t s);
 cudaError_t launch_p1(const Geom &g, const PassState &p, const int4 *triples, int ntriples,
                       cudaStream_t s);
 cudaError_t launch_dlap(const Geom &g, const PassState &p, int sm_count, cudaStream_t s);

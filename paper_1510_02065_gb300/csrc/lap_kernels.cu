@@ -105,22 +105,6 @@ __global__ void __launch_bounds__(kDlapWarps * 32)
 
 // -------------------------------------------- complementary C + C -> B
 
-// In RLT1 mode the input of C -> B is C plus the spread of B (no D in between);
-// this kernel writes it to yS so that the fused transfer reads one buffer.
-__global__ void spread_x_to_y_kernel(PassState p, int N)
-{
-    if (*p.stop) return;
-    const int m = N - 1;
-    const long long tiles = (long long)N * N * m * m;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tiles;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int kk = (int)((t / m) % m);
-        const int ij = (int)(t / ((long long)m * m));
-        const int b = p.x[ij];
-        p.yS[t] = p.yC[t] + b / m + (kk < b % m ? 1 : 0);
-    }
-}
-
 template <int NS, bool PACK>
 __global__ void __launch_bounds__(kClapWarps * 32) clap_kernel(PassState p, int N)
 {
@@ -318,11 +302,8 @@ static cudaError_t clap_go(const Geom &g, const PassState &p, cudaStream_t s)
 cudaError_t launch_clap(const Geom &g, const PassState &p, cudaStream_t s)
 {
     if (p.rlt1_only) {
-        const long long tiles = g.tiles;
-        int grid = (int)((tiles + 255) / 256);
-        if (grid > 4096) grid = 4096;
-        spread_x_to_y_kernel<<<grid, 256, 0, s>>>(p, g.N);
-        cudaError_t e = cudaGetLastError();
+        // without D, the input of C -> B is C plus the spread of B
+        cudaError_t e = launch_spread_x(g, p, s);
         if (e != cudaSuccess) return e;
     }
     if (g.N - 1 <= 32) return p.pack ? clap_go<1, true>(g, p, s) : clap_go<1, false>(g, p, s);

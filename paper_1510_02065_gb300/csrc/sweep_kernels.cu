@@ -1,8 +1,9 @@
-// sweep_kernels.cu -- initialisation and the fused pass over D (sm_103a).
+// sweep_kernels.cu -- initialisation and the spreading passes (sm_103a).
 //
-// p1_kernel performs the first three operations of the loop of Algorithm 1 in
-// one read and one write of D:
-//   spread B -> C   (Sec. 4.2): c'_ijkn = c_ijkn + the share of b_ij of row k,
+// spread_x_to_y_kernel: spread B -> C (Sec. 4.2), c'_ijkn = c_ijkn + the share
+// of b_ij of row k, one small pass over C.
+// p1_kernel performs the next two operations of the loop of Algorithm 1 in one
+// read and one write of D:
 //   spread C -> D   (Sec. 4.2): every d_ijknpq of row p gains the share of c'_ijkn,
 //   complementary D (Sec. 4.3, Eq. (11)): the six members of each class are
 //                   replaced by the equal split of their sum, the odd units going
@@ -19,6 +20,10 @@
 // JC columns j of rows shared with the CTAs of the other chunks.  The CTA stages
 // them in shared memory with 16-byte loads, splits every class, and writes the
 // rows back.  With i < k < p the lexicographic ranks of kinds 1..6 are 0..5.
+// Full rows move by 1-D bulk copies (cp.async.bulk) completing on one
+// mbarrier; the column pieces by 4-byte cp.async; all loads of a CTA are in
+// flight at once, and two CTAs per SM overlap one's copies with the other's
+// arithmetic.
 #include "device.cuh"
 #include "kernels.h"
 
@@ -110,6 +115,7 @@ template <int JC>
 __global__ void __launch_bounds__(kP1Threads, 2)
     p1_kernel(PassState p, int N, int RS, const int4 *__restrict__ triples, int nchunks,
               FastDiv fm, FastDiv fn)
+// fm divides by N-1, fn by N-2; yS holds c' (C plus the spread of B) per tile
 {
     if (*p.stop) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.counter = 0;  // work counter of the D -> C sweep
@@ -122,8 +128,7 @@ __global__ void __launch_bounds__(kP1Threads, 2)
     const int i = tr.x, k = tr.y, pp = tr.z;
     const int j0 = (blockIdx.x % nchunks) * JC;
     const int jc = min(JC, N - j0);
-    const int *__restrict__ yC = p.yC;
-    const int *__restrict__ xb = p.x;
+    const int *__restrict__ yS = p.yS;
     int *__restrict__ z = p.z;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.BAR);
     const unsigned rowBytes = (unsigned)RS * 4u;
@@ -151,56 +156,38 @@ __global__ void __launch_bounds__(kP1Threads, 2)
             }
         }
     } else {
+        // one thread per row (a, o): row i of tile (k,a,p,l) (kind 4) or of
+        // tile (p,a,k,l) (kind 6); for a fixed a these tiles are consecutive
         const int tw = (warp - 4) * 32 + lane, nt = (kP1Warps - 4) * 32;
-        for (int e = tw; e < 2 * N * m * JC; e += nt) {
-            const int jj = e % JC, ro = e / JC;           // JC is a power of two
+        for (int ro = tw; ro < 2 * N * m; ro += nt) {
             const int kind = ro >= N * m;
             const int r2 = ro - kind * N * m;
             const int a = (int)fdiv((unsigned)r2, fm), o = r2 - a * m;
-            const int j = j0 + jj;
             const int l = o + (o >= a);
-            if (jj >= jc || j == a || j == l) continue;
-            const int col = j - (j > a) - (j > l);
-            // kind 4: d_kapl(i)(j) in tile (k,a,p,l) row i; kind 6: tile (p,a,k,l) row i
-            const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
-            int *dst = sm + (kind ? L.A6 : L.A4) + a * L.P4 + o * L.JCp + jj;
-            cp_async4(dst, z + t * TS + (size_t)i * RS + col);
+            const int t = (kind ? ((pp * N + a) * m + k) * m : ((k * N + a) * m + pp - 1) * m) + o;
+            // the share of c' of this tile that row i receives
+            sm[(kind ? L.H6 : L.H4) + a * m + o] = share(yS[t], fn, i);
+            const int *src = z + t * TS + (size_t)i * RS;
+            int *dst = sm + (kind ? L.A6 : L.A4) + a * L.P4 + o * L.JCp;
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj) {
+                const int j = j0 + jj;
+                if (jj < jc && j != a && j != l) cp_async4(dst + jj, src + (j - (j > a) - (j > l)));
+            }
         }
     }
 
-    // ---- shares of the staged rows while the copies fly: the cost c' of the
-    // tile (c plus the share of b of its row in C) spread over the tile's rows
-    for (int q = warp; q < 4 * JC + 2 * N; q += kP1Warps) {
-        if (q < 4 * JC) {
-            const int kind = q / JC, jj = q % JC, j = j0 + jj;
-            if (jj >= jc) continue;
-            const int hb = kind == 0 ? L.H1 : kind == 1 ? L.H3 : kind == 2 ? L.H2 : L.H5;
-            for (int o = lane; o < m; o += 32) {
-                const int l = o + (o >= j);
-                int t, row, b, bk;
-                full_row(kind, N, i, k, pp, j, l, t, row);
-                if (kind == 0) { b = xb[i * N + j]; bk = k - 1; }       // b_ij over rows k != i
-                else if (kind == 1) { b = xb[k * N + l]; bk = i; }      // b_kl over rows i != k
-                else if (kind == 2) { b = xb[i * N + j]; bk = pp - 1; } // b_ij, row p
-                else { b = xb[pp * N + l]; bk = i; }                   // b_pl, row i
-                const int c1 = yC[t] + share(b, fm, bk);
-                sm[hb + jj * m + o] = share(c1, fn, row);
-            }
-        } else {
-            const int q2 = q - 4 * JC;
-            const int kind = q2 >= N, a = q2 - kind * N;
-            for (int o = lane; o < m; o += 32) {
-                const int l = o + (o >= a);
-                if (!kind) {  // kind 4: tile (k,a,p,l): b_ka over rows p != k, tile row i
-                    const int t = tidx_n(N, k, a, pp, l);
-                    const int c1 = yC[t] + share(xb[k * N + a], fm, pp - 1);
-                    sm[L.H4 + a * m + o] = share(c1, fn, i);
-                } else {      // kind 6: tile (p,a,k,l): b_pa over rows k != p, tile row i
-                    const int t = tidx_n(N, pp, a, k, l);
-                    const int c1 = yC[t] + share(xb[pp * N + a], fm, k);
-                    sm[L.H6 + a * m + o] = share(c1, fn, i);
-                }
-            }
+    // ---- shares of the full rows while the copies fly: c' of the tile (c plus
+    // the share of b, computed by the spread kernel into yS) over the tile's rows
+    for (int q = warp; q < 4 * JC; q += kP1Warps) {
+        const int kind = q / JC, jj = q % JC, j = j0 + jj;
+        if (jj >= jc) continue;
+        const int hb = kind == 0 ? L.H1 : kind == 1 ? L.H3 : kind == 2 ? L.H2 : L.H5;
+        for (int o = lane; o < m; o += 32) {
+            const int l = o + (o >= j);
+            int t, row;
+            full_row(kind, N, i, k, pp, j, l, t, row);
+            sm[hb + jj * m + o] = share(yS[t], fn, row);
         }
     }
 
@@ -264,19 +251,44 @@ __global__ void __launch_bounds__(kP1Threads, 2)
         bulk_wait_read_all();
     } else {
         const int tw = (warp - 4) * 32 + lane, nt = (kP1Warps - 4) * 32;
-        for (int e = tw; e < 2 * N * m * JC; e += nt) {
-            const int jj = e % JC, ro = e / JC;
+        for (int ro = tw; ro < 2 * N * m; ro += nt) {
             const int kind = ro >= N * m;
             const int r2 = ro - kind * N * m;
             const int a = (int)fdiv((unsigned)r2, fm), o = r2 - a * m;
-            const int j = j0 + jj;
             const int l = o + (o >= a);
-            if (jj >= jc || j == a || j == l) continue;
-            const int col = j - (j > a) - (j > l);
-            const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
-            z[t * TS + (size_t)i * RS + col] = sm[(kind ? L.A6 : L.A4) + a * L.P4 + o * L.JCp + jj];
+            const int t = (kind ? ((pp * N + a) * m + k) * m : ((k * N + a) * m + pp - 1) * m) + o;
+            int *dst = z + t * TS + (size_t)i * RS;
+            const int *src = sm + (kind ? L.A6 : L.A4) + a * L.P4 + o * L.JCp;
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj) {
+                const int j = j0 + jj;
+                if (jj < jc && j != a && j != l) dst[j - (j > a) - (j > l)] = src[jj];
+            }
         }
     }
+}
+
+// Costs spreading from B to C (Sec. 4.2): c'_ijkn = c_ijkn + the share of b_ij
+// of row k (k' = rank of k among the facilities != i), written to yS.  One
+// block row per (i, j), threads over the (N-1)^2 entries of C_ij.
+__global__ void spread_x_to_y_kernel(PassState p, int N, FastDiv fm)
+{
+    if (*p.stop) return;
+    const int m = N - 1;
+    const int ij = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int kk = (int)fdiv((unsigned)e, fm);
+    const long long t = (long long)ij * m * m + e;
+    p.yS[t] = p.yC[t] + share(p.x[ij], fm, kk);
+}
+
+cudaError_t launch_spread_x(const Geom &g, const PassState &p, cudaStream_t s)
+{
+    const int m = g.N - 1;
+    dim3 grid((m * m + 255) / 256, g.N * g.N);
+    spread_x_to_y_kernel<<<grid, 256, 0, s>>>(p, g.N, make_fastdiv(m));
+    return cudaGetLastError();
 }
 
 // c_ijkn <- f_ik * d_jn  (initialisation of Algorithm 1)
@@ -337,6 +349,8 @@ static cudaError_t p1_go(const Geom &g, const PassState &p, const int4 *triples,
 cudaError_t launch_p1(const Geom &g, const PassState &p, const int4 *triples, int ntriples,
                       cudaStream_t s)
 {
+    cudaError_t e = launch_spread_x(g, p, s);
+    if (e != cudaSuccess) return e;
     switch (p1_chunk(g.N)) {
     case 4: return p1_go<4>(g, p, triples, ntriples, s);
     case 2: return p1_go<2>(g, p, triples, ntriples, s);
