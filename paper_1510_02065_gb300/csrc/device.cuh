@@ -40,6 +40,13 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+__device__ __forceinline__ int lds32(uint32_t addr)
+{
+    int v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
@@ -210,8 +217,7 @@ __device__ __forceinline__ long long warp_sum64(long long x)
 //
 // PACK: when every key is below 2^25 the key and its column are packed into
 // one 32-bit value (key * 64 + column) and one reduction yields both the
-// minimum and the smallest column attaining it; a column's matched row and
-// that row's potential then share one word as well (one shuffle per step).
+// minimum and the smallest column attaining it.
 //
 // Value range: with entries in [0, A], |u|, |v| <= A and every key <= 3A, so
 // A <= 2^29 - 1 fits int32 (PACK needs 3A < 2^25).
@@ -232,13 +238,9 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
     bool valid[NS];
     int way[NS], dlab[NS];
     unsigned key[NS];
-    // Matched row and its potential of each column.  PACK: one word u * 64 + row
-    // (u < 2^24 there), -1 for a free column; otherwise rowOf / uM separately.
-    int ur[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         valid[s] = lane + 32 * s < n;
-        ur[s] = -1;
         rowOf[s] = -1;
         uM[s] = 0;
         v[s] = 0;
@@ -246,6 +248,8 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
         dlab[s] = 0;
     }
     int sumK = 0, sumK2 = 0;
+    const uint32_t Mlane = smem_addr(M) + 4u * lane;
+    const uint32_t ldB = 4u * (uint32_t)ld;
 
     for (int r = 0; r < n; ++r) {
         // key = distance label (+ D of its last update), packed with the column
@@ -260,11 +264,11 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
         unsigned mm;
         int Dk, j1;
         for (;;) {
-            const int *Mrow = M + i0 * ld + lane;
+            const uint32_t Mrow = Mlane + (uint32_t)i0 * ldB;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 if (valid[s]) {
-                    const int cand = Mrow[32 * s] - v[s] - c0;
+                    const int cand = lds32(Mrow + 128u * s) - v[s] - c0;
                     const unsigned ck = PACK ? ((unsigned)cand << 6) | (unsigned)(lane + 32 * s)
                                              : (unsigned)cand;
                     if ((int)ck < (int)key[s]) {
@@ -290,15 +294,8 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
                 }
             }
             const int src = j1 & 31, sl = j1 >> 5;
-            int rj, uj;
-            if constexpr (PACK) {
-                const int w = __shfl_sync(kFull, pick<NS>(ur, sl), src);
-                rj = w < 0 ? -1 : (w & 63);
-                uj = w >> 6;
-            } else {
-                rj = __shfl_sync(kFull, pick<NS>(rowOf, sl), src);
-                uj = __shfl_sync(kFull, pick<NS>(uM, sl), src);
-            }
+            const int rj = __shfl_sync(kFull, pick<NS>(rowOf, sl), src);
+            const int uj = __shfl_sync(kFull, pick<NS>(uM, sl), src);
             if (rj < 0 || mm == kDone) break;  // free column: augmenting path found
             if (lane == src) {
                 put<NS>(key, sl, kDone);
@@ -320,64 +317,32 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
             if (lab) {
                 const int dd = Dend - dlab[s];
                 v[s] -= dd;
-                if constexpr (PACK) ur[s] += dd << 6;
-                else uM[s] += dd;
+                uM[s] += dd;
             }
         }
         sumK += K;
         sumK2 += K * K;
 
-        // augment: every column on the path from jf back to the new row takes
-        // the (old) row and potential of its predecessor.  Gather them for all
-        // columns at once, then walk the path to find its members.
-        int nr[NS], nu[NS];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const int w = way[s] < 0 ? 0 : way[s];
-            int g0, g1 = 0, h0 = 0, h1 = 0;
-            if constexpr (PACK) {
-                g0 = __shfl_sync(kFull, ur[0], w & 31);
-                if constexpr (NS == 2) g1 = __shfl_sync(kFull, ur[1], w & 31);
-                const int gw = (NS == 2 && (w >> 5)) ? g1 : g0;
-                nr[s] = way[s] < 0 ? ((Dend << 6) | r) : gw;
-            } else {
-                g0 = __shfl_sync(kFull, rowOf[0], w & 31);
-                h0 = __shfl_sync(kFull, uM[0], w & 31);
-                if constexpr (NS == 2) {
-                    g1 = __shfl_sync(kFull, rowOf[1], w & 31);
-                    h1 = __shfl_sync(kFull, uM[1], w & 31);
-                }
-                const bool hi = NS == 2 && (w >> 5);
-                nr[s] = way[s] < 0 ? r : (hi ? g1 : g0);
-                nu[s] = way[s] < 0 ? Dend : (hi ? h1 : h0);
-            }
-        }
-        unsigned on0 = 0, on1 = 0;
+        // augment: each column on the path takes the row of its predecessor
         int c = jf;
         for (int hop = 0;; ++hop) {
             if (hop > K) return false;
-            if (c < 32) on0 |= 1u << c;
-            else on1 |= 1u << (c - 32);
-            const int w = __shfl_sync(kFull, pick<NS>(way, c >> 5), c & 31);
+            const int cs = c >> 5, cl = c & 31;
+            const int w = __shfl_sync(kFull, pick<NS>(way, cs), cl);
+            int nr = r, nu = Dend;
+            const int ws = (w < 0 ? 0 : w) >> 5, wl = (w < 0 ? 0 : w) & 31;
+            const int pr = __shfl_sync(kFull, pick<NS>(rowOf, ws), wl);
+            const int pu = __shfl_sync(kFull, pick<NS>(uM, ws), wl);
+            if (w >= 0) {
+                nr = pr;
+                nu = pu;
+            }
+            if (lane == cl) {
+                put<NS>(rowOf, cs, nr);
+                put<NS>(uM, cs, nu);
+            }
             if (w < 0) break;
             c = w;
-        }
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            if (((s ? on1 : on0) >> lane) & 1u) {
-                if constexpr (PACK) ur[s] = nr[s];
-                else {
-                    rowOf[s] = nr[s];
-                    uM[s] = nu[s];
-                }
-            }
-        }
-    }
-    if constexpr (PACK) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            rowOf[s] = ur[s] < 0 ? -1 : (ur[s] & 63);
-            uM[s] = ur[s] < 0 ? 0 : (ur[s] >> 6);
         }
     }
     steps_out += sumK;

@@ -16,12 +16,17 @@
 namespace rlt2 {
 
 constexpr int kDlapWarps = 4;
+#ifndef RLT2_DLAP_NBUF
+#define RLT2_DLAP_NBUF 2
+#endif
 constexpr int kClapWarps = 4;
 constexpr int kBatchWarps = 4;
 
 // ------------------------------------------------------------ D -> C sweep
 
-template <int NS, bool PACK>
+// NBUF = 2: each warp prefetches its next tile while it solves the current
+// one; NBUF = 1: one tile buffer per warp, twice the warps per SM.
+template <int NS, bool PACK, int NBUF>
 __global__ void __launch_bounds__(kDlapWarps * 32)
     dlap_kernel(PassState p, int n, int RS, long long ntiles)
 {
@@ -30,8 +35,8 @@ __global__ void __launch_bounds__(kDlapWarps * 32)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int TS = n * RS;
     const unsigned bytes = (unsigned)TS * 4u;
-    int *bufs = reinterpret_cast<int *>(smem) + (size_t)warp * 2 * TS;
-    unsigned char *tail = smem + (size_t)kDlapWarps * 2 * TS * 4;
+    int *bufs = reinterpret_cast<int *>(smem) + (size_t)warp * NBUF * TS;
+    unsigned char *tail = smem + (size_t)kDlapWarps * NBUF * TS * 4;
     uint64_t *bars = reinterpret_cast<uint64_t *>(tail) + warp * 2;
     int *uRow = reinterpret_cast<int *>(tail + kDlapWarps * 16) + warp * 64;
 
@@ -54,8 +59,8 @@ __global__ void __launch_bounds__(kDlapWarps * 32)
     int cur = 0;
     long long steps = 0, relax = 0, laps = 0;
     while (t < ntiles) {
-        const long long tn = grab();
-        const bool pref = tn < ntiles;
+        const long long tn = NBUF == 2 ? grab() : 0;
+        const bool pref = NBUF == 2 && tn < ntiles;
         if (pref && lane == 0) {
             fence_proxy_async_smem();
             bulk_load(bufs + (cur ^ 1) * TS, p.z + tn * TS, bytes, &bars[cur ^ 1]);
@@ -90,8 +95,16 @@ __global__ void __launch_bounds__(kDlapWarps * 32)
         if (lane == 0) p.yS[t] = (int)S;
         ++laps;
         __syncwarp();
-        t = tn;
-        cur ^= 1;
+        if constexpr (NBUF == 2) {
+            t = tn;
+            cur ^= 1;
+        } else {
+            t = grab();
+            if (t < ntiles && lane == 0) {
+                fence_proxy_async_smem();
+                bulk_load(bufs, p.z + t * TS, bytes, &bars[0]);
+            }
+        }
     }
     if (lane == 0 && laps) {
         atomicAdd(&p.status->laps, (unsigned long long)laps);
@@ -263,8 +276,9 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
 template <int NS, bool PACK>
 static cudaError_t dlap_go(const Geom &g, const PassState &p, int sm_count, cudaStream_t s)
 {
-    const size_t smem = (size_t)kDlapWarps * (2 * (size_t)g.TS * 4 + 16 + 256);
-    auto k = dlap_kernel<NS, PACK>;
+    constexpr int NB = RLT2_DLAP_NBUF;
+    const size_t smem = (size_t)kDlapWarps * (NB * (size_t)g.TS * 4 + 16 + 256);
+    auto k = dlap_kernel<NS, PACK, NB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
