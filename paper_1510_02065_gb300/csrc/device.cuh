@@ -40,13 +40,6 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ int lds32(uint32_t addr)
-{
-    int v;
-    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
@@ -248,8 +241,6 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
         dlab[s] = 0;
     }
     int sumK = 0, sumK2 = 0;
-    const uint32_t Mlane = smem_addr(M) + 4u * lane;
-    const uint32_t ldB = 4u * (uint32_t)ld;
 
     for (int r = 0; r < n; ++r) {
         // key = distance label (+ D of its last update), packed with the column
@@ -264,11 +255,11 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
         unsigned mm;
         int Dk, j1;
         for (;;) {
-            const uint32_t Mrow = Mlane + (uint32_t)i0 * ldB;
+            const int *Mrow = M + i0 * ld + lane;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 if (valid[s]) {
-                    const int cand = lds32(Mrow + 128u * s) - v[s] - c0;
+                    const int cand = Mrow[32 * s] - v[s] - c0;
                     const unsigned ck = PACK ? ((unsigned)cand << 6) | (unsigned)(lane + 32 * s)
                                              : (unsigned)cand;
                     if ((int)ck < (int)key[s]) {

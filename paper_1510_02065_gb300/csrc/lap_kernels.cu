@@ -17,7 +17,7 @@ namespace rlt2 {
 
 constexpr int kDlapWarps = 4;
 #ifndef RLT2_DLAP_NBUF
-#define RLT2_DLAP_NBUF 2
+#define RLT2_DLAP_NBUF 1
 #endif
 constexpr int kClapWarps = 4;
 constexpr int kBatchWarps = 4;
