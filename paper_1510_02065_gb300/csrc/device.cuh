@@ -217,16 +217,16 @@ __device__ __forceinline__ long long warp_sum64(long long x)
 //
 // M: shared memory, row r at M + r * ld, columns 0..n-1 (n <= 32 * NS).
 //
-// Every loop is bounded: a phase ends at the latest when every column is
-// labelled, and an augmenting path is at most as long as the phase.  If an
-// invariant fails (it cannot in exact arithmetic) the function stops and
-// returns false instead of spinning.
+// Every loop is bounded for any input, valid or not: a phase ends at the
+// latest when every column is labelled, and an augmenting path is at most as
+// long as the phase.  If an invariant fails (it cannot for entries in range)
+// the function stops and returns false instead of spinning.
 template <int NS, bool PACK>
 __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld, int n,
                                                int (&rowOf)[NS], int (&uM)[NS], int (&v)[NS],
                                                long long &steps_out, long long &relax_out)
 {
-    constexpr unsigned kDone = 0xffffffffu;  // key of a labelled (or absent) column
+    constexpr unsigned kDone = 0x80000000u;  // key of a labelled (or absent) column
     const int lane = threadIdx.x & 31;
     bool valid[NS];
     int way[NS], dlab[NS];
@@ -244,9 +244,11 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
 
     for (int r = 0; r < n; ++r) {
         // key = distance label (+ D of its last update), packed with the column
-        // when PACK; kDone marks labelled columns: as a signed value it is below
-        // every candidate, so no relaxation touches it, and as an unsigned value
-        // it is above every key, so no reduction picks it.
+        // when PACK; kDone = INT_MIN marks labelled columns: as a signed value no
+        // candidate is below it, so no relaxation touches it (whatever the data),
+        // and as an unsigned value it is above every valid key, so no reduction
+        // picks it while an unlabelled column remains.  Each step therefore
+        // labels a new column or ends the phase: at most n + 1 steps.
 #pragma unroll
         for (int s = 0; s < NS; ++s) key[s] = valid[s] ? 0x7fffffffu : kDone;
         int i0 = r;   // row scanned at this step
