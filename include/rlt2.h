@@ -155,9 +155,11 @@ int rlt2_work(rlt2_ctx *ctx, int64_t out[6]);
 int rlt2_stage_times(rlt2_ctx *ctx, double out[4], int *passes);
 int rlt2_reset_stage_times(rlt2_ctx *ctx);
 
-/* Device pointer of the context's stream-ordered state (for the Python binding's
- * zero-copy views): which 0 = x, 1 = y (C), 2 = z (tile-padded: row stride
- * rlt2_row_stride(N)).  Returns NULL on error. */
+/* Device pointer of the context's state: which 0 = x, 1 = y (C), 2 = z.  On
+ * the device, tile t of z holds N-2 rows (facilities p not in {i,k}) of
+ * rlt2_row_stride(N) = round_up(N, 4) ints indexed by the location q itself;
+ * columns j and n of the tile and q >= N hold no coefficient.  Returns NULL on
+ * error. */
 void *rlt2_device_state(rlt2_ctx *ctx, int which);
 int rlt2_row_stride(int N);
 

@@ -74,7 +74,7 @@ const char *rlt2_strerror(int code)
     }
 }
 
-int rlt2_row_stride(int N) { return (N - 2 + 3) & ~3; }
+int rlt2_row_stride(int N) { return (N + 3) & ~3; }
 
 static void free_ctx(rlt2_ctx *c)
 {
@@ -332,8 +332,26 @@ int rlt2_get_state(rlt2_ctx *c, int level, int32_t *host, size_t count)
         CK(cudaMemcpyAsync(host, c->yC, count * 4, cudaMemcpyDeviceToHost, c->stream));
     } else if (level == 2) {
         if (!c->z || count != (size_t)g.tiles * g.n * g.n) return RLT2_E_INVAL;
-        CK(cudaMemcpy2DAsync(host, (size_t)g.n * 4, c->z, (size_t)g.RS * 4, (size_t)g.n * 4,
-                             (size_t)g.tiles * g.n, cudaMemcpyDeviceToHost, c->stream));
+        // the store's rows are indexed by location: drop the tile's own two
+        // locations (and the padding) to reach the compact layout
+        std::vector<int32_t> tmp;
+        try {
+            tmp.resize((size_t)g.tiles * g.TS);
+        } catch (...) {
+            return RLT2_E_OOM;
+        }
+        CK(cudaMemcpyAsync(tmp.data(), c->z, tmp.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const int m = N - 1, n = g.n, W = g.W;
+        size_t o = 0;
+        for (long long t = 0; t < g.tiles; t++) {
+            const int nn = (int)(t % m), j = (int)((t / ((long long)m * m)) % N);
+            const int nl = nn + (nn >= j);
+            const int32_t *src = tmp.data() + (size_t)t * g.TS;
+            for (int r = 0; r < n; r++)
+                for (int q = 0; q < N; q++)
+                    if (q != j && q != nl) host[o++] = src[r * W + q];
+        }
     } else {
         return RLT2_E_INVAL;
     }

@@ -215,15 +215,18 @@ __device__ __forceinline__ long long warp_sum64(long long x)
 // Value range: with entries in [0, A], |u|, |v| <= A and every key <= 3A, so
 // A <= 2^29 - 1 fits int32 (PACK needs 3A < 2^25).
 //
-// M: shared memory, row r at M + r * ld, columns 0..n-1 (n <= 32 * NS).
+// M: shared memory, row r at M + r * ld (rows 0..n-1).  The n columns are the
+// indices c < width other than dead0 and dead1 (width <= 32 * NS); a column's
+// lane and slot follow its index, so ties still go to the smallest column.
 //
 // Every loop is bounded for any input, valid or not: a phase ends at the
 // latest when every column is labelled, and an augmenting path is at most as
 // long as the phase.  If an invariant fails (it cannot for entries in range)
 // the function stops and returns false instead of spinning.
 template <int NS, bool PACK>
-__device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld, int n,
-                                               int (&rowOf)[NS], int (&uM)[NS], int (&v)[NS],
+__device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld, int n, int width,
+                                               int dead0, int dead1, int (&rowOf)[NS],
+                                               int (&uM)[NS], int (&v)[NS],
                                                long long &steps_out, long long &relax_out)
 {
     constexpr unsigned kDone = 0x80000000u;  // key of a labelled (or absent) column
@@ -233,7 +236,8 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
     unsigned key[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        valid[s] = lane + 32 * s < n;
+        const int c = lane + 32 * s;
+        valid[s] = c < width && c != dead0 && c != dead1;
         rowOf[s] = -1;
         uM[s] = 0;
         v[s] = 0;
@@ -345,27 +349,31 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
 
 // S = sum of the row and column potentials = cost of the assignment.
 template <int NS>
-__device__ __forceinline__ long long lap_value(int n, const int (&uM)[NS], const int (&v)[NS])
+__device__ __forceinline__ long long lap_value(int width, int dead0, int dead1, const int (&uM)[NS],
+                                               const int (&v)[NS])
 {
     const int lane = threadIdx.x & 31;
     long long s = 0;
 #pragma unroll
-    for (int k = 0; k < NS; ++k)
-        if (lane + 32 * k < n) s += (long long)uM[k] + v[k];
+    for (int k = 0; k < NS; ++k) {
+        const int c = lane + 32 * k;
+        if (c < width && c != dead0 && c != dead1) s += (long long)uM[k] + v[k];
+    }
     return warp_sum64(s);
 }
 
 // Row potentials by row index into shared uRow[n] (and the column of each row
 // into colOf[n] when non-null); the caller syncs the warp afterwards.
 template <int NS>
-__device__ __forceinline__ void scatter_rows(int n, const int (&rowOf)[NS], const int (&uM)[NS],
+__device__ __forceinline__ void scatter_rows(int n, int width, int dead0, int dead1,
+                                             const int (&rowOf)[NS], const int (&uM)[NS],
                                              int *uRow, int *colOf)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
         const int c = lane + 32 * k;
-        if (c < n && rowOf[k] >= 0 && rowOf[k] < n) {
+        if (c < width && c != dead0 && c != dead1 && rowOf[k] >= 0 && rowOf[k] < n) {
             uRow[rowOf[k]] = uM[k];
             if (colOf) colOf[rowOf[k]] = c;
         }

@@ -7,14 +7,17 @@ namespace rlt2 {
 
 struct DevStatus;
 
-// Geometry of the tile store of D: tile t holds the (N-2) x (N-2) submatrix
-// D_ijkn, rows padded to a multiple of 4 ints so that every row and tile starts
-// on a 16-byte boundary.
+// Geometry of the tile store of D.  Tile t = ((i*N + j)*(N-1) + k')*(N-1) + n'
+// holds the submatrix D_ijkn: its N-2 rows are the facilities p not in {i,k}
+// (ascending) and its columns are indexed by the location q itself, W =
+// round_up(N, 4) of them; columns j and n (and q >= N) carry no coefficient.
+// Every row starts on a 16-byte boundary and any 4 consecutive locations
+// 4c..4c+3 form one aligned 16-byte piece of a row.
 struct Geom {
     int N;
-    int n;            // N - 2: tile size
-    int RS;           // row stride of a tile, ints
-    int TS;           // tile stride, ints (n * RS)
+    int n;            // N - 2: rows (and coefficients per row) of a tile
+    int W;            // row width in ints, round_up(N, 4)
+    int TS;           // tile stride, ints (n * W)
     long long tiles;  // N^2 (N-1)^2
 };
 
@@ -23,8 +26,8 @@ inline Geom make_geom(int N)
     Geom g;
     g.N = N;
     g.n = N - 2;
-    g.RS = (g.n + 3) & ~3;
-    g.TS = g.n * g.RS;
+    g.W = (N + 3) & ~3;
+    g.TS = g.n * g.W;
     g.tiles = (long long)N * N * (N - 1) * (N - 1);
     return g;
 }

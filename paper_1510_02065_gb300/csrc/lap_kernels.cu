@@ -1,10 +1,11 @@
 // lap_kernels.cu -- the cost concentrations of Algorithm 1 (Sec. 4.1) on sm_103a.
 //
 //   dlap_kernel   concentration D -> C: one Hungarian LAP of size N-2 per tile
-//                 D_ijkn; tiles are streamed into shared memory by 1-D bulk
-//                 copies (cp.async.bulk, double-buffered per warp, work taken
-//                 from a global counter); the residual tile is written back in
-//                 place and S goes to yS.
+//                 D_ijkn; each tile (N-2 rows x W location columns, two of
+//                 them without coefficient) comes into shared memory by one
+//                 1-D bulk copy (cp.async.bulk completing on an mbarrier), work
+//                 is taken from a global counter, the residual tile is written
+//                 back in place and S goes to yS.
 //   clap_kernel   transfer between complementary costs of C fused with the
 //                 concentration C -> B (N^2 LAPs of size N-1).
 //   xlap_kernel   concentration B -> LB (one LAP of size N), LB += LB', history,
@@ -28,12 +29,13 @@ constexpr int kBatchWarps = 4;
 // one; NBUF = 1: one tile buffer per warp, twice the warps per SM.
 template <int NS, bool PACK, int NBUF>
 __global__ void __launch_bounds__(kDlapWarps * 32)
-    dlap_kernel(PassState p, int n, int RS, long long ntiles)
+    dlap_kernel(PassState p, int N, int W, long long ntiles, FastDiv fmm, FastDiv fm, FastDiv fN)
 {
     if (*p.stop) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int TS = n * RS;
+    const int n = N - 2, m = N - 1;
+    const int TS = n * W;
     const unsigned bytes = (unsigned)TS * 4u;
     int *bufs = reinterpret_cast<int *>(smem) + (size_t)warp * NBUF * TS;
     unsigned char *tail = smem + (size_t)kDlapWarps * NBUF * TS * 4;
@@ -77,10 +79,16 @@ __global__ void __launch_bounds__(kDlapWarps * 32)
         parity ^= 1u << cur;
         const int *buf = bufs + cur * TS;
 
+        // the tile's own locations j and n are the columns without coefficient
+        const unsigned ij = fdiv((unsigned)t, fmm);
+        const unsigned rem = (unsigned)t - ij * (unsigned)(m * m);
+        const int nn = (int)(rem - fdiv(rem, fm) * (unsigned)m);
+        const int j = (int)(ij - fdiv(ij, fN) * (unsigned)N);
+        const int nl = nn + (nn >= j);
         int rowOf[NS], uM[NS], v[NS];
-        if (!warp_hungarian<NS, PACK>(buf, RS, n, rowOf, uM, v, steps, relax) && lane == 0)
+        if (!warp_hungarian<NS, PACK>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
             atomicOr(&p.status->err, kDevInternal);
-        scatter_rows<NS>(n, rowOf, uM, uRow, nullptr);
+        scatter_rows<NS>(n, N, j, nl, rowOf, uM, uRow, nullptr);
         __syncwarp();
         int *g = p.z + t * TS;
         for (int r = 0; r < n; ++r) {
@@ -88,10 +96,10 @@ __global__ void __launch_bounds__(kDlapWarps * 32)
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 const int c = lane + 32 * s;
-                if (c < RS) g[r * RS + c] = c < n ? buf[r * RS + c] - ur - v[s] : 0;
+                if (c < W) g[r * W + c] = (c < N && c != j && c != nl) ? buf[r * W + c] - ur - v[s] : 0;
             }
         }
-        const long long S = lap_value<NS>(n, uM, v);
+        const long long S = lap_value<NS>(N, j, nl, uM, v);
         if (lane == 0) p.yS[t] = (int)S;
         ++laps;
         __syncwarp();
@@ -143,9 +151,9 @@ __global__ void __launch_bounds__(kClapWarps * 32) clap_kernel(PassState p, int 
         }
         __syncwarp();
         int rowOf[NS], uM[NS], v[NS];
-        if (!warp_hungarian<NS, PACK>(buf, m, m, rowOf, uM, v, steps, relax) && lane == 0)
+        if (!warp_hungarian<NS, PACK>(buf, m, m, m, -1, -1, rowOf, uM, v, steps, relax) && lane == 0)
             atomicOr(&p.status->err, kDevInternal);
-        scatter_rows<NS>(m, rowOf, uM, uRow, nullptr);
+        scatter_rows<NS>(m, m, -1, -1, rowOf, uM, uRow, nullptr);
         __syncwarp();
         for (int r = 0; r < m; ++r) {
             const int ur = uRow[r];
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(kClapWarps * 32) clap_kernel(PassState p, int 
                 if (c < m) p.yC[base + r * m + c] = buf[r * m + c] - ur - v[s];
             }
         }
-        const long long S = lap_value<NS>(m, uM, v);
+        const long long S = lap_value<NS>(m, -1, -1, uM, v);
         if (lane == 0) p.x[prob] = (int)S;
         ++laps;
         __syncwarp();
@@ -181,9 +189,9 @@ __global__ void __launch_bounds__(32) xlap_kernel(PassState p, int N)
     __syncwarp();
     long long steps = 0, relax = 0;
     int rowOf[NS], uM[NS], v[NS];
-    if (!warp_hungarian<NS, PACK>(buf, N, N, rowOf, uM, v, steps, relax) && lane == 0)
+    if (!warp_hungarian<NS, PACK>(buf, N, N, N, -1, -1, rowOf, uM, v, steps, relax) && lane == 0)
         atomicOr(&p.status->err, kDevInternal);
-    scatter_rows<NS>(N, rowOf, uM, uRow, nullptr);
+    scatter_rows<NS>(N, N, -1, -1, rowOf, uM, uRow, nullptr);
     __syncwarp();
     for (int r = 0; r < N; ++r) {
         const int ur = uRow[r];
@@ -193,7 +201,7 @@ __global__ void __launch_bounds__(32) xlap_kernel(PassState p, int N)
             if (c < N) p.x[r * N + c] = buf[r * N + c] - ur - v[s];
         }
     }
-    const long long S = lap_value<NS>(N, uM, v);
+    const long long S = lap_value<NS>(N, -1, -1, uM, v);
     if (lane == 0) {
         const long long lb = *p.LB + S;
         *p.LB = lb;
@@ -245,12 +253,12 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
         long long steps = 0, relax = 0;
         int rowOf[NS], uM[NS], v[NS];
         const bool fine = mx < (1 << 25) / 3
-                              ? warp_hungarian<NS, true>(buf, n, n, rowOf, uM, v, steps, relax)
-                              : warp_hungarian<NS, false>(buf, n, n, rowOf, uM, v, steps, relax);
+                              ? warp_hungarian<NS, true>(buf, n, n, n, -1, -1, rowOf, uM, v, steps, relax)
+                              : warp_hungarian<NS, false>(buf, n, n, n, -1, -1, rowOf, uM, v, steps, relax);
         if (!fine && lane == 0) atomicOr(&status->err, kDevInternal);
-        scatter_rows<NS>(n, rowOf, uM, uRow, colOf);
+        scatter_rows<NS>(n, n, -1, -1, rowOf, uM, uRow, colOf);
         __syncwarp();
-        const long long s = lap_value<NS>(n, uM, v);
+        const long long s = lap_value<NS>(n, -1, -1, uM, v);
         for (int e = lane; e < n; e += 32) {
             if (assign) assign[(size_t)prob * n + e] = colOf[e];
             if (uo) uo[(size_t)prob * n + e] = uRow[e];
@@ -288,14 +296,16 @@ static cudaError_t dlap_go(const Geom &g, const PassState &p, int sm_count, cuda
     long long grid = (long long)per_sm * sm_count;
     const long long need = (g.tiles + kDlapWarps - 1) / kDlapWarps;
     if (grid > need) grid = need;
-    k<<<(unsigned)grid, kDlapWarps * 32, smem, s>>>(p, g.n, g.RS, g.tiles);
+    const int m = g.N - 1;
+    k<<<(unsigned)grid, kDlapWarps * 32, smem, s>>>(p, g.N, g.W, g.tiles, make_fastdiv(m * m),
+                                                     make_fastdiv(m), make_fastdiv(g.N));
     return cudaGetLastError();
 }
 
 // The work counter is reset by the fused pass over D, which precedes this kernel.
 cudaError_t launch_dlap(const Geom &g, const PassState &p, int sm_count, cudaStream_t s)
 {
-    if (g.n <= 32) return p.pack ? dlap_go<1, true>(g, p, sm_count, s) : dlap_go<1, false>(g, p, sm_count, s);
+    if (g.N <= 32) return p.pack ? dlap_go<1, true>(g, p, sm_count, s) : dlap_go<1, false>(g, p, sm_count, s);
     return p.pack ? dlap_go<2, true>(g, p, sm_count, s) : dlap_go<2, false>(g, p, sm_count, s);
 }
 

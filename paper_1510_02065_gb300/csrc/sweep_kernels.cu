@@ -17,13 +17,13 @@
 //   kind 2  d_ijpqkn  tile (i,j,p,q) row k      kind 5  d_pqijkn  tile (p,q,i,j) row k
 //   kind 3  d_knijpq  tile (k,n,i,j) row p      kind 6  d_pqknij  tile (p,q,k,n) row i
 // Kinds 1, 2, 3, 5 are whole tile rows owned by this CTA; kinds 4 and 6 are the
-// JC columns j of rows shared with the CTAs of the other chunks.  The CTA stages
-// them in shared memory with 16-byte loads, splits every class, and writes the
-// rows back.  With i < k < p the lexicographic ranks of kinds 1..6 are 0..5.
-// Full rows move by 1-D bulk copies (cp.async.bulk) completing on one
-// mbarrier; the column pieces by 4-byte cp.async; all loads of a CTA are in
-// flight at once, and two CTAs per SM overlap one's copies with the other's
-// arithmetic.
+// JC columns j of rows shared with the CTAs of the other chunks.  Tile columns
+// are indexed by location, so those JC columns are one aligned piece (16 bytes
+// for JC = 4) of the row.  The CTA stages everything in shared memory with
+// asynchronous copies (cp.async, all in flight at once), splits every class,
+// and writes rows and pieces back with 16-byte stores; two CTAs per SM overlap
+// one's copies with the other's arithmetic.  With i < k < p the lexicographic
+// ranks of kinds 1..6 are 0..5.
 #include "device.cuh"
 #include "kernels.h"
 
@@ -45,54 +45,42 @@ __device__ __forceinline__ int share(int x, const FastDiv &fm, int t)
     return q + (t < x - q * (int)fm.d ? 1 : 0);
 }
 
-// r-th element of [0, N) without a and b (a != b)
-__device__ __forceinline__ int skip2(int r, int a, int b)
-{
-    const int lo = min(a, b), hi = max(a, b);
-    r += (r >= lo);
-    r += (r >= hi);
-    return r;
-}
-
-// Shared-memory layout of one work unit (offsets in ints).  Full tile rows
-// (kinds 1, 3, 2, 5) keep the global row stride RS so that they move by bulk
-// copies; the JC-column pieces of kinds 4 and 6 use an odd row pitch.
+// Shared-memory layout of one work unit (offsets in ints, all 16-byte aligned).
+// Rows of kinds 1 and 3 are indexed (jj, location), pitch W; rows of kinds 2
+// and 5 likewise with pitch W + 4 (read by column); the JC-location pieces of
+// kinds 4 and 6 are indexed (a, l) with an odd number of pieces per a.
 struct P1Layout {
-    int n, m, JCp, P4;
-    int BAR, A1, A3, A2, A5, A4, A6, H1, H3, H2, H5, H4, H6, total;
+    int S13, S25, P46, H6p;
+    int A1, A3, A2, A5, A4, A6, H1, H3, H2, H5, H4, H6, total;
 };
 
-__host__ __device__ inline P1Layout p1_layout(int N, int JC, int RS)
+__host__ __device__ inline int up4(int x) { return (x + 3) & ~3; }
+
+__host__ __device__ inline P1Layout p1_layout(int N, int W, int JC)
 {
     P1Layout L;
-    L.n = N - 2;
-    L.m = N - 1;
-    L.JCp = JC | 1;
-    L.P4 = L.m * L.JCp;
-    if (!(L.P4 & 1)) L.P4 += 1;
+    L.S13 = W;
+    L.S25 = W + 4;
+    L.P46 = JC * (N | 1);
+    L.H6p = N | 1;
     int o = 0;
-    L.BAR = o; o += 4;  // one mbarrier, 16-byte slot
-    L.A1 = o; o += JC * L.m * RS;
-    L.A3 = o; o += JC * L.m * RS;
-    L.A2 = o; o += JC * L.m * RS;
-    L.A5 = o; o += JC * L.m * RS;
-    L.A4 = o; o += N * L.P4;
-    L.A6 = o; o += N * L.P4;
-    L.H1 = o; o += JC * L.m;
-    L.H3 = o; o += JC * L.m;
-    L.H2 = o; o += JC * L.m;
-    L.H5 = o; o += JC * L.m;
-    L.H4 = o; o += N * L.m;
-    L.H6 = o; o += N * L.m;
+    L.A1 = o; o += JC * N * L.S13;
+    L.A3 = o; o += JC * N * L.S13;
+    L.A2 = o; o += JC * N * L.S25;
+    L.A5 = o; o += JC * N * L.S25;
+    L.A4 = o; o += up4(N * L.P46);
+    L.A6 = o; o += up4(N * L.P46);
+    L.H1 = o; o += up4(JC * N);
+    L.H3 = o; o += up4(JC * N);
+    L.H2 = o; o += up4(JC * N);
+    L.H5 = o; o += up4(JC * N);
+    L.H4 = o; o += up4(N * N);
+    L.H6 = o; o += up4(N * L.H6p);
     L.total = o;
     return L;
 }
 
-size_t p1_smem_bytes(int N, int JC)
-{
-    const int RS = (N - 2 + 3) & ~3;
-    return (size_t)p1_layout(N, JC, RS).total * 4;
-}
+size_t p1_smem_bytes(int N, int JC) { return (size_t)p1_layout(N, up4(N), JC).total * 4; }
 
 int p1_chunk(int N)
 {
@@ -100,171 +88,155 @@ int p1_chunk(int N)
     return 1;
 }
 
-// Tile and tile row of the full rows: kind q (0: kind 1, 1: kind 3, 2: kind 2,
-// 3: kind 5), location j of the smallest facility, other location l.
-__device__ __forceinline__ void full_row(int q, int N, int i, int k, int pp, int j, int l, int &t,
+// Tile and tile row of a full row of kind q (0: kind 1, 1: kind 3, 2: kind 2,
+// 3: kind 5), location j of the smallest facility, other location x.
+__device__ __forceinline__ void full_row(int q, int N, int i, int k, int pp, int j, int x, int &t,
                                          int &row)
 {
-    if (q == 0) { t = tidx_n(N, i, j, k, l); row = pp - 2; }        // d_ijklpq: tile (i,j,k,l), row p
-    else if (q == 1) { t = tidx_n(N, k, l, i, j); row = pp - 2; }   // d_klijpq: tile (k,l,i,j), row p
-    else if (q == 2) { t = tidx_n(N, i, j, pp, l); row = k - 1; }   // d_ijplkn: tile (i,j,p,l), row k
-    else { t = tidx_n(N, pp, l, i, j); row = k - 1; }               // d_plijkn: tile (p,l,i,j), row k
+    if (q == 0) { t = tidx_n(N, i, j, k, x); row = pp - 2; }        // d_ijkxpq: tile (i,j,k,x), row p
+    else if (q == 1) { t = tidx_n(N, k, x, i, j); row = pp - 2; }   // d_kxijpq: tile (k,x,i,j), row p
+    else if (q == 2) { t = tidx_n(N, i, j, pp, x); row = k - 1; }   // d_ijpxkn: tile (i,j,p,x), row k
+    else { t = tidx_n(N, pp, x, i, j); row = k - 1; }               // d_pxijkn: tile (p,x,i,j), row k
 }
 
 template <int JC>
+__device__ __forceinline__ void cp_async_piece(void *dst, const void *src)
+{
+    if constexpr (JC == 4)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    else if constexpr (JC == 2)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+template <int JC>
+__device__ __forceinline__ void copy_piece(int *dst, const int *src)
+{
+    if constexpr (JC == 4) *reinterpret_cast<int4 *>(dst) = *reinterpret_cast<const int4 *>(src);
+    else if constexpr (JC == 2) *reinterpret_cast<int2 *>(dst) = *reinterpret_cast<const int2 *>(src);
+    else *dst = *src;
+}
+
+// fN divides by N, fW4 by W/4, fn by N-2; yS holds c' (C plus the spread of B) per tile
+template <int JC>
 __global__ void __launch_bounds__(kP1Threads, 2)
-    p1_kernel(PassState p, int N, int RS, const int4 *__restrict__ triples, int nchunks,
-              FastDiv fm, FastDiv fn)
-// fm divides by N-1, fn by N-2; yS holds c' (C plus the spread of B) per tile
+    p1_kernel(PassState p, int N, int W, const int4 *__restrict__ triples, int nchunks,
+              FastDiv fN, FastDiv fW4, FastDiv fn)
 {
     if (*p.stop) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.counter = 0;  // work counter of the D -> C sweep
     extern __shared__ __align__(128) int sm[];
-    const P1Layout L = p1_layout(N, JC, RS);
-    const int n = L.n, m = L.m;
-    const size_t TS = (size_t)n * RS;
+    const P1Layout L = p1_layout(N, W, JC);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t TS = (size_t)(N - 2) * W;
+    const int W4 = W >> 2;
     const int4 tr = triples[blockIdx.x / nchunks];
     const int i = tr.x, k = tr.y, pp = tr.z;
     const int j0 = (blockIdx.x % nchunks) * JC;
     const int jc = min(JC, N - j0);
     const int *__restrict__ yS = p.yS;
     int *__restrict__ z = p.z;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.BAR);
-    const unsigned rowBytes = (unsigned)RS * 4u;
+    const int NN = N * N;
 
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 4 * 32);
-        fence_mbar_init();
+    // ---- loads, all in flight at once: full rows in 16-byte pieces, then the
+    // JC-location pieces of kinds 4 and 6 (one aligned copy each)
+    for (int e = threadIdx.x; e < 4 * JC * N * W4; e += kP1Threads) {
+        const int rowid = (int)fdiv((unsigned)e, fW4), h = e - rowid * W4;
+        const int qj = (int)fdiv((unsigned)rowid, fN), x = rowid - qj * N;
+        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
+        if (jj >= jc || x == j) continue;
+        int t, row;
+        full_row(q, N, i, k, pp, j, x, t, row);
+        const int base = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
+        const int pitch = q < 2 ? L.S13 : L.S25;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(sm + base + (jj * N + x) * pitch + 4 * h)),
+                     "l"(z + t * TS + (size_t)row * W + 4 * h)
+                     : "memory");
     }
+    for (int e = threadIdx.x; e < 2 * NN; e += kP1Threads) {
+        const int kind = e >= NN, r2 = e - kind * NN;
+        const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
+        if (l == a) continue;
+        // kind 4: row i of tile (k,a,p,l); kind 6: row i of tile (p,a,k,l)
+        const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
+        cp_async_piece<JC>(sm + (kind ? L.A6 : L.A4) + a * L.P46 + l * JC,
+                           z + t * TS + (size_t)i * W + j0);
+    }
+
+    // ---- shares while the copies fly: c' of the tile spread over its rows
+    for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
+        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
+        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
+        if (jj >= jc || x == j) continue;
+        int t, row;
+        full_row(q, N, i, k, pp, j, x, t, row);
+        const int hb = q == 0 ? L.H1 : q == 1 ? L.H3 : q == 2 ? L.H2 : L.H5;
+        sm[hb + jj * N + x] = share(yS[t], fn, row);
+    }
+    for (int e = threadIdx.x; e < 2 * NN; e += kP1Warps * 32) {
+        const int kind = e >= NN, r2 = e - kind * NN;
+        const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
+        if (l == a) continue;
+        const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
+        sm[(kind ? L.H6 + a * L.H6p : L.H4 + a * N) + l] = share(yS[t], fn, i);
+    }
+
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
 
-    // ---- issue every load: full rows by bulk copies (warps 0-3, one kind
-    // each), the JC-column pieces of kinds 4 and 6 by 4-byte cp.async
-    if (warp < 4) {
-        const int q = warp;
-        const int ab = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
-        const int mine = lane < m ? (m - 1 - lane) / 32 + 1 : 0;
-        mbar_arrive_expect_tx(bar, (unsigned)(jc * mine) * rowBytes);
-        for (int jj = 0; jj < jc; ++jj) {
-            const int j = j0 + jj;
-            for (int o = lane; o < m; o += 32) {
-                const int l = o + (o >= j);
-                int t, row;
-                full_row(q, N, i, k, pp, j, l, t, row);
-                bulk_load_tx(sm + ab + (jj * m + o) * RS, z + t * TS + row * RS, rowBytes, bar);
-            }
-        }
-    } else {
-        // one thread per row (a, o): row i of tile (k,a,p,l) (kind 4) or of
-        // tile (p,a,k,l) (kind 6); for a fixed a these tiles are consecutive
-        const int tw = (warp - 4) * 32 + lane, nt = (kP1Warps - 4) * 32;
-        for (int ro = tw; ro < 2 * N * m; ro += nt) {
-            const int kind = ro >= N * m;
-            const int r2 = ro - kind * N * m;
-            const int a = (int)fdiv((unsigned)r2, fm), o = r2 - a * m;
-            const int l = o + (o >= a);
-            const int t = (kind ? ((pp * N + a) * m + k) * m : ((k * N + a) * m + pp - 1) * m) + o;
-            // the share of c' of this tile that row i receives
-            sm[(kind ? L.H6 : L.H4) + a * m + o] = share(yS[t], fn, i);
-            const int *src = z + t * TS + (size_t)i * RS;
-            int *dst = sm + (kind ? L.A6 : L.A4) + a * L.P4 + o * L.JCp;
-#pragma unroll
-            for (int jj = 0; jj < JC; ++jj) {
-                const int j = j0 + jj;
-                if (jj < jc && j != a && j != l) cp_async4(dst + jj, src + (j - (j > a) - (j > l)));
-            }
-        }
-    }
-
-    // ---- shares of the full rows while the copies fly: c' of the tile (c plus
-    // the share of b, computed by the spread kernel into yS) over the tile's rows
-    for (int q = warp; q < 4 * JC; q += kP1Warps) {
-        const int kind = q / JC, jj = q % JC, j = j0 + jj;
-        if (jj >= jc) continue;
-        const int hb = kind == 0 ? L.H1 : kind == 1 ? L.H3 : kind == 2 ? L.H2 : L.H5;
-        for (int o = lane; o < m; o += 32) {
-            const int l = o + (o >= j);
-            int t, row;
-            full_row(kind, N, i, k, pp, j, l, t, row);
-            sm[hb + jj * m + o] = share(yS[t], fn, row);
-        }
-    }
-
-    cp_async_wait_all();
-    const bool ok = __syncthreads_and(mbar_wait(bar, 0));
-    if (!ok) {
-        if (threadIdx.x == 0) atomicOr(&p.status->err, kDevTimeout);
-        mbar_wait(bar, 0);   // let the copies in flight land (bounded), then leave
-        return;
-    }
-
     // ---- split every class {(i,j),(k,nn),(p,qq)}, j in the chunk: one warp
-    // per (j, nn), lanes over the column s of qq in the kind-1 row
+    // per (j, nn), lanes over qq
     for (int jj = 0; jj < jc; ++jj) {
         const int j = j0 + jj;
-        for (int o = warp; o < m; o += kP1Warps) {
-            const int nn = o + (o >= j);
-            const int h1 = sm[L.H1 + jj * m + o], h3 = sm[L.H3 + jj * m + o];
-            int *r1 = sm + L.A1 + (jj * m + o) * RS;
-            int *r3 = sm + L.A3 + (jj * m + o) * RS;
-            for (int s = lane; s < n; s += 32) {
-                const int qq = skip2(s, j, nn);
-                const int q1 = qq - (qq > j);          // rank of qq among locations != j
-                const int s2 = o - (nn > qq);          // column of nn in tiles (.,j,.,qq)/(.,qq,.,j)
-                const int q4 = qq - (qq > nn);         // rank of qq among locations != nn
-                const int n6 = nn - (nn > qq);         // rank of nn among locations != qq
-                int *a2 = sm + L.A2 + (jj * m + q1) * RS + s2;
-                int *a5 = sm + L.A5 + (jj * m + q1) * RS + s2;
-                int *a4 = sm + L.A4 + nn * L.P4 + q4 * L.JCp + jj;
-                int *a6 = sm + L.A6 + qq * L.P4 + n6 * L.JCp + jj;
-                const int T = r1[s] + h1 + *a2 + sm[L.H2 + jj * m + q1] + r3[s] + h3 +
-                              *a4 + sm[L.H4 + nn * m + q4] + *a5 + sm[L.H5 + jj * m + q1] +
-                              *a6 + sm[L.H6 + qq * m + n6];
+        for (int nn = warp; nn < N; nn += kP1Warps) {
+            if (nn == j) continue;
+            const int h1 = sm[L.H1 + jj * N + nn], h3 = sm[L.H3 + jj * N + nn];
+            int *r1 = sm + L.A1 + (jj * N + nn) * L.S13;
+            int *r3 = sm + L.A3 + (jj * N + nn) * L.S13;
+            int *c2 = sm + L.A2 + jj * N * L.S25 + nn;    // column nn of the kind-2 rows
+            int *c5 = sm + L.A5 + jj * N * L.S25 + nn;
+            int *r4 = sm + L.A4 + nn * L.P46 + jj;        // pieces (nn, qq)
+            int *c6 = sm + L.A6 + nn * JC + jj;           // pieces (qq, nn)
+            const int *h2 = sm + L.H2 + jj * N, *h5 = sm + L.H5 + jj * N;
+            const int *h4 = sm + L.H4 + nn * N, *h6 = sm + L.H6 + nn;
+            for (int qq = lane; qq < N; qq += 32) {
+                if (qq == j || qq == nn) continue;
+                int *a2 = c2 + qq * L.S25, *a5 = c5 + qq * L.S25;
+                int *a4 = r4 + qq * JC, *a6 = c6 + qq * L.P46;
+                const int T = r1[qq] + h1 + *a2 + h2[qq] + r3[qq] + h3 + *a4 + h4[qq] + *a5 +
+                              h5[qq] + *a6 + h6[qq * L.H6p];
                 const int q6 = T / 6, rm = T - 6 * q6;
-                r1[s] = q6 + (0 < rm);   // ranks: d_ijknpq 0, d_ijpqkn 1, d_knijpq 2,
-                *a2 = q6 + (1 < rm);     //        d_knpqij 3, d_pqijkn 4, d_pqknij 5
-                r3[s] = q6 + (2 < rm);
+                r1[qq] = q6 + (0 < rm);   // ranks: d_ijknpq 0, d_ijpqkn 1, d_knijpq 2,
+                *a2 = q6 + (1 < rm);      //        d_knpqij 3, d_pqijkn 4, d_pqknij 5
+                r3[qq] = q6 + (2 < rm);
                 *a4 = q6 + (3 < rm);
                 *a5 = q6 + (4 < rm);
                 *a6 = q6 + (5 < rm);
             }
         }
     }
-    fence_proxy_async_smem();
     __syncthreads();
 
-    // ---- write back: full rows by bulk stores, column pieces by plain stores
-    if (warp < 4) {
-        const int q = warp;
-        const int ab = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
-        for (int jj = 0; jj < jc; ++jj) {
-            const int j = j0 + jj;
-            for (int o = lane; o < m; o += 32) {
-                const int l = o + (o >= j);
-                int t, row;
-                full_row(q, N, i, k, pp, j, l, t, row);
-                bulk_store(z + t * TS + row * RS, sm + ab + (jj * m + o) * RS, rowBytes);
-            }
-        }
-        bulk_commit();
-        bulk_wait_read_all();
-    } else {
-        const int tw = (warp - 4) * 32 + lane, nt = (kP1Warps - 4) * 32;
-        for (int ro = tw; ro < 2 * N * m; ro += nt) {
-            const int kind = ro >= N * m;
-            const int r2 = ro - kind * N * m;
-            const int a = (int)fdiv((unsigned)r2, fm), o = r2 - a * m;
-            const int l = o + (o >= a);
-            const int t = (kind ? ((pp * N + a) * m + k) * m : ((k * N + a) * m + pp - 1) * m) + o;
-            int *dst = z + t * TS + (size_t)i * RS;
-            const int *src = sm + (kind ? L.A6 : L.A4) + a * L.P4 + o * L.JCp;
-#pragma unroll
-            for (int jj = 0; jj < JC; ++jj) {
-                const int j = j0 + jj;
-                if (jj < jc && j != a && j != l) dst[j - (j > a) - (j > l)] = src[jj];
-            }
-        }
+    // ---- write back: 16-byte stores of whole rows and pieces
+    for (int e = threadIdx.x; e < 4 * JC * N * W4; e += kP1Threads) {
+        const int rowid = (int)fdiv((unsigned)e, fW4), h = e - rowid * W4;
+        const int qj = (int)fdiv((unsigned)rowid, fN), x = rowid - qj * N;
+        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
+        if (jj >= jc || x == j) continue;
+        int t, row;
+        full_row(q, N, i, k, pp, j, x, t, row);
+        const int base = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
+        const int pitch = q < 2 ? L.S13 : L.S25;
+        *reinterpret_cast<int4 *>(z + t * TS + (size_t)row * W + 4 * h) =
+            *reinterpret_cast<const int4 *>(sm + base + (jj * N + x) * pitch + 4 * h);
+    }
+    for (int e = threadIdx.x; e < 2 * NN; e += kP1Threads) {
+        const int kind = e >= NN, r2 = e - kind * NN;
+        const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
+        if (l == a) continue;
+        const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
+        copy_piece<JC>(z + t * TS + (size_t)i * W + j0, sm + (kind ? L.A6 : L.A4) + a * L.P46 + l * JC);
     }
 }
 
@@ -341,8 +313,8 @@ static cudaError_t p1_go(const Geom &g, const PassState &p, const int4 *triples,
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nchunks = (g.N + JC - 1) / JC;
-    k<<<ntriples * nchunks, kP1Threads, smem, s>>>(p, g.N, g.RS, triples, nchunks,
-                                                    make_fastdiv(g.N - 1), make_fastdiv(g.N - 2));
+    k<<<ntriples * nchunks, kP1Threads, smem, s>>>(p, g.N, g.W, triples, nchunks, make_fastdiv(g.N),
+                                                    make_fastdiv(g.W / 4), make_fastdiv(g.N - 2));
     return cudaGetLastError();
 }
 

@@ -34,8 +34,8 @@ def test_strerror_and_defaults(L):
     assert "overflow" in rlt2.rlt2_strerror(rlt2.RLT2_E_OVERFLOW) or "int32" in rlt2.rlt2_strerror(-3)
     o = rlt2.rlt2_default_opts()
     assert o.use_graph == 1 and o.max_iters == 65536 and o.rlt1_only == 0
-    assert rlt2.rlt2_row_stride(30) == 28 and rlt2.rlt2_row_stride(20) == 20
-    assert rlt2.rlt2_row_stride(35) == 36
+    assert rlt2.rlt2_row_stride(30) == 32 and rlt2.rlt2_row_stride(20) == 20
+    assert rlt2.rlt2_row_stride(35) == 36 and rlt2.rlt2_row_stride(3) == 4
 
 
 def _create_rc(L, F, D, N, Bl=None):
