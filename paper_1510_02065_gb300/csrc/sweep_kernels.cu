@@ -84,6 +84,9 @@ size_t p1_smem_bytes(int N, int JC) { return (size_t)p1_layout(N, up4(N), JC).to
 
 int p1_chunk(int N)
 {
+#ifdef RLT2_P1_JC
+    if (p1_smem_bytes(N, RLT2_P1_JC) <= 200 * 1024) return RLT2_P1_JC;  // build-time override
+#endif
     for (int jc : {4, 2}) if (p1_smem_bytes(N, jc) <= 110 * 1024) return jc;
     return 1;
 }
