@@ -183,6 +183,31 @@ int rlt2_row_stride(int N);
 int rlt2_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
                    int32_t *u, int32_t *v, int64_t *work, void *stream);
 
+/*
+ * rlt2_lap_batch_static -- rlt2_lap_batch for callers that must not let a
+ * library allocate device memory (the paper has no counterpart to this call).
+ * Such callers hand all device memory to one owning allocator, run under a
+ * hard memory budget, or cannot afford an allocation's latency or failure in
+ * the middle of their work; rlt2_lap_batch would allocate a small status block
+ * on every call.  This variant keeps that block (48 bytes: the kernel's error
+ * bits and work counters) in a fixed array of the library's own device memory,
+ * one per GPU, held from the library's loading until the process exits.
+ *
+ * Arguments, results and errors are those of rlt2_lap_batch; n beyond
+ * RLT2_LAP_STATIC_MAX_N is rejected with RLT2_E_INVAL.  The call allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) for that device; make it before any stream
+ *     capture on that device.
+ *   - Every call on a device reuses the same block and clears it first; two
+ *     calls whose work overlaps on the GPU (different streams, or host threads
+ *     calling at once) race on it, so serialise them.
+ *   - Synchronises the stream, like rlt2_lap_batch.
+ */
+#define RLT2_LAP_STATIC_MAX_N 64
+int rlt2_lap_batch_static(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
+                          int32_t *u, int32_t *v, int64_t *work, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,7 @@ def lib():
         "rlt2_device_state": (_vp, [_vp, C.c_int]),
         "rlt2_row_stride": (C.c_int, [C.c_int]),
         "rlt2_lap_batch": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "rlt2_lap_batch_static": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -196,6 +197,17 @@ def rlt2_lap_batch(M_ptr, n, count, S_ptr, assign_ptr=0, u_ptr=0, v_ptr=0, work_
     return lib().rlt2_lap_batch(_vp(M_ptr or None), int(n), int(count), _vp(S_ptr or None),
                                 _vp(assign_ptr or None), _vp(u_ptr or None), _vp(v_ptr or None),
                                 _vp(work_ptr or None), _vp(stream or None))
+
+
+def rlt2_lap_batch_static(M_ptr, n, count, S_ptr, assign_ptr=0, u_ptr=0, v_ptr=0, work_ptr=0,
+                          stream=0):
+    """rlt2_lap_batch without any device allocation by the library (for callers
+    whose device memory all comes from their own allocator): its status block
+    lives in a fixed per-GPU array; overlapping calls on one GPU race on it."""
+    return lib().rlt2_lap_batch_static(_vp(M_ptr or None), int(n), int(count), _vp(S_ptr or None),
+                                       _vp(assign_ptr or None), _vp(u_ptr or None),
+                                       _vp(v_ptr or None), _vp(work_ptr or None),
+                                       _vp(stream or None))
 
 
 # ------------------------------------------------------------ convenience
