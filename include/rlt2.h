@@ -163,6 +163,46 @@ int rlt2_reset_stage_times(rlt2_ctx *ctx);
 void *rlt2_device_state(rlt2_ctx *ctx, int which);
 int rlt2_row_stride(int N);
 
+/* A branch-and-bound node (Sec. 6): facility fac[t] is fixed to location
+ * loc[t], t < k; the facilities and locations are distinct. */
+typedef struct {
+    int k;
+    const int32_t *fac;
+    const int32_t *loc;
+} rlt2_node;
+
+/*
+ * Residual instance of a node (host only, no GPU): free facilities and free
+ * locations renumbered in ascending order (N' = N - k), and for any completion
+ * pi' of the node
+ *   Q(full pi) = lb_const + sum_x Blin[x][pi'(x)] + sum_{x!=y} Fp[x][y] Dp[pi'(x)][pi'(y)],
+ *   Blin[x][y] = sum_t F[fx][fac t] D[ly][loc t] + F[fac t][fx] D[loc t][ly],
+ *   lb_const   = sum_{t!=t'} F[fac t][fac t'] D[loc t][loc t'].
+ * Fp, Dp, Blin: caller buffers of N'*N' int32.  Errors: RLT2_E_INVAL (bad or
+ * repeated indices), RLT2_E_OVERFLOW (a linear cost beyond int32).  Bounding
+ * (Fp, Dp, Blin, lb_const) with rlt2_create bounds the node.
+ */
+int rlt2_subproblem(const int32_t *F, const int32_t *D, int N, int k, const int32_t *fac,
+                    const int32_t *loc, int32_t *Fp, int32_t *Dp, int32_t *Blin, int64_t *lb_const);
+
+/*
+ * Bound B nodes of one instance together: `iters` passes of Algorithm 1 on
+ * each node's residual instance (cold start), every stage of every pass one
+ * kernel launch for all nodes, all passes captured into one CUDA graph and
+ * launched once.  Each node's result equals rlt2_create + rlt2_iterate(iters)
+ * on its residual instance, bit for bit.
+ *   F, D      host, N x N (the instance); nodes[B] (host); every N - k >= 3
+ *   lb_out    host, B int64: each node's LB (lb_const included)
+ *   ms_out    (may be NULL) milliseconds of device work from the first
+ *             initialisation to the last pass (CUDA events)
+ *   opts      stream (NULL: the legacy default stream); rlt1_only must be 0
+ * One device allocation holds every node's state (about 4 B * N'^2 (N'-1)^2
+ * (N'-2) * round_up(N',4) each) and is freed before returning; synchronises.
+ * Errors: as rlt2_create, per node.
+ */
+int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node *nodes, int B,
+                     int iters, const rlt2_opts *opts, int64_t *lb_out, double *ms_out);
+
 /*
  * Batched linear assignment with the library's Hungarian kernel (the LAP of
  * Sec. 4.1, solved by the method the dual ascent uses).  count independent

@@ -14,20 +14,179 @@
 
 using namespace rlt2;
 
+namespace {
+
+int cuda_code(cudaError_t e)
+{
+    if (e == cudaSuccess) return RLT2_OK;
+    if (e == cudaErrorMemoryAllocation) return RLT2_E_OOM;
+    return RLT2_E_CUDA;
+}
+
+#define CK(call)                                     \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_code(e_); \
+    } while (0)
+
+// U bounds Q(pi) - LB for every permutation pi; every reduced cost lies on some
+// pi and all are >= 0, so every cost and every class sum is <= U.
+long long guard_U(const int32_t *F, const int32_t *D, int N, const int32_t *B)
+{
+    long long sf = 0, md = 0, sb = 0;
+    for (int i = 0; i < N; i++)
+        for (int k = 0; k < N; k++)
+            if (i != k) {
+                sf += F[i * N + k];
+                md = std::max<long long>(md, D[i * N + k]);
+            }
+    if (B)
+        for (int i = 0; i < N; i++) {
+            long long mb = 0;
+            for (int j = 0; j < N; j++) mb = std::max<long long>(mb, B[i * N + j]);
+            sb += mb;
+        }
+    return sf * md + sb;
+}
+
+int check_instance(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin, long long *U)
+{
+    if (!F || !D || N < RLT2_MIN_N || N > RLT2_MAX_N) return RLT2_E_INVAL;
+    for (int e = 0; e < N * N; e++)
+        if (F[e] < 0 || D[e] < 0 || (B_lin && B_lin[e] < 0)) return RLT2_E_INVAL;
+    *U = guard_U(F, D, N, B_lin);
+    return *U > RLT2_LAP_MAX_ENTRY ? RLT2_E_OVERFLOW : RLT2_OK;
+}
+
+long long n_triples(int N) { return (long long)N * (N - 1) * (N - 2) / 6; }
+
+// Facility triples i < k < p ordered by p, then k, then i: the first C(N,3)
+// of the table for any larger N are exactly the triples of N.
+std::vector<int4> triple_table(int N)
+{
+    std::vector<int4> t;
+    for (int p = 2; p < N; p++)
+        for (int k = 1; k < p; k++)
+            for (int i = 0; i < k; i++) t.push_back(make_int4(i, k, p, 0));
+    return t;
+}
+
+// Device memory carved from one allocation (256-byte aligned pieces).
+struct Arena {
+    size_t used = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t off = used;
+        used += (bytes + 255) & ~size_t(255);
+        return off;
+    }
+};
+
+// One instance's state inside an arena (byte offsets).
+struct NodeOffsets {
+    size_t z, yS, yC, x, LB, hist, iter, stop;
+};
+
+NodeOffsets plan_node(Arena &a, int N, bool with_d, int hist_cap)
+{
+    const Geom g = make_geom(N);
+    NodeOffsets o;
+    o.z = with_d ? a.take((size_t)g.tiles * g.TS * 4) : (size_t)-1;
+    o.yS = a.take((size_t)g.tiles * 4);
+    o.yC = a.take((size_t)g.tiles * 4);
+    o.x = a.take((size_t)N * N * 4);
+    o.LB = a.take(8);
+    o.hist = a.take((size_t)hist_cap * 8);
+    o.iter = a.take(4);
+    o.stop = a.take(4);
+    return o;
+}
+
+PassState node_state(char *base, const NodeOffsets &o, int hist_cap, const rlt2_opts &opts)
+{
+    PassState p{};
+    p.z = o.z == (size_t)-1 ? nullptr : reinterpret_cast<int *>(base + o.z);
+    p.yS = reinterpret_cast<int *>(base + o.yS);
+    p.yC = reinterpret_cast<int *>(base + o.yC);
+    p.x = reinterpret_cast<int *>(base + o.x);
+    p.LB = reinterpret_cast<long long *>(base + o.LB);
+    p.hist = reinterpret_cast<long long *>(base + o.hist);
+    p.iter = reinterpret_cast<int *>(base + o.iter);
+    p.stop = reinterpret_cast<int *>(base + o.stop);
+    p.hist_cap = hist_cap;
+    p.ub = opts.ub;
+    p.min_progress = opts.min_progress;
+    return p;
+}
+
+// Copy F, D (and B_lin) of one instance to the device and run the
+// initialisation of Algorithm 1 on it.
+cudaError_t init_node(const NodeDesc &nd, const int32_t *F, const int32_t *D, const int32_t *B_lin,
+                      long long lb_const, int32_t *staging, cudaStream_t s)
+{
+    const size_t nn = (size_t)nd.N * nd.N;
+    cudaError_t e = cudaMemcpyAsync(staging, F, nn * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(staging + nn, D, nn * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && B_lin)
+        e = cudaMemcpyAsync(staging + 2 * nn, B_lin, nn * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_init(nd, staging, staging + nn, B_lin ? staging + 2 * nn : nullptr, lb_const, s);
+    return e;
+}
+
+// One pass of Algorithm 1 for the whole group.  ev: 5 events around the stages.
+cudaError_t enqueue_pass(const Group &g, int sm_count, cudaStream_t s, cudaEvent_t *ev)
+{
+    cudaError_t e;
+    auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
+    if ((e = mark(0)) != cudaSuccess) return e;
+    if (!g.rlt1_only) {
+        if ((e = launch_p1(g, s)) != cudaSuccess) return e;
+        if ((e = mark(1)) != cudaSuccess) return e;
+        if ((e = launch_dlap(g, sm_count, s)) != cudaSuccess) return e;
+    } else if ((e = mark(1)) != cudaSuccess) {
+        return e;
+    }
+    if ((e = mark(2)) != cudaSuccess) return e;
+    if ((e = launch_clap(g, s)) != cudaSuccess) return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
+    if ((e = launch_xlap(g, s)) != cudaSuccess) return e;
+    return mark(4);
+}
+
+cudaError_t capture_passes(const Group &g, int sm_count, cudaStream_t s, int passes,
+                           cudaGraph_t *graph, cudaGraphExec_t *exec)
+{
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e2 = cudaSuccess;
+    for (int t = 0; t < passes && e2 == cudaSuccess; t++) e2 = enqueue_pass(g, sm_count, s, nullptr);
+    e = cudaStreamEndCapture(s, graph);
+    if (e2 != cudaSuccess) return e2;
+    if (e != cudaSuccess) return e;
+    return cudaGraphInstantiate(exec, *graph, 0);
+}
+
+int group_status(const Group &g, cudaStream_t s)
+{
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, &g.status->err, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err & kDevTimeout) return RLT2_E_TIMEOUT;
+    if (err & kDevInternal) return RLT2_E_INTERNAL;
+    return RLT2_OK;
+}
+
+}  // namespace
+
 struct rlt2_ctx {
-    Geom g;
     rlt2_opts opts;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int sm_count = 0;
-    int *z = nullptr, *yS = nullptr, *yC = nullptr, *x = nullptr;
-    long long *LB = nullptr, *hist = nullptr;
-    int *iter = nullptr, *stop = nullptr;
-    unsigned *counter = nullptr;
-    DevStatus *status = nullptr;
-    int4 *triples = nullptr;
-    int ntriples = 0;
-    PassState ps{};
+    char *mem = nullptr;   // all device state of the context, one allocation
+    Group g{};             // a group of one instance
+    NodeDesc node{};       // host copy of that instance's descriptor
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int enqueued = 0;
@@ -36,18 +195,17 @@ struct rlt2_ctx {
     size_t ev_used = 0;
 };
 
-static int cuda_code(cudaError_t e)
+static void free_ctx(rlt2_ctx *c)
 {
-    if (e == cudaSuccess) return RLT2_OK;
-    if (e == cudaErrorMemoryAllocation) return RLT2_E_OOM;
-    return RLT2_E_CUDA;
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    cudaFree(c->mem);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
 }
-
-#define CK(call)                                  \
-    do {                                          \
-        cudaError_t e_ = (call);                  \
-        if (e_ != cudaSuccess) return cuda_code(e_); \
-    } while (0)
 
 extern "C" {
 
@@ -76,70 +234,22 @@ const char *rlt2_strerror(int code)
 
 int rlt2_row_stride(int N) { return (N + 3) & ~3; }
 
-static void free_ctx(rlt2_ctx *c)
-{
-    if (!c) return;
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->graph) cudaGraphDestroy(c->graph);
-    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
-    cudaFree(c->z);
-    cudaFree(c->yS);
-    cudaFree(c->yC);
-    cudaFree(c->x);
-    cudaFree(c->LB);
-    cudaFree(c->hist);
-    cudaFree(c->iter);
-    cudaFree(c->stop);
-    cudaFree(c->counter);
-    cudaFree(c->status);
-    cudaFree(c->triples);
-    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-    delete c;
-}
-
 void rlt2_destroy(rlt2_ctx *c) { free_ctx(c); }
-
-// U bounds Q(pi) - LB for every permutation pi; every reduced cost lies on some
-// pi and all are >= 0, so every cost and every class sum is <= U.
-static long long guard_U(const int32_t *F, const int32_t *D, int N, const int32_t *B)
-{
-    long long sf = 0, md = 0, sb = 0;
-    for (int i = 0; i < N; i++)
-        for (int k = 0; k < N; k++)
-            if (i != k) {
-                sf += F[i * N + k];
-                md = std::max<long long>(md, D[i * N + k]);
-            }
-    if (B)
-        for (int i = 0; i < N; i++) {
-            long long mb = 0;
-            for (int j = 0; j < N; j++) mb = std::max<long long>(mb, B[i * N + j]);
-            sb += mb;
-        }
-    return sf * md + sb;
-}
 
 int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin, int64_t lb_const,
                 const rlt2_opts *opts, rlt2_ctx **out)
 {
     if (!out) return RLT2_E_INVAL;
     *out = nullptr;
-    if (!F || !D || N < RLT2_MIN_N || N > RLT2_MAX_N) return RLT2_E_INVAL;
-    for (int e = 0; e < N * N; e++)
-        if (F[e] < 0 || D[e] < 0 || (B_lin && B_lin[e] < 0)) return RLT2_E_INVAL;
-    const long long U = guard_U(F, D, N, B_lin);
-    if (U > RLT2_LAP_MAX_ENTRY) return RLT2_E_OVERFLOW;
+    long long U = 0;
+    int rc = check_instance(F, D, N, B_lin, &U);
+    if (rc != RLT2_OK) return rc;
 
     rlt2_ctx *c = new (std::nothrow) rlt2_ctx();
     if (!c) return RLT2_E_OOM;
     if (opts) c->opts = *opts;
     else rlt2_default_opts(&c->opts);
     if (c->opts.max_iters <= 0) c->opts.max_iters = 65536;
-    c->g = make_geom(N);
-    const Geom &g = c->g;
-
-    int rc = RLT2_OK;
     auto fail = [&](int code) {
         free_ctx(c);
         return code;
@@ -155,106 +265,58 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
             return fail(RLT2_E_CUDA);
         c->own_stream = true;
     }
-    auto A = [&](void **p, size_t bytes) {
-        cudaError_t e = cudaMalloc(p, bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            rc = cuda_code(e);
-            return false;
-        }
-        return true;
-    };
-    const size_t nt = (size_t)g.tiles;
-    if (!c->opts.rlt1_only && !A((void **)&c->z, nt * g.TS * 4)) return fail(rc);
-    if (!A((void **)&c->yS, nt * 4) || !A((void **)&c->yC, nt * 4) ||
-        !A((void **)&c->x, (size_t)N * N * 4) || !A((void **)&c->LB, 8) ||
-        !A((void **)&c->hist, (size_t)c->opts.max_iters * 8) || !A((void **)&c->iter, 4) ||
-        !A((void **)&c->stop, 4) || !A((void **)&c->counter, 4) ||
-        !A((void **)&c->status, sizeof(DevStatus)))
-        return fail(rc);
 
-    std::vector<int4> tri;
-    for (int i = 0; i < N; i++)
-        for (int k = i + 1; k < N; k++)
-            for (int p = k + 1; p < N; p++) tri.push_back(make_int4(i, k, p, 0));
-    c->ntriples = (int)tri.size();
-    if (!A((void **)&c->triples, tri.size() * sizeof(int4))) return fail(rc);
-    if (cudaMemcpy(c->triples, tri.data(), tri.size() * sizeof(int4), cudaMemcpyHostToDevice) !=
-        cudaSuccess)
-        return fail(RLT2_E_CUDA);
-
-    PassState &p = c->ps;
-    p.z = c->z;
-    p.yS = c->yS;
-    p.yC = c->yC;
-    p.x = c->x;
-    p.LB = c->LB;
-    p.hist = c->hist;
-    p.iter = c->iter;
-    p.stop = c->stop;
-    p.counter = c->counter;
-    p.status = c->status;
-    p.hist_cap = c->opts.max_iters;
-    p.ub = c->opts.ub;
-    p.min_progress = c->opts.min_progress;
-    p.pack = 3 * U < (1LL << 25);
-    p.rlt1_only = c->opts.rlt1_only != 0;
-
-    // inputs to the device, then the initialisation of Algorithm 1
-    int32_t *dF = nullptr, *dD = nullptr, *dB = nullptr;
-    if (!A((void **)&dF, (size_t)N * N * 4) || !A((void **)&dD, (size_t)N * N * 4) ||
-        (B_lin && !A((void **)&dB, (size_t)N * N * 4))) {
-        cudaFree(dF);
-        cudaFree(dD);
-        return fail(rc);
+    const bool with_d = !c->opts.rlt1_only;
+    const int JC = p1_chunk(N);
+    const std::vector<int4> tri = triple_table(N);
+    Arena a;
+    const NodeOffsets no = plan_node(a, N, with_d, c->opts.max_iters);
+    const size_t o_node = a.take(sizeof(NodeDesc));
+    const size_t o_tri = a.take(tri.size() * sizeof(int4));
+    const size_t o_cnt = a.take(4);
+    const size_t o_st = a.take(sizeof(DevStatus));
+    const size_t o_stage = a.take((size_t)3 * N * N * 4);
+    cudaError_t e = cudaMalloc((void **)&c->mem, a.used);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->mem = nullptr;
+        return fail(cuda_code(e));
     }
-    cudaError_t e = cudaMemcpyAsync(dF, F, (size_t)N * N * 4, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dD, D, (size_t)N * N * 4, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess && B_lin)
-        e = cudaMemcpyAsync(dB, B_lin, (size_t)N * N * 4, cudaMemcpyHostToDevice, c->stream);
-    long long lb0 = lb_const;
-    if (e == cudaSuccess) e = launch_init(g, p, dF, dD, dB, lb0, c->stream);
+    char *base = c->mem;
+    NodeDesc &nd = c->node;
+    fill_node(nd, N, JC);
+    nd.p = node_state(base, no, c->opts.max_iters, c->opts);
+    nd.tile_base = 0;
+    nd.cta_base = 0;
+    nd.prob_base = 0;
+
+    Group &g = c->g;
+    g.nodes = reinterpret_cast<const NodeDesc *>(base + o_node);
+    g.B = 1;
+    g.tiles = nd.tiles;
+    g.ctas = (int)(n_triples(N) * nd.nchunks);
+    g.probs = N * N;
+    g.maxN = N;
+    g.maxTS = nd.TS;
+    g.JC = JC;
+    g.pack = 3 * U < (1LL << 25);
+    g.rlt1_only = !with_d;
+    g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
+    g.status = reinterpret_cast<DevStatus *>(base + o_st);
+    g.triples = reinterpret_cast<const int4 *>(base + o_tri);
+
+    e = cudaMemcpyAsync(base + o_node, &nd, sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_tri, tri.data(), tri.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.status, 0, sizeof(DevStatus), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.counter, 0, 4, c->stream);
+    if (e == cudaSuccess)
+        e = init_node(nd, F, D, B_lin, lb_const, reinterpret_cast<int32_t *>(base + o_stage), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(dF);
-    cudaFree(dD);
-    cudaFree(dB);
     if (e != cudaSuccess) return fail(cuda_code(e));
     *out = c;
     return RLT2_OK;
-}
-
-// One pass of Algorithm 1: fused spread/complementary pass over D, D -> C,
-// complementary C + C -> B, B -> LB.  ev: 5 events to record around the stages.
-static cudaError_t enqueue_pass(rlt2_ctx *c, cudaEvent_t *ev)
-{
-    const Geom &g = c->g;
-    const PassState &p = c->ps;
-    cudaError_t e;
-    auto mark = [&](int s) { return ev ? cudaEventRecord(ev[s], c->stream) : cudaSuccess; };
-    if ((e = mark(0)) != cudaSuccess) return e;
-    if (!c->opts.rlt1_only) {
-        if ((e = launch_p1(g, p, c->triples, c->ntriples, c->stream)) != cudaSuccess) return e;
-        if ((e = mark(1)) != cudaSuccess) return e;
-        if ((e = launch_dlap(g, p, c->sm_count, c->stream)) != cudaSuccess) return e;
-    } else if ((e = mark(1)) != cudaSuccess) {
-        return e;
-    }
-    if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = launch_clap(g, p, c->stream)) != cudaSuccess) return e;
-    if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = launch_xlap(g, p, c->stream)) != cudaSuccess) return e;
-    return mark(4);
-}
-
-static cudaError_t build_graph(rlt2_ctx *c)
-{
-    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return e;
-    cudaError_t e2 = enqueue_pass(c, nullptr);
-    e = cudaStreamEndCapture(c->stream, &c->graph);
-    if (e2 != cudaSuccess) return e2;
-    if (e != cudaSuccess) return e;
-    return cudaGraphInstantiate(&c->gexec, c->graph, 0);
 }
 
 int rlt2_iterate(rlt2_ctx *c, int k)
@@ -273,23 +335,13 @@ int rlt2_iterate(rlt2_ctx *c, int k)
             c->ev_used += 5;
         }
         if (c->opts.use_graph && !ev) {
-            if (!c->gexec) CK(build_graph(c));
+            if (!c->gexec) CK(capture_passes(c->g, c->sm_count, c->stream, 1, &c->graph, &c->gexec));
             CK(cudaGraphLaunch(c->gexec, c->stream));
         } else {
-            CK(enqueue_pass(c, ev));   // profiling launches stage by stage
+            CK(enqueue_pass(c->g, c->sm_count, c->stream, ev));  // profiling: stage by stage
         }
         c->enqueued++;
     }
-    return RLT2_OK;
-}
-
-static int check_status(rlt2_ctx *c)
-{
-    int err = 0;
-    CK(cudaMemcpyAsync(&err, &c->status->err, 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (err & kDevTimeout) return RLT2_E_TIMEOUT;
-    if (err & kDevInternal) return RLT2_E_INTERNAL;
     return RLT2_OK;
 }
 
@@ -298,9 +350,9 @@ int rlt2_bound(rlt2_ctx *c, double *lb, int64_t *lb_exact, int *iters)
     if (!c) return RLT2_E_INVAL;
     long long v = 0;
     int it = 0;
-    CK(cudaMemcpyAsync(&v, c->LB, 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&it, c->iter, 4, cudaMemcpyDeviceToHost, c->stream));
-    int rc = check_status(c);
+    CK(cudaMemcpyAsync(&v, c->node.p.LB, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&it, c->node.p.iter, 4, cudaMemcpyDeviceToHost, c->stream));
+    int rc = group_status(c->g, c->stream);
     if (lb) *lb = (double)v;
     if (lb_exact) *lb_exact = v;
     if (iters) *iters = it;
@@ -311,10 +363,10 @@ int rlt2_bound_history(rlt2_ctx *c, int64_t *out, int cap, int *count)
 {
     if (!c || (!out && cap > 0) || cap < 0) return RLT2_E_INVAL;
     int it = 0;
-    CK(cudaMemcpyAsync(&it, c->iter, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&it, c->node.p.iter, 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     int n = std::min(std::min(it, cap), c->opts.max_iters);
-    if (n > 0) CK(cudaMemcpy(out, c->hist, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    if (n > 0) CK(cudaMemcpy(out, c->node.p.hist, (size_t)n * 8, cudaMemcpyDeviceToHost));
     if (count) *count = n;
     return RLT2_OK;
 }
@@ -322,32 +374,32 @@ int rlt2_bound_history(rlt2_ctx *c, int64_t *out, int cap, int *count)
 int rlt2_get_state(rlt2_ctx *c, int level, int32_t *host, size_t count)
 {
     if (!c || !host) return RLT2_E_INVAL;
-    const Geom &g = c->g;
-    const int N = g.N;
+    const NodeDesc &nd = c->node;
+    const int N = nd.N, n = N - 2;
     if (level == 0) {
         if (count != (size_t)N * N) return RLT2_E_INVAL;
-        CK(cudaMemcpyAsync(host, c->x, count * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(host, nd.p.x, count * 4, cudaMemcpyDeviceToHost, c->stream));
     } else if (level == 1) {
-        if (count != (size_t)g.tiles) return RLT2_E_INVAL;
-        CK(cudaMemcpyAsync(host, c->yC, count * 4, cudaMemcpyDeviceToHost, c->stream));
+        if (count != (size_t)nd.tiles) return RLT2_E_INVAL;
+        CK(cudaMemcpyAsync(host, nd.p.yC, count * 4, cudaMemcpyDeviceToHost, c->stream));
     } else if (level == 2) {
-        if (!c->z || count != (size_t)g.tiles * g.n * g.n) return RLT2_E_INVAL;
+        if (!nd.p.z || count != (size_t)nd.tiles * n * n) return RLT2_E_INVAL;
         // the store's rows are indexed by location: drop the tile's own two
         // locations (and the padding) to reach the compact layout
         std::vector<int32_t> tmp;
         try {
-            tmp.resize((size_t)g.tiles * g.TS);
+            tmp.resize((size_t)nd.tiles * nd.TS);
         } catch (...) {
             return RLT2_E_OOM;
         }
-        CK(cudaMemcpyAsync(tmp.data(), c->z, tmp.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(tmp.data(), nd.p.z, tmp.size() * 4, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
-        const int m = N - 1, n = g.n, W = g.W;
+        const int m = N - 1, W = nd.W;
         size_t o = 0;
-        for (long long t = 0; t < g.tiles; t++) {
+        for (long long t = 0; t < nd.tiles; t++) {
             const int nn = (int)(t % m), j = (int)((t / ((long long)m * m)) % N);
             const int nl = nn + (nn >= j);
-            const int32_t *src = tmp.data() + (size_t)t * g.TS;
+            const int32_t *src = tmp.data() + (size_t)t * nd.TS;
             for (int r = 0; r < n; r++)
                 for (int q = 0; q < N; q++)
                     if (q != j && q != nl) host[o++] = src[r * W + q];
@@ -363,7 +415,7 @@ int rlt2_work(rlt2_ctx *c, int64_t out[6])
 {
     if (!c || !out) return RLT2_E_INVAL;
     DevStatus s;
-    CK(cudaMemcpyAsync(&s, c->status, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&s, c->g.status, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     out[0] = (int64_t)s.laps;
     out[1] = (int64_t)s.steps;
@@ -379,14 +431,12 @@ int rlt2_stage_times(rlt2_ctx *c, double out[4], int *passes)
     if (!c || !out) return RLT2_E_INVAL;
     CK(cudaStreamSynchronize(c->stream));
     double acc[4] = {0, 0, 0, 0};
-    for (size_t b = 0; b + 5 <= c->ev_used; b += 5) {
-        const int map[4][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}};
+    for (size_t b = 0; b + 5 <= c->ev_used; b += 5)
         for (int s = 0; s < 4; s++) {
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, c->events[b + map[s][0]], c->events[b + map[s][1]]));
+            CK(cudaEventElapsedTime(&ms, c->events[b + s], c->events[b + s + 1]));
             acc[s] += ms;
         }
-    }
     for (int s = 0; s < 4; s++) out[s] = acc[s];
     if (passes) *passes = (int)(c->ev_used / 5);
     return RLT2_OK;
@@ -404,12 +454,198 @@ void *rlt2_device_state(rlt2_ctx *c, int which)
 {
     if (!c) return nullptr;
     switch (which) {
-    case 0: return c->x;
-    case 1: return c->yC;
-    case 2: return c->z;
+    case 0: return c->node.p.x;
+    case 1: return c->node.p.yC;
+    case 2: return c->node.p.z;
     default: return nullptr;
     }
 }
+
+// ----------------------------------------------------- branch-and-bound nodes
+
+int rlt2_subproblem(const int32_t *F, const int32_t *D, int N, int k, const int32_t *fac,
+                    const int32_t *loc, int32_t *Fp, int32_t *Dp, int32_t *Blin, int64_t *lb_const)
+{
+    if (!F || !D || N < 1 || N > RLT2_MAX_N || k < 0 || k > N || (k > 0 && (!fac || !loc)) ||
+        !Fp || !Dp || !Blin || !lb_const)
+        return RLT2_E_INVAL;
+    std::vector<char> ffix(N, 0), lfix(N, 0);
+    for (int t = 0; t < k; t++) {
+        if (fac[t] < 0 || fac[t] >= N || loc[t] < 0 || loc[t] >= N || ffix[fac[t]] || lfix[loc[t]])
+            return RLT2_E_INVAL;
+        ffix[fac[t]] = lfix[loc[t]] = 1;
+    }
+    std::vector<int> fr, lr;  // free facilities, free locations (ascending)
+    for (int a = 0; a < N; a++)
+        if (!ffix[a]) fr.push_back(a);
+    for (int l = 0; l < N; l++)
+        if (!lfix[l]) lr.push_back(l);
+    const int Np = N - k;
+    long long c0 = 0;
+    for (int t = 0; t < k; t++)
+        for (int t2 = 0; t2 < k; t2++)
+            if (t != t2) c0 += (long long)F[fac[t] * N + fac[t2]] * D[loc[t] * N + loc[t2]];
+    for (int x = 0; x < Np; x++)
+        for (int y = 0; y < Np; y++) {
+            Fp[x * Np + y] = F[fr[x] * N + fr[y]];
+            Dp[x * Np + y] = D[lr[x] * N + lr[y]];
+            // facility fr[x] at location lr[y] against every fixed pair, both directions
+            long long b = 0;
+            for (int t = 0; t < k; t++)
+                b += (long long)F[fr[x] * N + fac[t]] * D[lr[y] * N + loc[t]] +
+                     (long long)F[fac[t] * N + fr[x]] * D[loc[t] * N + lr[y]];
+            if (b > 0x7fffffffLL) return RLT2_E_OVERFLOW;
+            Blin[x * Np + y] = (int32_t)b;
+        }
+    *lb_const = c0;
+    return RLT2_OK;
+}
+
+int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node *nodes, int B,
+                     int iters, const rlt2_opts *opts, int64_t *lb_out, double *ms_out)
+{
+    if (!F || !D || N < RLT2_MIN_N || N > RLT2_MAX_N || !nodes || B < 1 || iters < 0 || !lb_out)
+        return RLT2_E_INVAL;
+    rlt2_opts o;
+    if (opts) o = *opts;
+    else rlt2_default_opts(&o);
+    if (o.rlt1_only) return RLT2_E_INVAL;  // the batch runs the full RLT2 dual ascent
+    cudaStream_t s = (cudaStream_t)o.stream;
+    int dev = 0, sm_count = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+
+    // residual instance of every node (host)
+    struct Inst {
+        int Np;
+        std::vector<int32_t> F, D, B;
+        long long cst;
+    };
+    std::vector<Inst> in(B);
+    int maxN = 0;
+    bool pack = true;
+    for (int b = 0; b < B; b++) {
+        const int k = nodes[b].k;
+        if (k < 0 || N - k < RLT2_MIN_N) return RLT2_E_INVAL;
+        Inst &I = in[b];
+        I.Np = N - k;
+        const size_t nn = (size_t)I.Np * I.Np;
+        I.F.resize(nn);
+        I.D.resize(nn);
+        I.B.resize(nn);
+        int64_t cst = 0;
+        int rc = rlt2_subproblem(F, D, N, k, nodes[b].fac, nodes[b].loc, I.F.data(), I.D.data(),
+                                 I.B.data(), &cst);
+        if (rc != RLT2_OK) return rc;
+        I.cst = cst;
+        long long U = 0;
+        rc = check_instance(I.F.data(), I.D.data(), I.Np, I.B.data(), &U);
+        if (rc != RLT2_OK) return rc;
+        pack = pack && 3 * U < (1LL << 25);
+        maxN = std::max(maxN, I.Np);
+    }
+    const int JC = p1_chunk(maxN);
+    const int hist_cap = std::max(iters, 1);
+
+    // one allocation for the whole group
+    Arena a;
+    std::vector<NodeOffsets> no(B);
+    for (int b = 0; b < B; b++) no[b] = plan_node(a, in[b].Np, true, hist_cap);
+    const std::vector<int4> tri = triple_table(maxN);
+    const size_t o_nodes = a.take((size_t)B * sizeof(NodeDesc));
+    const size_t o_tri = a.take(tri.size() * sizeof(int4));
+    const size_t o_cnt = a.take(4);
+    const size_t o_st = a.take(sizeof(DevStatus));
+    const size_t o_stage = a.take((size_t)3 * maxN * maxN * 4 * B);
+    char *base = nullptr;
+    cudaError_t e = cudaMalloc((void **)&base, a.used);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_code(e);
+    }
+    std::vector<NodeDesc> hn(B);
+    Group g{};
+    long long tiles = 0;
+    long long all_tiles = 0;
+    for (int b = 0; b < B; b++) all_tiles += make_geom(in[b].Np).tiles;
+    if (all_tiles >= (1LL << 31)) {  // tile indices of a group are 32-bit
+        cudaFree(base);
+        return RLT2_E_INVAL;
+    }
+    int ctas = 0, probs = 0, maxTS = 0;
+    for (int b = 0; b < B; b++) {
+        NodeDesc &nd = hn[b];
+        fill_node(nd, in[b].Np, JC);
+        nd.p = node_state(base, no[b], hist_cap, o);
+        nd.tile_base = tiles;
+        nd.cta_base = ctas;
+        nd.prob_base = probs;
+        tiles += nd.tiles;
+        ctas += (int)(n_triples(nd.N) * nd.nchunks);
+        probs += nd.N * nd.N;
+        maxTS = std::max(maxTS, nd.TS);
+    }
+    g.nodes = reinterpret_cast<const NodeDesc *>(base + o_nodes);
+    g.B = B;
+    g.tiles = tiles;
+    g.ctas = ctas;
+    g.probs = probs;
+    g.maxN = maxN;
+    g.maxTS = maxTS;
+    g.JC = JC;
+    g.pack = pack;
+    g.rlt1_only = false;
+    g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
+    g.status = reinterpret_cast<DevStatus *>(base + o_st);
+    g.triples = reinterpret_cast<const int4 *>(base + o_tri);
+
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = RLT2_OK;
+    do {
+        if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(base + o_nodes, hn.data(), (size_t)B * sizeof(NodeDesc),
+                                 cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            break;
+        if ((e = cudaMemcpyAsync(base + o_tri, tri.data(), tri.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            break;
+        if ((e = cudaMemsetAsync(g.status, 0, sizeof(DevStatus), s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(g.counter, 0, 4, s)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(t0, s)) != cudaSuccess) break;
+        int32_t *stage = reinterpret_cast<int32_t *>(base + o_stage);
+        for (int b = 0; b < B && e == cudaSuccess; b++)
+            e = init_node(hn[b], in[b].F.data(), in[b].D.data(), in[b].B.data(), in[b].cst,
+                          stage + (size_t)b * 3 * maxN * maxN, s);
+        if (e != cudaSuccess) break;
+        // all passes of all nodes: one captured graph, one launch
+        if (iters > 0) {
+            if ((e = capture_passes(g, sm_count, s, iters, &graph, &exec)) != cudaSuccess) break;
+            if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
+        }
+        if ((e = cudaEventRecord(t1, s)) != cudaSuccess) break;
+        rc = group_status(g, s);
+        for (int b = 0; b < B && e == cudaSuccess; b++)
+            e = cudaMemcpyAsync(&lb_out[b], hn[b].p.LB, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && ms_out) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, t0, t1);
+            *ms_out = ms;
+        }
+    } while (0);
+    if (e != cudaSuccess) rc = cuda_code(e);
+    cudaStreamSynchronize(s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaFree(base);
+    return rc;
+}
+
+// ------------------------------------------------------------------ LAP batch
 
 int rlt2_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign, int32_t *u,
                    int32_t *v, int64_t *work, void *stream)

@@ -215,6 +215,9 @@ __device__ __forceinline__ long long warp_sum64(long long x)
 // Value range: with entries in [0, A], |u|, |v| <= A and every key <= 3A, so
 // A <= 2^29 - 1 fits int32 (PACK needs 3A < 2^25).
 //
+// steps_out / relax_out accumulate the LAP's work (32-bit: a caller sums at
+// most one launch's LAPs of one warp, far below 2^32 for n <= 64).
+//
 // M: shared memory, row r at M + r * ld (rows 0..n-1).  The n columns are the
 // indices c < width other than dead0 and dead1 (width <= 32 * NS); a column's
 // lane and slot follow its index, so ties still go to the smallest column.
@@ -227,7 +230,7 @@ template <int NS, bool PACK>
 __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld, int n, int width,
                                                int dead0, int dead1, int (&rowOf)[NS],
                                                int (&uM)[NS], int (&v)[NS],
-                                               long long &steps_out, long long &relax_out)
+                                               unsigned &steps_out, unsigned &relax_out)
 {
     constexpr unsigned kDone = 0x80000000u;  // key of a labelled (or absent) column
     const int lane = threadIdx.x & 31;
@@ -342,8 +345,8 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
             c = w;
         }
     }
-    steps_out += sumK;
-    relax_out += (long long)n * sumK - ((long long)sumK2 - sumK) / 2;
+    steps_out += (unsigned)sumK;
+    relax_out += (unsigned)(n * sumK - (sumK2 - sumK) / 2);
     return true;
 }
 

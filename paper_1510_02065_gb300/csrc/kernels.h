@@ -1,11 +1,18 @@
-// kernels.h -- host-side launchers of the device kernels (internal to the library).
+// kernels.h -- internal interface between the C ABI and the device kernels.
+//
+// Every stage kernel advances a *group* of RLT2 instances at once: a table of
+// per-instance descriptors, each work item (CTA, warp or thread) finding its
+// instance by binary search over prefix counts.  A single dual ascent is a
+// group of one; a batch of branch-and-bound nodes of different residual sizes
+// is a larger group advanced by the same launches.
 #pragma once
 #include <cuda_runtime.h>
+
 #include <cstdint>
 
-namespace rlt2 {
+#include "device.cuh"
 
-struct DevStatus;
+namespace rlt2 {
 
 // Geometry of the tile store of D.  Tile t = ((i*N + j)*(N-1) + k')*(N-1) + n'
 // holds the submatrix D_ijkn: its N-2 rows are the facilities p not in {i,k}
@@ -32,36 +39,90 @@ inline Geom make_geom(int N)
     return g;
 }
 
-// Per-pass device state shared by the stage kernels.
+// Device state of one instance.
 struct PassState {
-    int *z;                  // tile store of D
-    int *yS;                 // S of each D-tile concentration (C before its transfer)
-    int *yC;                 // reduced C after concentration C->B
-    int *x;                  // reduced B
-    long long *LB;           // bound
-    long long *hist;         // LB after each pass
-    int *iter;               // passes completed
-    int *stop;               // stopping rule fired
-    unsigned *counter;       // work counter of the D->C sweep
-    DevStatus *status;
+    int *z;            // tile store of D (null without D)
+    int *yS;           // per tile: c' before D->C, then S of the tile's LAP
+    int *yC;           // reduced C after concentration C->B
+    int *x;            // reduced B
+    long long *LB;     // bound
+    long long *hist;   // LB after each pass
+    int *iter;         // passes completed
+    int *stop;         // stopping rule fired
     int hist_cap;
     double ub, min_progress;
-    bool pack;               // keys fit the packed reduction
-    bool rlt1_only;
 };
 
-cudaError_t launch_init(const Geom &g, const PassState &p, const int32_t *F, const int32_t *D,
+// One instance as the kernels see it.
+struct NodeDesc {
+    PassState p;
+    int N, W, TS;
+    int nchunks;          // location chunks of the fused pass over D
+    long long tiles;
+    long long tile_base;  // first group-wide tile index of this instance
+    int cta_base;         // first fused-pass CTA of this instance
+    int prob_base;        // first C->B problem of this instance
+    FastDiv fN, fm, fmm, fn, fW4;
+};
+
+inline void fill_node(NodeDesc &d, int N, int JC)
+{
+    const Geom g = make_geom(N);
+    d.N = N;
+    d.W = g.W;
+    d.TS = g.TS;
+    d.tiles = g.tiles;
+    d.nchunks = (N + JC - 1) / JC;
+    d.fN = make_fastdiv(N);
+    d.fm = make_fastdiv(N - 1);
+    d.fmm = make_fastdiv((N - 1) * (N - 1));
+    d.fn = make_fastdiv(N - 2);
+    d.fW4 = make_fastdiv(g.W / 4);
+}
+
+// A group of instances advanced together.
+struct Group {
+    const NodeDesc *nodes;  // device array [B]
+    int B;
+    long long tiles;        // total tiles
+    int ctas;               // total fused-pass CTAs
+    int probs;              // total C->B problems
+    int maxN, maxTS;        // largest instance
+    int JC;                 // locations per fused-pass CTA (one value for the group)
+    bool pack;              // every instance's keys fit the packed reduction
+    bool rlt1_only;
+    unsigned *counter;      // D->C work counter
+    DevStatus *status;      // error bits and work counters of the group
+    const int4 *triples;    // facility triples i<k<p ordered by p: the first C(N,3) serve N
+};
+
+int p1_chunk(int N);                   // locations per CTA of the fused pass over D
+size_t p1_smem_bytes(int N, int JC);   // its dynamic shared memory
+
+// Initialise instance `node` of the group (index b) from device copies of its
+// F, D and linear costs (Blin may be null).
+cudaError_t launch_init(const NodeDesc &node, const int32_t *F, const int32_t *D,
                         const int32_t *Blin, long long lb_const, cudaStream_t s);
-cudaError_t launch_spread_x(const Geom &g, const PassState &p, cudaStream_t s);
-cudaError_t launch_p1(const Geom &g, const PassState &p, const int4 *triples, int ntriples,
-                      cudaStream_t s);
-cudaError_t launch_dlap(const Geom &g, const PassState &p, int sm_count, cudaStream_t s);
-cudaError_t launch_clap(const Geom &g, const PassState &p, cudaStream_t s);
-cudaError_t launch_xlap(const Geom &g, const PassState &p, cudaStream_t s);
+cudaError_t launch_spread_x(const Group &g, cudaStream_t s);
+cudaError_t launch_p1(const Group &g, cudaStream_t s);
+cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s);
+cudaError_t launch_clap(const Group &g, cudaStream_t s);
+cudaError_t launch_xlap(const Group &g, cudaStream_t s);
 cudaError_t launch_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
                              int32_t *u, int32_t *v, int64_t *work, DevStatus *status,
                              cudaStream_t s);
 
-int p1_chunk(int N);                    // locations per CTA of the fused pass over D
-size_t p1_smem_bytes(int N, int JC);    // its dynamic shared memory
+// Index of the instance owning group-wide item x; base(node) is its first item.
+template <typename F>
+__device__ __forceinline__ int find_node(const NodeDesc *nodes, int B, long long x, F base)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base(nodes[mid]) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 }  // namespace rlt2

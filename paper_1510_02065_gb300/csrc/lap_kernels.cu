@@ -17,126 +17,113 @@
 namespace rlt2 {
 
 constexpr int kDlapWarps = 4;
-#ifndef RLT2_DLAP_NBUF
-#define RLT2_DLAP_NBUF 1
-#endif
 constexpr int kClapWarps = 4;
+constexpr int kXlapWarps = 4;
 constexpr int kBatchWarps = 4;
 
 // ------------------------------------------------------------ D -> C sweep
 
-// NBUF = 2: each warp prefetches its next tile while it solves the current
-// one; NBUF = 1: one tile buffer per warp, twice the warps per SM.
-template <int NS, bool PACK, int NBUF>
-__global__ void __launch_bounds__(kDlapWarps * 32)
-    dlap_kernel(PassState p, int N, int W, long long ntiles, FastDiv fmm, FastDiv fm, FastDiv fN)
+// One tile buffer per warp; a warp takes group-wide tile indices from a global
+// counter, finds the tile's instance, brings the tile in with one bulk copy
+// and solves its LAP.  Tiles of one instance are consecutive in the group-wide
+// order, so the instance found for the previous tile is tried first.
+template <int NS, bool PACK>
+__global__ void __launch_bounds__(kDlapWarps * 32) dlap_kernel(Group g)
 {
-    if (*p.stop) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = N - 2, m = N - 1;
-    const int TS = n * W;
-    const unsigned bytes = (unsigned)TS * 4u;
-    int *bufs = reinterpret_cast<int *>(smem) + (size_t)warp * NBUF * TS;
-    unsigned char *tail = smem + (size_t)kDlapWarps * NBUF * TS * 4;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tail) + warp * 2;
-    int *uRow = reinterpret_cast<int *>(tail + kDlapWarps * 16) + warp * 64;
+    int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * g.maxTS;
+    unsigned char *tail = smem + (size_t)kDlapWarps * g.maxTS * 4;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tail) + warp;
+    int *uRow = reinterpret_cast<int *>(tail + kDlapWarps * 8) + warp * 64;
 
     if (lane == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncwarp();
 
-    auto grab = [&]() -> long long {
-        unsigned t = 0;
-        if (lane == 0) t = atomicAdd(p.counter, 1u);
-        return (long long)__shfl_sync(kFull, t, 0);
-    };
-
-    long long t = grab();
-    if (t < ntiles && lane == 0) bulk_load(bufs, p.z + t * TS, bytes, &bars[0]);
-    unsigned parity = 0;  // bit b: parity of the next completion of bars[b]
-    int cur = 0;
-    long long steps = 0, relax = 0, laps = 0;
-    while (t < ntiles) {
-        const long long tn = NBUF == 2 ? grab() : 0;
-        const bool pref = NBUF == 2 && tn < ntiles;
-        if (pref && lane == 0) {
+    unsigned parity = 0;
+    unsigned steps = 0, relax = 0, laps = 0;
+    const unsigned ntiles = (unsigned)g.tiles;  // < 2^31 for any group the host accepts
+    int b = 0;
+    for (;;) {
+        unsigned T = 0;
+        if (lane == 0) T = atomicAdd(g.counter, 1u);
+        T = __shfl_sync(kFull, T, 0);
+        if (T >= ntiles) break;
+        if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
+            b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
+        const NodeDesc &nd = g.nodes[b];
+        if (*nd.p.stop) continue;
+        const unsigned t = T - (unsigned)nd.tile_base;
+        const int N = nd.N, W = nd.W, n = N - 2, m = N - 1, TS = nd.TS;
+        if (lane == 0) {
             fence_proxy_async_smem();
-            bulk_load(bufs + (cur ^ 1) * TS, p.z + tn * TS, bytes, &bars[cur ^ 1]);
+            bulk_load(buf, nd.p.z + (size_t)t * TS, (unsigned)TS * 4u, bar);
         }
-        const bool got = __all_sync(kFull, mbar_wait(&bars[cur], (parity >> cur) & 1u));
-        if (!got) {
-            // give up: record it, let the copies in flight land (bounded), leave
-            if (lane == 0) atomicOr(&p.status->err, kDevTimeout);
-            mbar_wait(&bars[cur], (parity >> cur) & 1u);
-            if (pref) mbar_wait(&bars[cur ^ 1], (parity >> (cur ^ 1)) & 1u);
+        if (!__all_sync(kFull, mbar_wait(bar, parity))) {
+            // give up: record it, let the copy in flight land (bounded), leave
+            if (lane == 0) atomicOr(&g.status->err, kDevTimeout);
+            mbar_wait(bar, parity);
             __syncwarp();
             return;
         }
-        parity ^= 1u << cur;
-        const int *buf = bufs + cur * TS;
+        parity ^= 1u;
 
         // the tile's own locations j and n are the columns without coefficient
-        const unsigned ij = fdiv((unsigned)t, fmm);
-        const unsigned rem = (unsigned)t - ij * (unsigned)(m * m);
-        const int nn = (int)(rem - fdiv(rem, fm) * (unsigned)m);
-        const int j = (int)(ij - fdiv(ij, fN) * (unsigned)N);
+        const unsigned ij = fdiv(t, nd.fmm);
+        const unsigned rem = t - ij * (unsigned)(m * m);
+        const int nn = (int)(rem - fdiv(rem, nd.fm) * (unsigned)m);
+        const int j = (int)(ij - fdiv(ij, nd.fN) * (unsigned)N);
         const int nl = nn + (nn >= j);
         int rowOf[NS], uM[NS], v[NS];
         if (!warp_hungarian<NS, PACK>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
-            atomicOr(&p.status->err, kDevInternal);
+            atomicOr(&g.status->err, kDevInternal);
         scatter_rows<NS>(n, N, j, nl, rowOf, uM, uRow, nullptr);
         __syncwarp();
-        int *g = p.z + t * TS;
+        int *gz = nd.p.z + (size_t)t * TS;
         for (int r = 0; r < n; ++r) {
             const int ur = uRow[r];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 const int c = lane + 32 * s;
-                if (c < W) g[r * W + c] = (c < N && c != j && c != nl) ? buf[r * W + c] - ur - v[s] : 0;
+                if (c < W) gz[r * W + c] = (c < N && c != j && c != nl) ? buf[r * W + c] - ur - v[s] : 0;
             }
         }
         const long long S = lap_value<NS>(N, j, nl, uM, v);
-        if (lane == 0) p.yS[t] = (int)S;
+        if (lane == 0) nd.p.yS[t] = (int)S;
         ++laps;
         __syncwarp();
-        if constexpr (NBUF == 2) {
-            t = tn;
-            cur ^= 1;
-        } else {
-            t = grab();
-            if (t < ntiles && lane == 0) {
-                fence_proxy_async_smem();
-                bulk_load(bufs, p.z + t * TS, bytes, &bars[0]);
-            }
-        }
     }
     if (lane == 0 && laps) {
-        atomicAdd(&p.status->laps, (unsigned long long)laps);
-        atomicAdd(&p.status->steps, (unsigned long long)steps);
-        atomicAdd(&p.status->relax, (unsigned long long)relax);
-        atomicAdd(&p.status->dlaps, (unsigned long long)laps);
-        atomicAdd(&p.status->dsteps, (unsigned long long)steps);
-        atomicAdd(&p.status->drelax, (unsigned long long)relax);
+        atomicAdd(&g.status->laps, (unsigned long long)laps);
+        atomicAdd(&g.status->steps, (unsigned long long)steps);
+        atomicAdd(&g.status->relax, (unsigned long long)relax);
+        atomicAdd(&g.status->dlaps, (unsigned long long)laps);
+        atomicAdd(&g.status->dsteps, (unsigned long long)steps);
+        atomicAdd(&g.status->drelax, (unsigned long long)relax);
     }
 }
 
 // -------------------------------------------- complementary C + C -> B
 
+// One warp per C->B problem (instance, i, j) of the group.
 template <int NS, bool PACK>
-__global__ void __launch_bounds__(kClapWarps * 32) clap_kernel(PassState p, int N)
+__global__ void __launch_bounds__(kClapWarps * 32) clap_kernel(Group g, int pitch)
 {
-    if (*p.stop) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = N - 1;
-    int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * (m * m + 64);
-    int *uRow = buf + m * m;
-    long long steps = 0, relax = 0, laps = 0;
-    for (int prob = blockIdx.x * kClapWarps + warp; prob < N * N; prob += gridDim.x * kClapWarps) {
+    int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * pitch;
+    unsigned steps = 0, relax = 0, laps = 0;
+    for (int P = blockIdx.x * kClapWarps + warp; P < g.probs; P += gridDim.x * kClapWarps) {
+        const NodeDesc &nd =
+            g.nodes[find_node(g.nodes, g.B, P, [](const NodeDesc &d) { return (long long)d.prob_base; })];
+        const PassState &p = nd.p;
+        if (*p.stop) continue;
+        const int N = nd.N, m = N - 1;
+        int *uRow = buf + m * m;
+        const int prob = P - nd.prob_base;
         const int i = prob / N, j = prob % N;
         const long long base = (long long)prob * m * m;
         // transfer between the complementary pair {c_ijkn, c_knij} (Eq. (10)):
@@ -152,7 +139,7 @@ __global__ void __launch_bounds__(kClapWarps * 32) clap_kernel(PassState p, int 
         __syncwarp();
         int rowOf[NS], uM[NS], v[NS];
         if (!warp_hungarian<NS, PACK>(buf, m, m, m, -1, -1, rowOf, uM, v, steps, relax) && lane == 0)
-            atomicOr(&p.status->err, kDevInternal);
+            atomicOr(&g.status->err, kDevInternal);
         scatter_rows<NS>(m, m, -1, -1, rowOf, uM, uRow, nullptr);
         __syncwarp();
         for (int r = 0; r < m; ++r) {
@@ -169,28 +156,34 @@ __global__ void __launch_bounds__(kClapWarps * 32) clap_kernel(PassState p, int 
         __syncwarp();
     }
     if (lane == 0 && laps) {
-        atomicAdd(&p.status->laps, (unsigned long long)laps);
-        atomicAdd(&p.status->steps, (unsigned long long)steps);
-        atomicAdd(&p.status->relax, (unsigned long long)relax);
+        atomicAdd(&g.status->laps, (unsigned long long)laps);
+        atomicAdd(&g.status->steps, (unsigned long long)steps);
+        atomicAdd(&g.status->relax, (unsigned long long)relax);
     }
 }
 
 // ------------------------------------------------------------- B -> LB
 
+// One warp per instance of the group.
 template <int NS, bool PACK>
-__global__ void __launch_bounds__(32) xlap_kernel(PassState p, int N)
+__global__ void __launch_bounds__(kXlapWarps * 32) xlap_kernel(Group g, int pitch)
 {
-    if (*p.stop) return;
     extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    int *buf = reinterpret_cast<int *>(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * kXlapWarps + warp;
+    if (b >= g.B) return;
+    const NodeDesc &nd = g.nodes[b];
+    const PassState &p = nd.p;
+    if (*p.stop) return;
+    const int N = nd.N;
+    int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * pitch;
     int *uRow = buf + N * N;
     for (int e = lane; e < N * N; e += 32) buf[e] = p.x[e];
     __syncwarp();
-    long long steps = 0, relax = 0;
+    unsigned steps = 0, relax = 0;
     int rowOf[NS], uM[NS], v[NS];
     if (!warp_hungarian<NS, PACK>(buf, N, N, N, -1, -1, rowOf, uM, v, steps, relax) && lane == 0)
-        atomicOr(&p.status->err, kDevInternal);
+        atomicOr(&g.status->err, kDevInternal);
     scatter_rows<NS>(N, N, -1, -1, rowOf, uM, uRow, nullptr);
     __syncwarp();
     for (int r = 0; r < N; ++r) {
@@ -213,9 +206,9 @@ __global__ void __launch_bounds__(32) xlap_kernel(PassState p, int N)
             if ((double)lb >= p.ub) *p.stop = 1;
             if (p.min_progress > 0.0 && (double)S / p.ub < p.min_progress) *p.stop = 1;
         }
-        atomicAdd(&p.status->laps, 1ull);
-        atomicAdd(&p.status->steps, (unsigned long long)steps);
-        atomicAdd(&p.status->relax, (unsigned long long)relax);
+        atomicAdd(&g.status->laps, 1ull);
+        atomicAdd(&g.status->steps, (unsigned long long)steps);
+        atomicAdd(&g.status->relax, (unsigned long long)relax);
     }
 }
 
@@ -250,7 +243,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
             }
             continue;
         }
-        long long steps = 0, relax = 0;
+        unsigned steps = 0, relax = 0;
         int rowOf[NS], uM[NS], v[NS];
         const bool fine = mx < (1 << 25) / 3
                               ? warp_hungarian<NS, true>(buf, n, n, n, -1, -1, rowOf, uM, v, steps, relax)
@@ -282,11 +275,10 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
 // ---------------------------------------------------------------- launchers
 
 template <int NS, bool PACK>
-static cudaError_t dlap_go(const Geom &g, const PassState &p, int sm_count, cudaStream_t s)
+static cudaError_t dlap_go(const Group &g, int sm_count, cudaStream_t s)
 {
-    constexpr int NB = RLT2_DLAP_NBUF;
-    const size_t smem = (size_t)kDlapWarps * (NB * (size_t)g.TS * 4 + 16 + 256);
-    auto k = dlap_kernel<NS, PACK, NB>;
+    const size_t smem = (size_t)kDlapWarps * ((size_t)g.maxTS * 4 + 8 + 256);
+    auto k = dlap_kernel<NS, PACK>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -296,56 +288,59 @@ static cudaError_t dlap_go(const Geom &g, const PassState &p, int sm_count, cuda
     long long grid = (long long)per_sm * sm_count;
     const long long need = (g.tiles + kDlapWarps - 1) / kDlapWarps;
     if (grid > need) grid = need;
-    const int m = g.N - 1;
-    k<<<(unsigned)grid, kDlapWarps * 32, smem, s>>>(p, g.N, g.W, g.tiles, make_fastdiv(m * m),
-                                                     make_fastdiv(m), make_fastdiv(g.N));
+    if (grid < 1) grid = 1;
+    k<<<(unsigned)grid, kDlapWarps * 32, smem, s>>>(g);
     return cudaGetLastError();
 }
 
 // The work counter is reset by the fused pass over D, which precedes this kernel.
-cudaError_t launch_dlap(const Geom &g, const PassState &p, int sm_count, cudaStream_t s)
+cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s)
 {
-    if (g.N <= 32) return p.pack ? dlap_go<1, true>(g, p, sm_count, s) : dlap_go<1, false>(g, p, sm_count, s);
-    return p.pack ? dlap_go<2, true>(g, p, sm_count, s) : dlap_go<2, false>(g, p, sm_count, s);
+    if (g.maxN <= 32) return g.pack ? dlap_go<1, true>(g, sm_count, s) : dlap_go<1, false>(g, sm_count, s);
+    return g.pack ? dlap_go<2, true>(g, sm_count, s) : dlap_go<2, false>(g, sm_count, s);
 }
 
 template <int NS, bool PACK>
-static cudaError_t clap_go(const Geom &g, const PassState &p, cudaStream_t s)
+static cudaError_t clap_go(const Group &g, cudaStream_t s)
 {
-    const int m = g.N - 1;
-    const size_t smem = (size_t)kClapWarps * (m * m + 64) * 4;
+    const int m = g.maxN - 1;
+    const int pitch = m * m + 64;
+    const size_t smem = (size_t)kClapWarps * pitch * 4;
     auto k = clap_kernel<NS, PACK>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int probs = g.N * g.N;
-    const int grid = (probs + kClapWarps - 1) / kClapWarps;
-    k<<<grid, kClapWarps * 32, smem, s>>>(p, g.N);
+    const int grid = (g.probs + kClapWarps - 1) / kClapWarps;
+    k<<<grid, kClapWarps * 32, smem, s>>>(g, pitch);
     return cudaGetLastError();
 }
 
-cudaError_t launch_clap(const Geom &g, const PassState &p, cudaStream_t s)
+cudaError_t launch_clap(const Group &g, cudaStream_t s)
 {
-    if (p.rlt1_only) {
+    if (g.rlt1_only) {
         // without D, the input of C -> B is C plus the spread of B
-        cudaError_t e = launch_spread_x(g, p, s);
+        cudaError_t e = launch_spread_x(g, s);
         if (e != cudaSuccess) return e;
     }
-    if (g.N - 1 <= 32) return p.pack ? clap_go<1, true>(g, p, s) : clap_go<1, false>(g, p, s);
-    return p.pack ? clap_go<2, true>(g, p, s) : clap_go<2, false>(g, p, s);
+    if (g.maxN - 1 <= 32) return g.pack ? clap_go<1, true>(g, s) : clap_go<1, false>(g, s);
+    return g.pack ? clap_go<2, true>(g, s) : clap_go<2, false>(g, s);
 }
 
 template <int NS, bool PACK>
-static cudaError_t xlap_go(const Geom &g, const PassState &p, cudaStream_t s)
+static cudaError_t xlap_go(const Group &g, cudaStream_t s)
 {
-    const size_t smem = (size_t)(g.N * g.N + 64) * 4;
-    xlap_kernel<NS, PACK><<<1, 32, smem, s>>>(p, g.N);
+    const int pitch = g.maxN * g.maxN + 64;
+    const size_t smem = (size_t)kXlapWarps * pitch * 4;
+    auto k = xlap_kernel<NS, PACK>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<(g.B + kXlapWarps - 1) / kXlapWarps, kXlapWarps * 32, smem, s>>>(g, pitch);
     return cudaGetLastError();
 }
 
-cudaError_t launch_xlap(const Geom &g, const PassState &p, cudaStream_t s)
+cudaError_t launch_xlap(const Group &g, cudaStream_t s)
 {
-    if (g.N <= 32) return p.pack ? xlap_go<1, true>(g, p, s) : xlap_go<1, false>(g, p, s);
-    return p.pack ? xlap_go<2, true>(g, p, s) : xlap_go<2, false>(g, p, s);
+    if (g.maxN <= 32) return g.pack ? xlap_go<1, true>(g, s) : xlap_go<1, false>(g, s);
+    return g.pack ? xlap_go<2, true>(g, s) : xlap_go<2, false>(g, s);
 }
 
 template <int NS>

@@ -121,22 +121,27 @@ __device__ __forceinline__ void copy_piece(int *dst, const int *src)
     else *dst = *src;
 }
 
-// fN divides by N, fW4 by W/4, fn by N-2; yS holds c' (C plus the spread of B) per tile
+// One CTA per (instance, facility triple, location chunk) of the group; yS
+// holds c' (C plus the spread of B) per tile.
 template <int JC>
-__global__ void __launch_bounds__(kP1Threads, 2)
-    p1_kernel(PassState p, int N, int W, const int4 *__restrict__ triples, int nchunks,
-              FastDiv fN, FastDiv fW4, FastDiv fn)
+__global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *g.counter = 0;  // work counter of the D -> C sweep
+    const NodeDesc &nd =
+        g.nodes[find_node(g.nodes, g.B, blockIdx.x, [](const NodeDesc &d) { return (long long)d.cta_base; })];
+    const PassState p = nd.p;
     if (*p.stop) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *p.counter = 0;  // work counter of the D -> C sweep
+    const int N = nd.N, W = nd.W, nchunks = nd.nchunks;
+    const FastDiv fN = nd.fN, fW4 = nd.fW4, fn = nd.fn;
+    const int bid = blockIdx.x - nd.cta_base;
     extern __shared__ __align__(128) int sm[];
     const P1Layout L = p1_layout(N, W, JC);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t TS = (size_t)(N - 2) * W;
     const int W4 = W >> 2;
-    const int4 tr = triples[blockIdx.x / nchunks];
+    const int4 tr = g.triples[bid / nchunks];
     const int i = tr.x, k = tr.y, pp = tr.z;
-    const int j0 = (blockIdx.x % nchunks) * JC;
+    const int j0 = (bid % nchunks) * JC;
     const int jc = min(JC, N - j0);
     const int *__restrict__ yS = p.yS;
     int *__restrict__ z = p.z;
@@ -245,24 +250,26 @@ __global__ void __launch_bounds__(kP1Threads, 2)
 
 // Costs spreading from B to C (Sec. 4.2): c'_ijkn = c_ijkn + the share of b_ij
 // of row k (k' = rank of k among the facilities != i), written to yS.  One
-// block row per (i, j), threads over the (N-1)^2 entries of C_ij.
-__global__ void spread_x_to_y_kernel(PassState p, int N, FastDiv fm)
+// thread per tile of the group.
+__global__ void spread_x_to_y_kernel(Group g)
 {
-    if (*p.stop) return;
-    const int m = N - 1;
-    const int ij = blockIdx.y;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m * m) return;
-    const int kk = (int)fdiv((unsigned)e, fm);
-    const long long t = (long long)ij * m * m + e;
-    p.yS[t] = p.yC[t] + share(p.x[ij], fm, kk);
+    for (long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x; T < g.tiles;
+         T += (long long)gridDim.x * blockDim.x) {
+        const NodeDesc &nd = g.nodes[find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; })];
+        if (*nd.p.stop) continue;
+        const unsigned t = (unsigned)(T - nd.tile_base);
+        const unsigned ij = fdiv(t, nd.fmm);
+        const unsigned e = t - ij * nd.fmm.d;
+        const int kk = (int)fdiv(e, nd.fm);
+        nd.p.yS[t] = nd.p.yC[t] + share(nd.p.x[ij], nd.fm, kk);
+    }
 }
 
-cudaError_t launch_spread_x(const Geom &g, const PassState &p, cudaStream_t s)
+cudaError_t launch_spread_x(const Group &g, cudaStream_t s)
 {
-    const int m = g.N - 1;
-    dim3 grid((m * m + 255) / 256, g.N * g.N);
-    spread_x_to_y_kernel<<<grid, 256, 0, s>>>(p, g.N, make_fastdiv(m));
+    long long blocks = (g.tiles + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    spread_x_to_y_kernel<<<(unsigned)blocks, 256, 0, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -286,50 +293,46 @@ __global__ void init_scalars_kernel(PassState p, long long lb_const)
     *p.LB = lb_const;
     *p.iter = 0;
     *p.stop = 0;
-    DevStatus z = {};
-    *p.status = z;
 }
 
-cudaError_t launch_init(const Geom &g, const PassState &p, const int32_t *F, const int32_t *D,
+cudaError_t launch_init(const NodeDesc &nd, const int32_t *F, const int32_t *D,
                         const int32_t *Blin, long long lb_const, cudaStream_t s)
 {
+    const PassState &p = nd.p;
     cudaError_t e = cudaSuccess;
-    if (p.z) e = cudaMemsetAsync(p.z, 0, (size_t)g.tiles * g.TS * 4, s);
+    if (p.z) e = cudaMemsetAsync(p.z, 0, (size_t)nd.tiles * nd.TS * 4, s);
     if (e != cudaSuccess) return e;
-    int grid = (int)((g.tiles + 255) / 256);
+    long long grid = (nd.tiles + 255) / 256;
     if (grid > 8192) grid = 8192;
-    init_y_kernel<<<grid, 256, 0, s>>>(p.yC, g.N, F, D);
+    init_y_kernel<<<(unsigned)grid, 256, 0, s>>>(p.yC, nd.N, F, D);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (Blin) e = cudaMemcpyAsync(p.x, Blin, (size_t)g.N * g.N * 4, cudaMemcpyDeviceToDevice, s);
-    else e = cudaMemsetAsync(p.x, 0, (size_t)g.N * g.N * 4, s);
+    if (Blin) e = cudaMemcpyAsync(p.x, Blin, (size_t)nd.N * nd.N * 4, cudaMemcpyDeviceToDevice, s);
+    else e = cudaMemsetAsync(p.x, 0, (size_t)nd.N * nd.N * 4, s);
     if (e != cudaSuccess) return e;
     init_scalars_kernel<<<1, 1, 0, s>>>(p, lb_const);
     return cudaGetLastError();
 }
 
 template <int JC>
-static cudaError_t p1_go(const Geom &g, const PassState &p, const int4 *triples, int ntriples,
-                         cudaStream_t s)
+static cudaError_t p1_go(const Group &g, cudaStream_t s)
 {
-    const size_t smem = p1_smem_bytes(g.N, JC);
+    const size_t smem = p1_smem_bytes(g.maxN, JC);
     auto k = p1_kernel<JC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int nchunks = (g.N + JC - 1) / JC;
-    k<<<ntriples * nchunks, kP1Threads, smem, s>>>(p, g.N, g.W, triples, nchunks, make_fastdiv(g.N),
-                                                    make_fastdiv(g.W / 4), make_fastdiv(g.N - 2));
+    k<<<g.ctas, kP1Threads, smem, s>>>(g);
     return cudaGetLastError();
 }
 
-cudaError_t launch_p1(const Geom &g, const PassState &p, const int4 *triples, int ntriples,
-                      cudaStream_t s)
+// Spread B -> C, then the fused spread C -> D / complementary D pass.
+cudaError_t launch_p1(const Group &g, cudaStream_t s)
 {
-    cudaError_t e = launch_spread_x(g, p, s);
+    cudaError_t e = launch_spread_x(g, s);
     if (e != cudaSuccess) return e;
-    switch (p1_chunk(g.N)) {
-    case 4: return p1_go<4>(g, p, triples, ntriples, s);
-    case 2: return p1_go<2>(g, p, triples, ntriples, s);
-    default: return p1_go<1>(g, p, triples, ntriples, s);
+    switch (g.JC) {
+    case 4: return p1_go<4>(g, s);
+    case 2: return p1_go<2>(g, s);
+    default: return p1_go<1>(g, s);
     }
 }
 

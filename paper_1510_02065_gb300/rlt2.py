@@ -38,6 +38,10 @@ class Rlt2Error(RuntimeError):
         super().__init__("%s failed: %s (%d)" % (where, rlt2_strerror(code), code))
 
 
+class rlt2_node(C.Structure):
+    _fields_ = [("k", C.c_int), ("fac", C.POINTER(C.c_int32)), ("loc", C.POINTER(C.c_int32))]
+
+
 class rlt2_opts(C.Structure):
     _fields_ = [("rlt1_only", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
                 ("max_iters", C.c_int), ("ub", C.c_double), ("min_progress", C.c_double),
@@ -78,6 +82,10 @@ def lib():
         "rlt2_row_stride": (C.c_int, [C.c_int]),
         "rlt2_lap_batch": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "rlt2_lap_batch_static": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "rlt2_subproblem": (C.c_int, [_i32p, _i32p, C.c_int, C.c_int, _i32p, _i32p, _i32p, _i32p,
+                                      _i32p, _i64p]),
+        "rlt2_batch_bound": (C.c_int, [_i32p, _i32p, C.c_int, C.POINTER(rlt2_node), C.c_int, C.c_int,
+                                       C.POINTER(rlt2_opts), _i64p, _dblp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -208,6 +216,42 @@ def rlt2_lap_batch_static(M_ptr, n, count, S_ptr, assign_ptr=0, u_ptr=0, v_ptr=0
                                        _vp(assign_ptr or None), _vp(u_ptr or None),
                                        _vp(v_ptr or None), _vp(work_ptr or None),
                                        _vp(stream or None))
+
+
+def rlt2_subproblem(F, D, fac, loc):
+    """Residual instance of a node fixing fac[t] -> loc[t] -> (Fp, Dp, Blin, lb_const)."""
+    F = np.ascontiguousarray(F, np.int32)
+    D = np.ascontiguousarray(D, np.int32)
+    fac = np.ascontiguousarray(fac, np.int32)
+    loc = np.ascontiguousarray(loc, np.int32)
+    N, k = F.shape[0], len(fac)
+    Np = N - k
+    Fp = np.zeros((Np, Np), np.int32)
+    Dp = np.zeros((Np, Np), np.int32)
+    Bl = np.zeros((Np, Np), np.int32)
+    cst = C.c_int64()
+    _chk(lib().rlt2_subproblem(_p32(F), _p32(D), N, k, _p32(fac), _p32(loc), _p32(Fp), _p32(Dp),
+                               _p32(Bl), C.byref(cst)), "rlt2_subproblem")
+    return Fp, Dp, Bl, cst.value
+
+
+def rlt2_batch_bound(F, D, nodes, iters, stream=0):
+    """nodes: list of (fac, loc) arrays -> (LB per node as int64 array, device ms)."""
+    F = np.ascontiguousarray(F, np.int32)
+    D = np.ascontiguousarray(D, np.int32)
+    keep = [(np.ascontiguousarray(f, np.int32), np.ascontiguousarray(l, np.int32)) for f, l in nodes]
+    arr = (rlt2_node * len(keep))()
+    for b, (f, l) in enumerate(keep):
+        arr[b].k = len(f)
+        arr[b].fac = _p32(f)
+        arr[b].loc = _p32(l)
+    o = rlt2_default_opts()
+    o.stream = stream or None
+    out = np.zeros(len(keep), np.int64)
+    ms = C.c_double()
+    _chk(lib().rlt2_batch_bound(_p32(F), _p32(D), F.shape[0], arr, len(keep), int(iters), C.byref(o),
+                                _p64(out), C.byref(ms)), "rlt2_batch_bound")
+    return out, ms.value
 
 
 # ------------------------------------------------------------ convenience

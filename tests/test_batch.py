@@ -1,0 +1,92 @@
+"""Branch-and-bound nodes: residual instances and batched bounding.
+
+* rlt2_subproblem (host code of the library) against the oracle's own
+  derivation, entry by entry (CPU, no GPU);
+* rlt2_batch_bound (one graph launch for all nodes) against one context per
+  node on the same residual instance, and against the oracle, bit for bit.
+"""
+import numpy as np
+import pytest
+
+from paper_1510_02065_gb300 import build
+from paper_1510_02065_gb300 import instances as I
+from paper_1510_02065_gb300 import rlt2
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return rlt2.lib()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_subproblem_matches_oracle(L, orc, seed):
+    rng = np.random.default_rng(seed)
+    N = int(rng.integers(5, 14))
+    F, D = I.clustered_euclid(N, seed=seed)
+    if seed % 2:
+        F = rng.integers(0, 9, size=(N, N)).astype(np.int32)   # asymmetric
+        np.fill_diagonal(F, 0)
+    k = int(rng.integers(0, N - 2))
+    fac = rng.choice(N, size=k, replace=False)
+    loc = rng.choice(N, size=k, replace=False)
+    Fp, Dp, Bl, cst = rlt2.rlt2_subproblem(F, D, fac, loc)
+    Fo, Do, Blo, csto = orc.subproblem(F, D, fac, loc)
+    assert (Fp == Fo).all() and (Dp == Do).all() and (Bl == Blo).all() and cst == csto
+
+
+def test_subproblem_rejects_repeats(L):
+    F, D = I.uniform_symmetric(6, seed=0)
+    with pytest.raises(rlt2.Rlt2Error):
+        rlt2.rlt2_subproblem(F, D, [1, 1], [2, 3])
+    with pytest.raises(rlt2.Rlt2Error):
+        rlt2.rlt2_subproblem(F, D, [1, 7], [2, 3])
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    rlt2.lib()
+    return t
+
+
+@pytest.mark.gpu
+def test_batch_equals_single_contexts_and_oracle(gpu, orc):
+    F, D = I.clustered_euclid(12, seed=3)
+    nodes = []
+    rng = np.random.default_rng(5)
+    for s in range(10):
+        k = int(rng.integers(0, 8))           # residual sizes 4..12, ragged
+        nodes.append((rng.choice(12, size=k, replace=False), rng.choice(12, size=k, replace=False)))
+    iters = 7
+    lbs, ms = rlt2.rlt2_batch_bound(F, D, nodes, iters)
+    assert ms > 0
+    for b, (fac, loc) in enumerate(nodes):
+        Fp, Dp, Bl, cst = rlt2.rlt2_subproblem(F, D, fac, loc)
+        with rlt2.Context(Fp, Dp, B_lin=Bl, lb_const=cst) as ctx:
+            ctx.iterate(iters)
+            assert ctx.bound()[1] == lbs[b], b
+        st = orc.State(Fp, Dp, B_lin=Bl, lb_const=cst)
+        assert st.run(iters)[-1] == lbs[b], b
+
+
+@pytest.mark.gpu
+def test_batch_of_one_and_zero_passes(gpu):
+    F, D = I.uniform_symmetric(9, seed=2)
+    lbs, _ = rlt2.rlt2_batch_bound(F, D, [(np.array([], np.int32), np.array([], np.int32))], 4)
+    with rlt2.Context(F, D) as ctx:
+        ctx.iterate(4)
+        assert ctx.bound()[1] == lbs[0]
+    fac, loc = np.array([2]), np.array([5])
+    lbs0, _ = rlt2.rlt2_batch_bound(F, D, [(fac, loc)], 0)
+    assert lbs0[0] == rlt2.rlt2_subproblem(F, D, fac, loc)[3]
+
+
+@pytest.mark.gpu
+def test_batch_rejects_too_small_residual(gpu):
+    F, D = I.uniform_symmetric(6, seed=1)
+    with pytest.raises(rlt2.Rlt2Error):
+        rlt2.rlt2_batch_bound(F, D, [(np.arange(4), np.arange(4))], 2)   # N' = 2
