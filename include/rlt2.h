@@ -195,7 +195,7 @@ int rlt2_subproblem(const int32_t *F, const int32_t *D, int N, int k, const int3
  *   lb_out    host, B int64: each node's LB (lb_const included)
  *   ms_out    (may be NULL) milliseconds of device work from the first
  *             initialisation to the last pass (CUDA events)
- *   opts      stream (NULL: the legacy default stream); rlt1_only must be 0
+ *   opts      stream (NULL: a stream created for the call); rlt1_only must be 0
  * One device allocation holds every node's state (about 4 B * N'^2 (N'-1)^2
  * (N'-2) * round_up(N',4) each) and is freed before returning; synchronises.
  * Errors: as rlt2_create, per node.

@@ -510,7 +510,6 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     if (opts) o = *opts;
     else rlt2_default_opts(&o);
     if (o.rlt1_only) return RLT2_E_INVAL;  // the batch runs the full RLT2 dual ascent
-    cudaStream_t s = (cudaStream_t)o.stream;
     int dev = 0, sm_count = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -557,10 +556,18 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     const size_t o_cnt = a.take(4);
     const size_t o_st = a.take(sizeof(DevStatus));
     const size_t o_stage = a.take((size_t)3 * maxN * maxN * 4 * B);
+    // stream capture needs a stream other than the legacy default one
+    cudaStream_t s = (cudaStream_t)o.stream;
+    cudaStream_t own = nullptr;
+    if (!s) {
+        CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+        s = own;
+    }
     char *base = nullptr;
     cudaError_t e = cudaMalloc((void **)&base, a.used);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (own) cudaStreamDestroy(own);
         return cuda_code(e);
     }
     std::vector<NodeDesc> hn(B);
@@ -570,6 +577,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     for (int b = 0; b < B; b++) all_tiles += make_geom(in[b].Np).tiles;
     if (all_tiles >= (1LL << 31)) {  // tile indices of a group are 32-bit
         cudaFree(base);
+        if (own) cudaStreamDestroy(own);
         return RLT2_E_INVAL;
     }
     int ctas = 0, probs = 0, maxTS = 0;
@@ -642,6 +650,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     cudaFree(base);
+    if (own) cudaStreamDestroy(own);
     return rc;
 }
 
