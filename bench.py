@@ -46,7 +46,45 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the cpu_baseline sample (0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-nodes", type=int, default=256,
+                    help="B&B nodes of the batched-bounding measurement (0: skip)")
+    ap.add_argument("--batch-iters", type=int, default=100)
     return ap.parse_args()
+
+
+def batch_measure(rlt2, instances, torch, nodes_count, iters):
+    """Batched B&B bounding against the plain one-node-at-a-time path.
+
+    Nodes of one 25-facility clustered instance, node s fixing 1-15 random
+    facilities (residual sizes 10-24), `iters` passes each.  Batched: one
+    rlt2_batch_bound call (one captured graph for all nodes and passes).
+    Plain: per node rlt2_subproblem, rlt2_create, rlt2_iterate, rlt2_bound,
+    rlt2_destroy.  Both wall-clock, both including every allocation and copy;
+    the bounds must be identical.
+    """
+    F, D = instances.clustered_euclid(25, seed=0)
+    nodes = instances.subproblem_nodes(25, nodes_count)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbs, dev_ms = rlt2.rlt2_batch_bound(F, D, nodes, iters)
+    t_batch = time.perf_counter() - t0
+    s = torch.cuda.Stream()
+    plain = []
+    t0 = time.perf_counter()
+    for fac, loc in nodes:
+        Fp, Dp, Bl, cst = rlt2.rlt2_subproblem(F, D, fac, loc)
+        with rlt2.Context(Fp, Dp, B_lin=Bl, lb_const=cst, max_iters=iters + 1,
+                          stream=s.cuda_stream) as c:
+            c.iterate(iters)
+            plain.append(c.bound()[1])
+    t_plain = time.perf_counter() - t0
+    sizes = [25 - len(f) for f, _ in nodes]
+    return {"metric": "batched B&B nodes/sec vs plain", "unit": "nodes/s",
+            "batched": nodes_count / t_batch, "plain": nodes_count / t_plain,
+            "speedup": t_plain / t_batch, "identical_bounds": list(plain) == [int(x) for x in lbs],
+            "nodes": nodes_count, "iters": iters, "residual_N": [min(sizes), max(sizes)],
+            "batched_device_ms": dev_ms, "graph_launches": 1,
+            "config": "clustered N=25 seed 0, node s fixes 1-15 pairs from default_rng(1000+s)"}
 
 
 def load_peaks():
@@ -333,6 +371,9 @@ def main():
                        "h2d_bytes_per_step": 2 * N * N * 4 / K, "d2h_bytes_per_step": 12,
                        "includes": "rlt2_create (alloc, H2D, init) + per step rlt2_iterate(1) + "
                                    "rlt2_bound + rlt2_destroy"}
+
+    if args.batch_nodes > 0:
+        line["batch"] = batch_measure(rlt2, instances, torch, args.batch_nodes, args.batch_iters)
 
     if rank == 0 and world == 1 and args.cpu_budget > 0:
         t_pass, nslices, rest = oracle_sample(F, D, args.cpu_budget)
