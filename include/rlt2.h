@@ -163,6 +163,33 @@ int rlt2_reset_stage_times(rlt2_ctx *ctx);
 void *rlt2_device_state(rlt2_ctx *ctx, int which);
 int rlt2_row_stride(int N);
 
+/* Bytes of device memory rlt2_create allocates for an instance of size N
+ * (0 for N out of range); max_iters <= 0 means the default. */
+size_t rlt2_state_bytes(int N, int rlt1_only, int max_iters);
+
+/*
+ * Groups: several live contexts advanced together, every stage of every pass
+ * one kernel launch for all of them (continuous batching: a server forms a new
+ * group whenever contexts join or leave).  The group only references the
+ * contexts' device state; each context's results are exactly those of
+ * rlt2_iterate on it alone.
+ *   rlt2_group_create   ctxs[count] (all RLT2 or all RLT1 mode); stream NULL:
+ *                       a stream created for the group.  The group's launches
+ *                       start after every context's pending work.
+ *   rlt2_group_iterate  enqueue k passes of every member (returns at once);
+ *                       every member's later calls wait for them.
+ *   rlt2_group_sync     wait; RLT2_E_TIMEOUT / RLT2_E_INTERNAL if a kernel of
+ *                       the group reported one.
+ *   rlt2_group_destroy  waits, then releases the group (not the contexts).
+ * A context may belong to one group at a time; destroy the group before its
+ * contexts.
+ */
+typedef struct rlt2_group rlt2_group;
+int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group **out);
+int rlt2_group_iterate(rlt2_group *group, int k);
+int rlt2_group_sync(rlt2_group *group);
+void rlt2_group_destroy(rlt2_group *group);
+
 /* A branch-and-bound node (Sec. 6): facility fac[t] is fixed to location
  * loc[t], t < k; the facilities and locations are distinct. */
 typedef struct {

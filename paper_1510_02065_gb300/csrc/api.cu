@@ -461,6 +461,164 @@ void *rlt2_device_state(rlt2_ctx *c, int which)
     }
 }
 
+size_t rlt2_state_bytes(int N, int rlt1_only, int max_iters)
+{
+    if (N < RLT2_MIN_N || N > RLT2_MAX_N) return 0;
+    if (max_iters <= 0) max_iters = 65536;
+    Arena a;
+    plan_node(a, N, !rlt1_only, max_iters);
+    a.take(sizeof(NodeDesc));
+    a.take((size_t)n_triples(N) * sizeof(int4));
+    a.take(4);
+    a.take(sizeof(DevStatus));
+    a.take((size_t)3 * N * N * 4);
+    return a.used;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- groups of contexts
+
+struct rlt2_group {
+    Group g{};
+    char *mem = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    std::vector<rlt2_ctx *> ctxs;
+    cudaEvent_t done = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void free_group(rlt2_group *gr)
+{
+    if (!gr) return;
+    if (gr->stream) cudaStreamSynchronize(gr->stream);
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    if (gr->done) cudaEventDestroy(gr->done);
+    cudaFree(gr->mem);
+    if (gr->own_stream && gr->stream) cudaStreamDestroy(gr->stream);
+    delete gr;
+}
+
+extern "C" {
+
+int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group **out)
+{
+    if (!out || !ctxs || count < 1) return RLT2_E_INVAL;
+    *out = nullptr;
+    for (int b = 0; b < count; b++)
+        if (!ctxs[b] || ctxs[b]->g.rlt1_only != ctxs[0]->g.rlt1_only) return RLT2_E_INVAL;
+    rlt2_group *gr = new (std::nothrow) rlt2_group();
+    if (!gr) return RLT2_E_OOM;
+    auto fail = [&](int code) {
+        free_group(gr);
+        return code;
+    };
+    gr->ctxs.assign(ctxs, ctxs + count);
+    gr->sm_count = ctxs[0]->sm_count;
+    if (stream) {
+        gr->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&gr->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(RLT2_E_CUDA);
+        gr->own_stream = true;
+    }
+    if (cudaEventCreateWithFlags(&gr->done, cudaEventDisableTiming) != cudaSuccess)
+        return fail(RLT2_E_CUDA);
+    int maxN = 0;
+    bool pack = true;
+    for (rlt2_ctx *c : gr->ctxs) {
+        maxN = std::max(maxN, c->node.N);
+        pack = pack && c->g.pack;
+    }
+    const int JC = p1_chunk(maxN);
+    const std::vector<int4> tri = triple_table(maxN);
+    Arena a;
+    const size_t o_nodes = a.take((size_t)count * sizeof(NodeDesc));
+    const size_t o_tri = a.take(tri.size() * sizeof(int4));
+    const size_t o_cnt = a.take(4);
+    const size_t o_st = a.take(sizeof(DevStatus));
+    cudaError_t e = cudaMalloc((void **)&gr->mem, a.used);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        gr->mem = nullptr;
+        return fail(cuda_code(e));
+    }
+    std::vector<NodeDesc> hn(count);
+    long long tiles = 0;
+    int ctas = 0, probs = 0, maxTS = 0;
+    for (int b = 0; b < count; b++) {
+        NodeDesc &nd = hn[b];
+        nd = gr->ctxs[b]->node;            // the context's own state, shared
+        fill_node(nd, nd.N, JC);           // the group's location chunk
+        nd.tile_base = tiles;
+        nd.cta_base = ctas;
+        nd.prob_base = probs;
+        tiles += nd.tiles;
+        ctas += (int)(n_triples(nd.N) * nd.nchunks);
+        probs += nd.N * nd.N;
+        maxTS = std::max(maxTS, nd.TS);
+    }
+    if (tiles >= (1LL << 31)) return fail(RLT2_E_INVAL);
+    Group &g = gr->g;
+    g.nodes = reinterpret_cast<const NodeDesc *>(gr->mem + o_nodes);
+    g.B = count;
+    g.tiles = tiles;
+    g.ctas = ctas;
+    g.probs = probs;
+    g.maxN = maxN;
+    g.maxTS = maxTS;
+    g.JC = JC;
+    g.pack = pack;
+    g.rlt1_only = ctxs[0]->g.rlt1_only;
+    g.counter = reinterpret_cast<unsigned *>(gr->mem + o_cnt);
+    g.status = reinterpret_cast<DevStatus *>(gr->mem + o_st);
+    g.triples = reinterpret_cast<const int4 *>(gr->mem + o_tri);
+    // the group's stream starts after every context's pending work
+    for (rlt2_ctx *c : gr->ctxs) {
+        if (cudaEventRecord(gr->done, c->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(gr->stream, gr->done, 0) != cudaSuccess)
+            return fail(RLT2_E_CUDA);
+    }
+    e = cudaMemcpyAsync(gr->mem + o_nodes, hn.data(), (size_t)count * sizeof(NodeDesc),
+                        cudaMemcpyHostToDevice, gr->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(gr->mem + o_tri, tri.data(), tri.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, gr->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.status, 0, sizeof(DevStatus), gr->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.counter, 0, 4, gr->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(gr->stream);  // host copies are on the stack
+    if (e != cudaSuccess) return fail(cuda_code(e));
+    *out = gr;
+    return RLT2_OK;
+}
+
+int rlt2_group_iterate(rlt2_group *gr, int k)
+{
+    if (!gr || k < 0) return RLT2_E_INVAL;
+    for (rlt2_ctx *c : gr->ctxs)
+        if ((long long)c->enqueued + k > c->opts.max_iters) return RLT2_E_STATE;
+    if (k == 0) return RLT2_OK;
+    if (!gr->exec) CK(capture_passes(gr->g, gr->sm_count, gr->stream, 1, &gr->graph, &gr->exec));
+    for (int t = 0; t < k; t++) CK(cudaGraphLaunch(gr->exec, gr->stream));
+    for (rlt2_ctx *c : gr->ctxs) c->enqueued += k;
+    // every context's later work starts after the group's passes
+    CK(cudaEventRecord(gr->done, gr->stream));
+    for (rlt2_ctx *c : gr->ctxs) CK(cudaStreamWaitEvent(c->stream, gr->done, 0));
+    return RLT2_OK;
+}
+
+int rlt2_group_sync(rlt2_group *gr)
+{
+    if (!gr) return RLT2_E_INVAL;
+    return group_status(gr->g, gr->stream);
+}
+
+void rlt2_group_destroy(rlt2_group *gr) { free_group(gr); }
+
 // ----------------------------------------------------- branch-and-bound nodes
 
 int rlt2_subproblem(const int32_t *F, const int32_t *D, int N, int k, const int32_t *fac,

@@ -82,6 +82,11 @@ def lib():
         "rlt2_row_stride": (C.c_int, [C.c_int]),
         "rlt2_lap_batch": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "rlt2_lap_batch_static": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "rlt2_state_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+        "rlt2_group_create": (C.c_int, [C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)]),
+        "rlt2_group_iterate": (C.c_int, [_vp, C.c_int]),
+        "rlt2_group_sync": (C.c_int, [_vp]),
+        "rlt2_group_destroy": (None, [_vp]),
         "rlt2_subproblem": (C.c_int, [_i32p, _i32p, C.c_int, C.c_int, _i32p, _i32p, _i32p, _i32p,
                                       _i32p, _i64p]),
         "rlt2_batch_bound": (C.c_int, [_i32p, _i32p, C.c_int, C.POINTER(rlt2_node), C.c_int, C.c_int,
@@ -216,6 +221,29 @@ def rlt2_lap_batch_static(M_ptr, n, count, S_ptr, assign_ptr=0, u_ptr=0, v_ptr=0
                                        _vp(assign_ptr or None), _vp(u_ptr or None),
                                        _vp(v_ptr or None), _vp(work_ptr or None),
                                        _vp(stream or None))
+
+
+def rlt2_state_bytes(N, rlt1_only=False, max_iters=65536) -> int:
+    return int(lib().rlt2_state_bytes(int(N), int(rlt1_only), int(max_iters)))
+
+
+def rlt2_group_create(ctxs, stream=0):
+    arr = (_vp * len(ctxs))(*ctxs)
+    out = _vp()
+    _chk(lib().rlt2_group_create(arr, len(ctxs), _vp(stream or None), C.byref(out)), "rlt2_group_create")
+    return out.value
+
+
+def rlt2_group_iterate(group, k):
+    _chk(lib().rlt2_group_iterate(_vp(group), int(k)), "rlt2_group_iterate")
+
+
+def rlt2_group_sync(group):
+    _chk(lib().rlt2_group_sync(_vp(group)), "rlt2_group_sync")
+
+
+def rlt2_group_destroy(group):
+    lib().rlt2_group_destroy(_vp(group))
 
 
 def rlt2_subproblem(F, D, fac, loc):

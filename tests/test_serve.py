@@ -1,0 +1,71 @@
+"""The continuous-batching server: every result in the mix equals the request
+bounded alone; admission respects the memory budget; oversize requests are
+rejected, not crashed."""
+import numpy as np
+import pytest
+
+from paper_1510_02065_gb300 import instances as I
+from paper_1510_02065_gb300 import rlt2
+from paper_1510_02065_gb300.serve import BoundServer, Request
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_02065_gb300 import build
+    build.build()
+    rlt2.lib()
+    return t
+
+
+def _requests(seed, count):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for r in range(count):
+        N = int(rng.integers(5, 12))
+        F, D = I.clustered_euclid(N, seed=100 + r)
+        reqs.append(Request(rid=r, F=F, D=D, iters=int(rng.integers(2, 9)),
+                            arrival=float(rng.integers(0, 12))))
+    return reqs
+
+
+def test_mix_equals_alone_and_budget_holds(gpu, orc):
+    reqs = _requests(1, 14)
+    biggest = max(rlt2.rlt2_state_bytes(r.N, False, r.iters + 1) for r in reqs)
+    budget = int(2.5 * biggest)
+    srv = BoundServer(mem_budget=budget, max_slots=6, passes_per_round=2)
+    stats = srv.serve(reqs, realtime=False)
+    assert stats["completed"] == len(reqs) and stats["rejected"] == 0
+    assert srv.peak_bytes <= budget
+    assert stats["mean_resident"] > 1.0          # requests really shared launches
+    for r in reqs:
+        with rlt2.Context(r.F, r.D) as ctx:
+            ctx.iterate(r.iters)
+            assert ctx.bound()[1] == r.lb, r.rid
+    for r in reqs[:4]:
+        assert orc.State(r.F, r.D).run(r.iters)[-1] == r.lb
+
+
+def test_oversize_request_is_rejected(gpu):
+    F, D = I.clustered_euclid(9, seed=0)
+    small = Request(rid=0, F=F, D=D, iters=3)
+    F2, D2 = I.clustered_euclid(14, seed=1)
+    big = Request(rid=1, F=F2, D=D2, iters=3)
+    srv = BoundServer(mem_budget=rlt2.rlt2_state_bytes(9, False, 4) + 1024)
+    stats = srv.serve([small, big], realtime=False)
+    assert stats["completed"] == 1 and stats["rejected"] == 1
+    assert big.error and small.lb is not None
+
+
+def test_realtime_latency_stats(gpu):
+    reqs = _requests(2, 6)
+    for r in reqs:
+        r.arrival = r.arrival * 0.01
+    stats = BoundServer(mem_budget=1 << 30).serve(reqs, realtime=True)
+    assert stats["completed"] == 6
+    assert 0 < stats["p50_latency"] <= stats["p99_latency"]
+    assert stats["throughput"] > 0
