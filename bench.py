@@ -49,7 +49,67 @@ def parse():
     ap.add_argument("--batch-nodes", type=int, default=256,
                     help="B&B nodes of the batched-bounding measurement (0: skip)")
     ap.add_argument("--batch-iters", type=int, default=100)
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the serving measurement (0: skip)")
+    ap.add_argument("--n35-steps", type=int, default=30,
+                    help="timed passes of the 35-facility root bound (0: skip)")
     return ap.parse_args()
+
+
+def serve_measure(instances, torch, count, passes=50, rate=50.0):
+    """Continuous-batching server on a Poisson stream of bound requests.
+
+    Arrivals: Poisson (rate/s, exponential gaps from default_rng(7)); request r
+    is the clustered instance of size N_r uniform in [12, 30] with seed r, 50
+    passes.  Admission by device memory (budget 64 GB).  If the measured
+    throughput is below the offered rate (saturation), the stream is served
+    again at 0.8x the measured capacity and both runs are reported.
+    """
+    from paper_1510_02065_gb300.serve import BoundServer, Request
+
+    def run(r):
+        arr, Ns = instances.poisson_requests(count, rate=r)
+        reqs = []
+        for rid in range(count):
+            F, D = instances.clustered_euclid(int(Ns[rid]), seed=rid)
+            reqs.append(Request(rid=rid, F=F, D=D, iters=passes, arrival=float(arr[rid])))
+        s = torch.cuda.Stream()
+        srv = BoundServer(mem_budget=64 << 30, max_slots=64, passes_per_round=5, stream=s.cuda_stream)
+        st = srv.serve(reqs, realtime=True)
+        st["offered_rate"] = r
+        return st
+
+    first = run(rate)
+    out = {"metric": "served RLT2 bound requests", "unit": "requests/s", "passes": passes,
+           "N_range": [12, 30], "offered": first}
+    if first["throughput"] is not None and first["throughput"] < 0.95 * rate:
+        out["at_0.8_capacity"] = run(0.8 * first["throughput"])
+    return out
+
+
+def n35_measure(rlt2, instances, torch, steps, warmup=3):
+    """Root bound of the 35-facility clustered instance (dense D store)."""
+    F, D, _ = instances.instance("clustered_n35")
+    s = torch.cuda.Stream()
+    with rlt2.Context(F, D, profile=True, max_iters=steps + warmup + 1, stream=s.cuda_stream) as c:
+        c.iterate(warmup)
+        torch.cuda.synchronize()
+        rlt2.rlt2_reset_stage_times(c.ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        c.iterate(steps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms, n = c.stage_times()
+        lb = c.bound()[1]
+    t = e0.elapsed_time(e1)
+    return {"metric": "RLT2 dual-ascent iters/sec at N=35", "unit": "iters/s",
+            "value": steps / (t / 1000.0), "steps": steps, "LB": lb,
+            "stages_ms": {"spread_complementary_D": ms[0] / n, "concentrate_D_to_C": ms[1] / n,
+                          "complementary_C_concentrate_C_to_B": ms[2] / n,
+                          "concentrate_B_to_LB": ms[3] / n},
+            "store": "dense (%.2f GB)" % (rlt2.rlt2_state_bytes(35) / 1e9)}
 
 
 def batch_measure(rlt2, instances, torch, nodes_count, iters):
@@ -374,6 +434,10 @@ def main():
 
     if args.batch_nodes > 0:
         line["batch"] = batch_measure(rlt2, instances, torch, args.batch_nodes, args.batch_iters)
+    if args.n35_steps > 0:
+        line["n35"] = n35_measure(rlt2, instances, torch, args.n35_steps)
+    if args.serve_requests > 0:
+        line["serve"] = serve_measure(instances, torch, args.serve_requests)
 
     if rank == 0 and world == 1 and args.cpu_budget > 0:
         t_pass, nslices, rest = oracle_sample(F, D, args.cpu_budget)
