@@ -304,6 +304,7 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
     g.triples = reinterpret_cast<const int4 *>(base + o_tri);
+    g.first = nd;
 
     e = cudaMemcpyAsync(base + o_node, &nd, sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
@@ -577,6 +578,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     g.counter = reinterpret_cast<unsigned *>(gr->mem + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(gr->mem + o_st);
     g.triples = reinterpret_cast<const int4 *>(gr->mem + o_tri);
+    g.first = hn[0];
     // the group's stream starts after every context's pending work
     for (rlt2_ctx *c : gr->ctxs) {
         if (cudaEventRecord(gr->done, c->stream) != cudaSuccess ||
@@ -764,6 +766,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
     g.triples = reinterpret_cast<const int4 *>(base + o_tri);
+    g.first = hn[0];
 
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaGraph_t graph = nullptr;

@@ -94,6 +94,7 @@ struct Group {
     unsigned *counter;      // D->C work counter
     DevStatus *status;      // error bits and work counters of the group
     const int4 *triples;    // facility triples i<k<p ordered by p: the first C(N,3) serve N
+    NodeDesc first;         // copy of nodes[0]: kernels of a group of one read it as a parameter
 };
 
 int p1_chunk(int N);                   // locations per CTA of the fused pass over D

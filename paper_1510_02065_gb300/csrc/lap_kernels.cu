@@ -23,13 +23,64 @@ constexpr int kBatchWarps = 4;
 
 // ------------------------------------------------------------ D -> C sweep
 
-// One tile buffer per warp; a warp takes group-wide tile indices from a global
-// counter, finds the tile's instance, brings the tile in with one bulk copy
-// and solves its LAP.  Tiles of one instance are consecutive in the group-wide
-// order, so the instance found for the previous tile is tried first.
+// One tile of D -> C: bring tile t of instance nd into buf with one bulk copy,
+// solve its LAP, write the residual tile back in place and S to yS.  Returns
+// false if the copy did not complete within the spin limit (recorded in
+// status; the copy in flight has landed or been waited for, bounded).
 template <int NS, bool PACK>
-__global__ void __launch_bounds__(kDlapWarps * 32) dlap_kernel(Group g)
+__device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *buf, uint64_t *bar,
+                                          unsigned &parity, int *uRow, int lane, unsigned &steps,
+                                          unsigned &relax, DevStatus *status)
 {
+    const int N = nd.N, W = nd.W, n = N - 2, m = N - 1, TS = nd.TS;
+    if (lane == 0) {
+        fence_proxy_async_smem();
+        bulk_load(buf, nd.p.z + (size_t)t * TS, (unsigned)TS * 4u, bar);
+    }
+    if (!__all_sync(kFull, mbar_wait(bar, parity))) {
+        if (lane == 0) atomicOr(&status->err, kDevTimeout);
+        mbar_wait(bar, parity);
+        __syncwarp();
+        return false;
+    }
+    parity ^= 1u;
+
+    // the tile's own locations j and n are the columns without coefficient
+    const unsigned ij = fdiv(t, nd.fmm);
+    const unsigned rem = t - ij * (unsigned)(m * m);
+    const int nn = (int)(rem - fdiv(rem, nd.fm) * (unsigned)m);
+    const int j = (int)(ij - fdiv(ij, nd.fN) * (unsigned)N);
+    const int nl = nn + (nn >= j);
+    int rowOf[NS], uM[NS], v[NS];
+    if (!warp_hungarian<NS, PACK>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
+        atomicOr(&status->err, kDevInternal);
+    scatter_rows<NS>(n, N, j, nl, rowOf, uM, uRow, nullptr);
+    __syncwarp();
+    int *gz = nd.p.z + (size_t)t * TS;
+    for (int r = 0; r < n; ++r) {
+        const int ur = uRow[r];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int c = lane + 32 * s;
+            if (c < W) gz[r * W + c] = (c < N && c != j && c != nl) ? buf[r * W + c] - ur - v[s] : 0;
+        }
+    }
+    const long long S = lap_value<NS>(N, j, nl, uM, v);
+    if (lane == 0) nd.p.yS[t] = (int)S;
+    __syncwarp();
+    return true;
+}
+
+// One tile buffer per warp; a warp takes group-wide tile indices from a global
+// counter, finds the tile's instance and solves the tile's LAP.  Tiles of one
+// instance are consecutive in the group-wide order, so the instance found for
+// the previous tile is tried first.  ONE (a group of one instance): the
+// instance is the kernel parameter g.first, read from parameter space, and the
+// stopping rule is checked once.
+template <int NS, bool PACK, bool ONE>
+__global__ void __launch_bounds__(kDlapWarps * 32, 16) dlap_kernel(Group g)
+{
+    if (ONE && *g.first.p.stop) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * g.maxTS;
@@ -52,49 +103,19 @@ __global__ void __launch_bounds__(kDlapWarps * 32) dlap_kernel(Group g)
         if (lane == 0) T = atomicAdd(g.counter, 1u);
         T = __shfl_sync(kFull, T, 0);
         if (T >= ntiles) break;
-        if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
-            b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
-        const NodeDesc &nd = g.nodes[b];
-        if (*nd.p.stop) continue;
-        const unsigned t = T - (unsigned)nd.tile_base;
-        const int N = nd.N, W = nd.W, n = N - 2, m = N - 1, TS = nd.TS;
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            bulk_load(buf, nd.p.z + (size_t)t * TS, (unsigned)TS * 4u, bar);
+        bool ok;
+        if constexpr (ONE) {
+            ok = dlap_tile<NS, PACK>(g.first, T, buf, bar, parity, uRow, lane, steps, relax, g.status);
+        } else {
+            if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
+                b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
+            const NodeDesc &nd = g.nodes[b];
+            if (*nd.p.stop) continue;
+            ok = dlap_tile<NS, PACK>(nd, T - (unsigned)nd.tile_base, buf, bar, parity, uRow, lane, steps,
+                                     relax, g.status);
         }
-        if (!__all_sync(kFull, mbar_wait(bar, parity))) {
-            // give up: record it, let the copy in flight land (bounded), leave
-            if (lane == 0) atomicOr(&g.status->err, kDevTimeout);
-            mbar_wait(bar, parity);
-            __syncwarp();
-            return;
-        }
-        parity ^= 1u;
-
-        // the tile's own locations j and n are the columns without coefficient
-        const unsigned ij = fdiv(t, nd.fmm);
-        const unsigned rem = t - ij * (unsigned)(m * m);
-        const int nn = (int)(rem - fdiv(rem, nd.fm) * (unsigned)m);
-        const int j = (int)(ij - fdiv(ij, nd.fN) * (unsigned)N);
-        const int nl = nn + (nn >= j);
-        int rowOf[NS], uM[NS], v[NS];
-        if (!warp_hungarian<NS, PACK>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
-            atomicOr(&g.status->err, kDevInternal);
-        scatter_rows<NS>(n, N, j, nl, rowOf, uM, uRow, nullptr);
-        __syncwarp();
-        int *gz = nd.p.z + (size_t)t * TS;
-        for (int r = 0; r < n; ++r) {
-            const int ur = uRow[r];
-#pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                const int c = lane + 32 * s;
-                if (c < W) gz[r * W + c] = (c < N && c != j && c != nl) ? buf[r * W + c] - ur - v[s] : 0;
-            }
-        }
-        const long long S = lap_value<NS>(N, j, nl, uM, v);
-        if (lane == 0) nd.p.yS[t] = (int)S;
+        if (!ok) return;
         ++laps;
-        __syncwarp();
     }
     if (lane == 0 && laps) {
         atomicAdd(&g.status->laps, (unsigned long long)laps);
@@ -274,11 +295,11 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
 
 // ---------------------------------------------------------------- launchers
 
-template <int NS, bool PACK>
+template <int NS, bool PACK, bool ONE>
 static cudaError_t dlap_go(const Group &g, int sm_count, cudaStream_t s)
 {
     const size_t smem = (size_t)kDlapWarps * ((size_t)g.maxTS * 4 + 8 + 256);
-    auto k = dlap_kernel<NS, PACK>;
+    auto k = dlap_kernel<NS, PACK, ONE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -296,8 +317,14 @@ static cudaError_t dlap_go(const Group &g, int sm_count, cudaStream_t s)
 // The work counter is reset by the fused pass over D, which precedes this kernel.
 cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s)
 {
-    if (g.maxN <= 32) return g.pack ? dlap_go<1, true>(g, sm_count, s) : dlap_go<1, false>(g, sm_count, s);
-    return g.pack ? dlap_go<2, true>(g, sm_count, s) : dlap_go<2, false>(g, sm_count, s);
+    if (g.B == 1) {
+        if (g.maxN <= 32)
+            return g.pack ? dlap_go<1, true, true>(g, sm_count, s) : dlap_go<1, false, true>(g, sm_count, s);
+        return g.pack ? dlap_go<2, true, true>(g, sm_count, s) : dlap_go<2, false, true>(g, sm_count, s);
+    }
+    if (g.maxN <= 32)
+        return g.pack ? dlap_go<1, true, false>(g, sm_count, s) : dlap_go<1, false, false>(g, sm_count, s);
+    return g.pack ? dlap_go<2, true, false>(g, sm_count, s) : dlap_go<2, false, false>(g, sm_count, s);
 }
 
 template <int NS, bool PACK>

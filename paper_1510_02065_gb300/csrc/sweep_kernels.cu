@@ -122,13 +122,15 @@ __device__ __forceinline__ void copy_piece(int *dst, const int *src)
 }
 
 // One CTA per (instance, facility triple, location chunk) of the group; yS
-// holds c' (C plus the spread of B) per tile.
-template <int JC>
+// holds c' (C plus the spread of B) per tile.  ONE (a group of one instance):
+// the instance is the kernel parameter g.first.
+template <int JC, bool ONE>
 __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) *g.counter = 0;  // work counter of the D -> C sweep
     const NodeDesc &nd =
-        g.nodes[find_node(g.nodes, g.B, blockIdx.x, [](const NodeDesc &d) { return (long long)d.cta_base; })];
+        ONE ? g.first
+            : g.nodes[find_node(g.nodes, g.B, blockIdx.x, [](const NodeDesc &d) { return (long long)d.cta_base; })];
     const PassState p = nd.p;
     if (*p.stop) return;
     const int N = nd.N, W = nd.W, nchunks = nd.nchunks;
@@ -251,11 +253,14 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
 // Costs spreading from B to C (Sec. 4.2): c'_ijkn = c_ijkn + the share of b_ij
 // of row k (k' = rank of k among the facilities != i), written to yS.  One
 // thread per tile of the group.
+template <bool ONE>
 __global__ void spread_x_to_y_kernel(Group g)
 {
+    if (ONE && *g.first.p.stop) return;
     for (long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x; T < g.tiles;
          T += (long long)gridDim.x * blockDim.x) {
-        const NodeDesc &nd = g.nodes[find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; })];
+        const NodeDesc &nd =
+            ONE ? g.first : g.nodes[find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; })];
         if (*nd.p.stop) continue;
         const unsigned t = (unsigned)(T - nd.tile_base);
         const unsigned ij = fdiv(t, nd.fmm);
@@ -269,7 +274,8 @@ cudaError_t launch_spread_x(const Group &g, cudaStream_t s)
 {
     long long blocks = (g.tiles + 255) / 256;
     if (blocks > 8192) blocks = 8192;
-    spread_x_to_y_kernel<<<(unsigned)blocks, 256, 0, s>>>(g);
+    if (g.B == 1) spread_x_to_y_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(g);
+    else spread_x_to_y_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -317,7 +323,7 @@ template <int JC>
 static cudaError_t p1_go(const Group &g, cudaStream_t s)
 {
     const size_t smem = p1_smem_bytes(g.maxN, JC);
-    auto k = p1_kernel<JC>;
+    auto k = g.B == 1 ? p1_kernel<JC, true> : p1_kernel<JC, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<g.ctas, kP1Threads, smem, s>>>(g);
