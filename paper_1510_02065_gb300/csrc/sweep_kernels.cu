@@ -149,20 +149,26 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
     int *__restrict__ z = p.z;
     const int NN = N * N;
 
-    // ---- loads, all in flight at once: full rows in 16-byte pieces, then the
-    // JC-location pieces of kinds 4 and 6 (one aligned copy each)
-    for (int e = threadIdx.x; e < 4 * JC * N * W4; e += kP1Threads) {
-        const int rowid = (int)fdiv((unsigned)e, fW4), h = e - rowid * W4;
-        const int qj = (int)fdiv((unsigned)rowid, fN), x = rowid - qj * N;
+    // ---- loads, all in flight at once: every full row by one bulk copy
+    // completing on bar, then the JC-location pieces of kinds 4 and 6 (one
+    // aligned cp.async each)
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const unsigned rowBytes = (unsigned)W * 4u;
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, (unsigned)(4 * jc * (N - 1)) * rowBytes);
+    for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
+        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
         const int q = qj / JC, jj = qj % JC, j = j0 + jj;
         if (jj >= jc || x == j) continue;
         int t, row;
         full_row(q, N, i, k, pp, j, x, t, row);
         const int base = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
         const int pitch = q < 2 ? L.S13 : L.S25;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(sm + base + (jj * N + x) * pitch + 4 * h)),
-                     "l"(z + t * TS + (size_t)row * W + 4 * h)
-                     : "memory");
+        bulk_load_tx(sm + base + (jj * N + x) * pitch, z + t * TS + (size_t)row * W, rowBytes, &bar);
     }
     for (int e = threadIdx.x; e < 2 * NN; e += kP1Threads) {
         const int kind = e >= NN, r2 = e - kind * NN;
@@ -193,7 +199,13 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
     }
 
     asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
+    if (__syncthreads_or(!mbar_wait(&bar, 0))) {
+        // give up: record it, let the copies in flight land (bounded), leave
+        if (threadIdx.x == 0) atomicOr(&g.status->err, kDevTimeout);
+        mbar_wait(&bar, 0);
+        __syncthreads();
+        return;
+    }
 
     // ---- split every class {(i,j),(k,nn),(p,qq)}, j in the chunk: one warp
     // per (j, nn), lanes over qq
@@ -226,21 +238,22 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
             }
         }
     }
+    fence_proxy_async_smem();
     __syncthreads();
 
-    // ---- write back: 16-byte stores of whole rows and pieces
-    for (int e = threadIdx.x; e < 4 * JC * N * W4; e += kP1Threads) {
-        const int rowid = (int)fdiv((unsigned)e, fW4), h = e - rowid * W4;
-        const int qj = (int)fdiv((unsigned)rowid, fN), x = rowid - qj * N;
+    // ---- write back: whole rows by bulk stores (after the split's shared
+    // writes are made visible to the async proxy), pieces by 16-byte stores
+    for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
+        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
         const int q = qj / JC, jj = qj % JC, j = j0 + jj;
         if (jj >= jc || x == j) continue;
         int t, row;
         full_row(q, N, i, k, pp, j, x, t, row);
         const int base = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
         const int pitch = q < 2 ? L.S13 : L.S25;
-        *reinterpret_cast<int4 *>(z + t * TS + (size_t)row * W + 4 * h) =
-            *reinterpret_cast<const int4 *>(sm + base + (jj * N + x) * pitch + 4 * h);
+        bulk_store(z + t * TS + (size_t)row * W, sm + base + (jj * N + x) * pitch, rowBytes);
     }
+    bulk_commit();
     for (int e = threadIdx.x; e < 2 * NN; e += kP1Threads) {
         const int kind = e >= NN, r2 = e - kind * NN;
         const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
@@ -248,6 +261,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
         const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
         copy_piece<JC>(z + t * TS + (size_t)i * W + j0, sm + (kind ? L.A6 : L.A4) + a * L.P46 + l * JC);
     }
+    bulk_wait_read_all();  // shared memory stays valid until the bulk stores have read it
 }
 
 // Costs spreading from B to C (Sec. 4.2): c'_ijkn = c_ijkn + the share of b_ij
