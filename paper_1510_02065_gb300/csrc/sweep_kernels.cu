@@ -47,8 +47,10 @@ __device__ __forceinline__ int share(int x, const FastDiv &fm, int t)
 
 // Shared-memory layout of one work unit (offsets in ints, all 16-byte aligned).
 // Rows of kinds 1 and 3 are indexed (jj, location), pitch W; rows of kinds 2
-// and 5 likewise with pitch W + 4 (read by column); the JC-location pieces of
-// kinds 4 and 6 are indexed (a, l) with an odd number of pieces per a.
+// and 5 likewise, read by column, with pitch S25 = 4 x odd (W, or W + 4 when
+// W / 4 is even): a column read across 32 rows then meets 8 distinct banks,
+// the fewest 16-byte-aligned rows allow.  The JC-location pieces of kinds 4
+// and 6 are indexed (a, l) with an odd number of pieces per a.
 struct P1Layout {
     int S13, S25, P46, H6p;
     int A1, A3, A2, A5, A4, A6, H1, H3, H2, H5, H4, H6, total;
@@ -60,7 +62,7 @@ __host__ __device__ inline P1Layout p1_layout(int N, int W, int JC)
 {
     P1Layout L;
     L.S13 = W;
-    L.S25 = W + 4;
+    L.S25 = (W / 4) % 2 ? W : W + 4;
     L.P46 = JC * (N | 1);
     L.H6p = N | 1;
     int o = 0;
@@ -119,6 +121,29 @@ __device__ __forceinline__ void copy_piece(int *dst, const int *src)
     if constexpr (JC == 4) *reinterpret_cast<int4 *>(dst) = *reinterpret_cast<const int4 *>(src);
     else if constexpr (JC == 2) *reinterpret_cast<int2 *>(dst) = *reinterpret_cast<const int2 *>(src);
     else *dst = *src;
+}
+
+// JC consecutive ints of shared memory (JC-aligned) to registers and back.
+template <int JC>
+__device__ __forceinline__ void load_piece(int (&r)[JC], const int *src)
+{
+    if constexpr (JC == 4) {
+        const int4 v = *reinterpret_cast<const int4 *>(src);
+        r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else if constexpr (JC == 2) {
+        const int2 v = *reinterpret_cast<const int2 *>(src);
+        r[0] = v.x; r[1] = v.y;
+    } else {
+        r[0] = *src;
+    }
+}
+
+template <int JC>
+__device__ __forceinline__ void store_piece(int *dst, const int (&r)[JC])
+{
+    if constexpr (JC == 4) *reinterpret_cast<int4 *>(dst) = make_int4(r[0], r[1], r[2], r[3]);
+    else if constexpr (JC == 2) *reinterpret_cast<int2 *>(dst) = make_int2(r[0], r[1]);
+    else *dst = r[0];
 }
 
 // One CTA per (instance, facility triple, location chunk) of the group; yS
@@ -208,34 +233,38 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
     }
 
     // ---- split every class {(i,j),(k,nn),(p,qq)}, j in the chunk: one warp
-    // per (j, nn), lanes over qq
-    for (int jj = 0; jj < jc; ++jj) {
-        const int j = j0 + jj;
-        for (int nn = warp; nn < N; nn += kP1Warps) {
-            if (nn == j) continue;
-            const int h1 = sm[L.H1 + jj * N + nn], h3 = sm[L.H3 + jj * N + nn];
-            int *r1 = sm + L.A1 + (jj * N + nn) * L.S13;
-            int *r3 = sm + L.A3 + (jj * N + nn) * L.S13;
-            int *c2 = sm + L.A2 + jj * N * L.S25 + nn;    // column nn of the kind-2 rows
-            int *c5 = sm + L.A5 + jj * N * L.S25 + nn;
-            int *r4 = sm + L.A4 + nn * L.P46 + jj;        // pieces (nn, qq)
-            int *c6 = sm + L.A6 + nn * JC + jj;           // pieces (qq, nn)
-            const int *h2 = sm + L.H2 + jj * N, *h5 = sm + L.H5 + jj * N;
-            const int *h4 = sm + L.H4 + nn * N, *h6 = sm + L.H6 + nn;
-            for (int qq = lane; qq < N; qq += 32) {
-                if (qq == j || qq == nn) continue;
-                int *a2 = c2 + qq * L.S25, *a5 = c5 + qq * L.S25;
-                int *a4 = r4 + qq * JC, *a6 = c6 + qq * L.P46;
-                const int T = r1[qq] + h1 + *a2 + h2[qq] + r3[qq] + h3 + *a4 + h4[qq] + *a5 +
-                              h5[qq] + *a6 + h6[qq * L.H6p];
+    // per nn, lanes over qq, each lane the JC classes of its (nn, qq).  Their
+    // members of kinds 4 and 6 are exactly the pieces (nn, qq) and (qq, nn),
+    // which move as one vector each.
+    for (int nn = warp; nn < N; nn += kP1Warps) {
+        const int *h4 = sm + L.H4 + nn * N, *h6 = sm + L.H6 + nn;
+        for (int qq = lane; qq < N; qq += 32) {
+            if (qq == nn) continue;
+            int *a4 = sm + L.A4 + nn * L.P46 + qq * JC;   // piece (nn, qq)
+            int *a6 = sm + L.A6 + qq * L.P46 + nn * JC;   // piece (qq, nn)
+            int p4[JC], p6[JC];
+            load_piece<JC>(p4, a4);
+            load_piece<JC>(p6, a6);
+            const int h46 = h4[qq] + h6[qq * L.H6p];
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj) {
+                const int j = j0 + jj;
+                if (jj >= jc || j == nn || j == qq) continue;
+                const int rn = jj * N + nn, rq = jj * N + qq;
+                int *a1 = sm + L.A1 + rn * L.S13 + qq, *a3 = sm + L.A3 + rn * L.S13 + qq;
+                int *a2 = sm + L.A2 + rq * L.S25 + nn, *a5 = sm + L.A5 + rq * L.S25 + nn;
+                const int T = *a1 + sm[L.H1 + rn] + *a2 + sm[L.H2 + rq] + *a3 + sm[L.H3 + rn] + p4[jj] +
+                              *a5 + sm[L.H5 + rq] + p6[jj] + h46;
                 const int q6 = T / 6, rm = T - 6 * q6;
-                r1[qq] = q6 + (0 < rm);   // ranks: d_ijknpq 0, d_ijpqkn 1, d_knijpq 2,
+                *a1 = q6 + (0 < rm);      // ranks: d_ijknpq 0, d_ijpqkn 1, d_knijpq 2,
                 *a2 = q6 + (1 < rm);      //        d_knpqij 3, d_pqijkn 4, d_pqknij 5
-                r3[qq] = q6 + (2 < rm);
-                *a4 = q6 + (3 < rm);
+                *a3 = q6 + (2 < rm);
+                p4[jj] = q6 + (3 < rm);
                 *a5 = q6 + (4 < rm);
-                *a6 = q6 + (5 < rm);
+                p6[jj] = q6 + (5 < rm);
             }
+            store_piece<JC>(a4, p4);
+            store_piece<JC>(a6, p6);
         }
     }
     fence_proxy_async_smem();

@@ -93,6 +93,7 @@ WORKLOADS = {
     "uniform_n8": (uniform_symmetric, dict(N=8, seed=0), 50),
     "grid_n12": (grid_manhattan, dict(N=12, rows=3, cols=4, seed=0), 100),
     "clustered_n20": (clustered_euclid, dict(N=20, seed=0), 200),
+    "clustered_n25": (clustered_euclid, dict(N=25, seed=0), 100),
     "clustered_n30": (clustered_euclid, dict(N=30, seed=0), 50),
     "clustered_n35": (clustered_euclid, dict(N=35, seed=0), 300),
 }
