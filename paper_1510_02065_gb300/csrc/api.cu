@@ -286,6 +286,7 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
     NodeDesc &nd = c->node;
     fill_node(nd, N, JC);
     nd.p = node_state(base, no, c->opts.max_iters, c->opts);
+    encode_zmap(nd, JC);
     nd.tile_base = 0;
     nd.cta_base = 0;
     nd.prob_base = 0;
@@ -555,6 +556,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
         NodeDesc &nd = hn[b];
         nd = gr->ctxs[b]->node;            // the context's own state, shared
         fill_node(nd, nd.N, JC);           // the group's location chunk
+        encode_zmap(nd, JC);
         nd.tile_base = tiles;
         nd.cta_base = ctas;
         nd.prob_base = probs;
@@ -745,6 +747,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
         NodeDesc &nd = hn[b];
         fill_node(nd, in[b].Np, JC);
         nd.p = node_state(base, no[b], hist_cap, o);
+        encode_zmap(nd, JC);
         nd.tile_base = tiles;
         nd.cta_base = ctas;
         nd.prob_base = probs;

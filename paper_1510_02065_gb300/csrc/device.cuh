@@ -107,6 +107,37 @@ __device__ __forceinline__ void bulk_wait_read_all()
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+// Tiled 5-D tensor copy global -> shared through tensor map `map` (generic
+// address of a map in parameter, constant or global space), box origin
+// c0..c4 (c0 x 4 bytes a multiple of 16), completing its bytes on bar.
+__device__ __forceinline__ void tensor_load5(void *dst_smem, const void *map, int c0, int c1, int c2,
+                                             int c3, int c4, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst_smem)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Tiled 5-D tensor copy shared -> global (bulk-group completion); elements
+// outside the tensor are not written.
+__device__ __forceinline__ void tensor_store5(const void *map, int c0, int c1, int c2, int c3, int c4,
+                                              const void *src_smem)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(
+            map),
+        "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(src_smem))
+        : "memory");
+}
+
+// Order this thread's later tensor copies after the (host-written) map in global memory.
+__device__ __forceinline__ void tensormap_acquire(const void *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 // 4-byte asynchronous copy global -> shared (cp.async), and its completion.
 __device__ __forceinline__ void cp_async4(void *dst_smem, const void *src_gmem)
 {

@@ -6,6 +6,7 @@
 // group of one; a batch of branch-and-bound nodes of different residual sizes
 // is a larger group advanced by the same launches.
 #pragma once
+#include <cuda.h>  // CUtensorMap (type only; maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -55,6 +56,14 @@ struct PassState {
 
 // One instance as the kernels see it.
 struct NodeDesc {
+    // The tile store as a 5-D tensor of ints: (column q, row, n', k', i*N + j),
+    // box (4, 1, m|1, 1, N): the location-chunk pieces of one facility row
+    // across all tiles of a fixed facility pair, as the fused pass over D
+    // moves them (valid when zmap_ok; m = N - 1, the box overhang m|1 > m only
+    // pads the shared-memory pitch and is out of bounds, zero-filled on load
+    // and skipped on store).
+    CUtensorMap zmap;
+    int zmap_ok;
     PassState p;
     int N, W, TS;
     int nchunks;          // location chunks of the fused pass over D
@@ -98,6 +107,9 @@ struct Group {
 };
 
 int p1_chunk(int N);                   // locations per CTA of the fused pass over D
+// Encode nd.zmap for the fused pass with location chunk JC (sets zmap_ok;
+// false leaves the pieces to per-piece copies).  nd.p.z and the geometry must be set.
+bool encode_zmap(NodeDesc &nd, int JC);
 size_t p1_smem_bytes(int N, int JC);   // its dynamic shared memory
 
 // Initialise instance `node` of the group (index b) from device copies of its

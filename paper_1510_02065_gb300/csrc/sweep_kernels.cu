@@ -24,6 +24,8 @@
 // and writes rows and pieces back with 16-byte stores; two CTAs per SM overlap
 // one's copies with the other's arithmetic.  With i < k < p the lexicographic
 // ranks of kinds 1..6 are 0..5.
+#include <cstring>
+
 #include "device.cuh"
 #include "kernels.h"
 
@@ -50,7 +52,9 @@ __device__ __forceinline__ int share(int x, const FastDiv &fm, int t)
 // and 5 likewise, read by column, with pitch S25 = 4 x odd (W, or W + 4 when
 // W / 4 is even): a column read across 32 rows then meets 8 distinct banks,
 // the fewest 16-byte-aligned rows allow.  The JC-location pieces of kinds 4
-// and 6 are indexed (a, l) with an odd number of pieces per a.
+// and 6 are indexed (a, l') with l' = l - (l > a) the rank of l among the
+// locations != a, and m|1 (odd) pieces per a: the layout of the tensor box of
+// zmap, and a conflict-free 16-byte read of pieces (qq, nn) across lanes qq.
 struct P1Layout {
     int S13, S25, P46, H6p;
     int A1, A3, A2, A5, A4, A6, H1, H3, H2, H5, H4, H6, total;
@@ -63,14 +67,15 @@ __host__ __device__ inline P1Layout p1_layout(int N, int W, int JC)
     P1Layout L;
     L.S13 = W;
     L.S25 = (W / 4) % 2 ? W : W + 4;
-    L.P46 = JC * (N | 1);
+    L.P46 = JC * ((N - 1) | 1);
     L.H6p = N | 1;
     int o = 0;
     L.A1 = o; o += JC * N * L.S13;
     L.A3 = o; o += JC * N * L.S13;
     L.A2 = o; o += JC * N * L.S25;
     L.A5 = o; o += JC * N * L.S25;
-    L.A4 = o; o += up4(N * L.P46);
+    o = (o + 31) & ~31;  // tensor-copy destinations on 128-byte boundaries
+    L.A4 = o; o += (N * L.P46 + 31) & ~31;
     L.A6 = o; o += up4(N * L.P46);
     L.H1 = o; o += up4(JC * N);
     L.H3 = o; o += up4(JC * N);
@@ -83,6 +88,47 @@ __host__ __device__ inline P1Layout p1_layout(int N, int W, int JC)
 }
 
 size_t p1_smem_bytes(int N, int JC) { return (size_t)p1_layout(N, up4(N), JC).total * 4; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+bool encode_zmap(NodeDesc &nd, int JC)
+{
+    nd.zmap_ok = 0;
+    std::memset(&nd.zmap, 0, sizeof(nd.zmap));
+    if (JC != 4 || !nd.p.z) return false;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t N = (cuuint64_t)nd.N, m = N - 1, W = (cuuint64_t)nd.W, n = N - 2;
+    const cuuint64_t dim[5] = {W, n, m, m, N * N};
+    const cuuint64_t stride[4] = {W * 4, W * n * 4, W * n * m * 4, W * n * m * m * 4};
+    const cuuint32_t box[5] = {4, 1, (cuuint32_t)(m | 1), 1, (cuuint32_t)N};
+    const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
+    if (fn(&nd.zmap, CU_TENSOR_MAP_DATA_TYPE_INT32, 5, nd.p.z, dim, stride, box, estride,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    nd.zmap_ok = 1;
+    return true;
+}
 
 int p1_chunk(int N)
 {
@@ -150,7 +196,7 @@ __device__ __forceinline__ void store_piece(int *dst, const int (&r)[JC])
 // holds c' (C plus the spread of B) per tile.  ONE (a group of one instance):
 // the instance is the kernel parameter g.first.
 template <int JC, bool ONE>
-__global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
+__global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant__ Group g)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) *g.counter = 0;  // work counter of the D -> C sweep
     const NodeDesc &nd =
@@ -174,17 +220,28 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
     int *__restrict__ z = p.z;
     const int NN = N * N;
 
-    // ---- loads, all in flight at once: every full row by one bulk copy
-    // completing on bar, then the JC-location pieces of kinds 4 and 6 (one
-    // aligned cp.async each)
+    // ---- loads, all in flight at once, completing on bar: every full row by
+    // one bulk copy; the JC-location pieces of kinds 4 and 6 by one tensor
+    // copy per kind (rows i of tiles (k,a,p,l), resp. (p,a,k,l), all a and l)
+    // where the map exists (JC = 4), else one aligned cp.async per piece
     __shared__ __align__(8) uint64_t bar;
+    const bool tma = JC == 4 && nd.zmap_ok;
+    const void *zmap = &nd.zmap;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
+        if (!ONE && tma) tensormap_acquire(zmap);
     }
     __syncthreads();
     const unsigned rowBytes = (unsigned)W * 4u;
-    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, (unsigned)(4 * jc * (N - 1)) * rowBytes);
+    if (threadIdx.x == 0) {
+        const unsigned pieceBytes = tma ? 2u * (unsigned)(N * L.P46) * 4u : 0u;
+        mbar_arrive_expect_tx(&bar, (unsigned)(4 * jc * (N - 1)) * rowBytes + pieceBytes);
+        if (tma) {
+            tensor_load5(sm + L.A4, zmap, j0, i, 0, pp - 1, k * N, &bar);  // kind 4: tile (k,a,p,l), row i
+            tensor_load5(sm + L.A6, zmap, j0, i, 0, k, pp * N, &bar);      // kind 6: tile (p,a,k,l), row i
+        }
+    }
     for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
         const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
         const int q = qj / JC, jj = qj % JC, j = j0 + jj;
@@ -195,13 +252,13 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
         const int pitch = q < 2 ? L.S13 : L.S25;
         bulk_load_tx(sm + base + (jj * N + x) * pitch, z + t * TS + (size_t)row * W, rowBytes, &bar);
     }
-    for (int e = threadIdx.x; e < 2 * NN; e += kP1Threads) {
+    for (int e = tma ? 2 * NN : threadIdx.x; e < 2 * NN; e += kP1Threads) {
         const int kind = e >= NN, r2 = e - kind * NN;
         const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
         if (l == a) continue;
         // kind 4: row i of tile (k,a,p,l); kind 6: row i of tile (p,a,k,l)
         const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
-        cp_async_piece<JC>(sm + (kind ? L.A6 : L.A4) + a * L.P46 + l * JC,
+        cp_async_piece<JC>(sm + (kind ? L.A6 : L.A4) + a * L.P46 + (l - (l > a)) * JC,
                            z + t * TS + (size_t)i * W + j0);
     }
 
@@ -240,8 +297,8 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
         const int *h4 = sm + L.H4 + nn * N, *h6 = sm + L.H6 + nn;
         for (int qq = lane; qq < N; qq += 32) {
             if (qq == nn) continue;
-            int *a4 = sm + L.A4 + nn * L.P46 + qq * JC;   // piece (nn, qq)
-            int *a6 = sm + L.A6 + qq * L.P46 + nn * JC;   // piece (qq, nn)
+            int *a4 = sm + L.A4 + nn * L.P46 + (qq - (qq > nn)) * JC;   // piece (nn, qq)
+            int *a6 = sm + L.A6 + qq * L.P46 + (nn - (nn > qq)) * JC;   // piece (qq, nn)
             int p4[JC], p6[JC];
             load_piece<JC>(p4, a4);
             load_piece<JC>(p6, a6);
@@ -282,13 +339,18 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(Group g)
         const int pitch = q < 2 ? L.S13 : L.S25;
         bulk_store(z + t * TS + (size_t)row * W, sm + base + (jj * N + x) * pitch, rowBytes);
     }
+    if (tma && threadIdx.x == 0) {
+        tensor_store5(zmap, j0, i, 0, pp - 1, k * N, sm + L.A4);
+        tensor_store5(zmap, j0, i, 0, k, pp * N, sm + L.A6);
+    }
     bulk_commit();
-    for (int e = threadIdx.x; e < 2 * NN; e += kP1Threads) {
+    for (int e = tma ? 2 * NN : threadIdx.x; e < 2 * NN; e += kP1Threads) {
         const int kind = e >= NN, r2 = e - kind * NN;
         const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
         if (l == a) continue;
         const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
-        copy_piece<JC>(z + t * TS + (size_t)i * W + j0, sm + (kind ? L.A6 : L.A4) + a * L.P46 + l * JC);
+        copy_piece<JC>(z + t * TS + (size_t)i * W + j0,
+                       sm + (kind ? L.A6 : L.A4) + a * L.P46 + (l - (l > a)) * JC);
     }
     bulk_wait_read_all();  // shared memory stays valid until the bulk stores have read it
 }

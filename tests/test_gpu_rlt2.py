@@ -10,7 +10,8 @@
   the C -> B and B -> LB kernels;
 * the stopping rule of Algorithm 1;
 * the 30-facility headline workload in the launch configuration the benchmark
-  times: the first pass against the oracle, later passes through properties
+  times, and a 34-facility instance (two column slots per lane, two-location
+  chunks): the first pass against the oracle, later passes through properties
   that hold at any size (conservation on sampled permutations, non-negative
   reduced costs, monotone LB).
 """
@@ -22,7 +23,7 @@ import pytest
 
 from paper_1510_02065_gb300 import instances as I
 from paper_1510_02065_gb300 import rlt2
-from tests.layout import compact_y, compact_z, state_hash
+from tests.layout import compact_y, compact_z, state_hash, tile_indices
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
@@ -196,22 +197,22 @@ def _conservation_sample(F, D, N, LB, x, y, z, perms):
     return worst
 
 
-@pytest.mark.slow
-def test_headline_n30(gpu, orc):
-    F, D, _ = I.instance("clustered_n30")
-    N = 30
-    rng = np.random.default_rng(30)
+def _first_pass_then_properties(orc, F, D, N, seed):
+    """First pass against the oracle (LB, all of B and C, 200,000 sampled D
+    entries), then three passes checked through properties that hold at any
+    size: non-negative reduced costs, monotone LB, conservation on 100
+    sampled permutations."""
+    rng = np.random.default_rng(seed)
     perms = [rng.permutation(N) for _ in range(100)]
     st = orc.State(F, D)
     with rlt2.Context(F, D) as ctx:
         ctx.iterate(1)
         st.iterate()
-        # first pass against the oracle: LB, all of B and C, 10^6 sampled D entries
         assert ctx.bound()[1] == st.LB
         assert (ctx.state(0) == st.b.reshape(-1)).all()
         assert (ctx.state(1) == compact_y(st.c)).all()
         z = ctx.state(2)
-        i, j, k, n = [a.astype(np.int64) for a in __import__("tests.layout", fromlist=["x"]).tile_indices(N)]
+        i, j, k, n = [a.astype(np.int64) for a in tile_indices(N)]
         sel = rng.integers(0, len(i), size=200000)
         rr = rng.integers(0, N - 2, size=sel.size)
         ss = rng.integers(0, N - 2, size=sel.size)
@@ -225,7 +226,61 @@ def test_headline_n30(gpu, orc):
         got = z[(sel * (N - 2) + rr) * (N - 2) + ss]
         assert (got == ref).all()
         st.close()
-        # later passes: properties that hold at any size
+        hist = [ctx.bound()[1]]
+        for t in range(3):
+            ctx.iterate(1)
+            hist.append(ctx.bound()[1])
+        x, y, z = ctx.state(0), ctx.state(1), ctx.state(2)
+        assert x.min() >= 0 and y.min() >= 0 and z.min() >= 0
+        assert all(a <= b for a, b in zip(hist, hist[1:]))
+        assert _conservation_sample(F, D, N, hist[-1], x, y, z, perms) == 0
+
+
+@pytest.mark.slow
+def test_headline_n30(gpu, orc):
+    """The 30-facility workload in the launch configuration the benchmark times."""
+    F, D, _ = I.instance("clustered_n30")
+    _first_pass_then_properties(orc, F, D, 30, 30)
+
+
+@pytest.mark.slow
+def test_two_slot_lanes_n34(gpu, orc):
+    """N = 34: LAPs of size 32 and 33 take two column slots per lane, and the
+    fused pass over D works on chunks of two locations with per-piece copies.
+    The oracle takes the spreading and complementary operations in full and the
+    D -> C concentration on three facility slices (tiles D_ijkn with i in the
+    slice); 10^6 sampled entries of those tiles after the first pass must agree,
+    then three more passes are checked through properties."""
+    N = 34
+    F, D = I.clustered_euclid(N, seed=N)
+    rng = np.random.default_rng(N)
+    perms = [rng.permutation(N) for _ in range(100)]
+    st = orc.State(F, D)
+    st.spread_B_to_C()
+    st.spread_C_to_D()
+    st.complementary_D()
+    slices = (0, N // 2, N - 1)
+    for a in slices:
+        st.concentrate_D_to_C_range(a, a + 1)
+    with rlt2.Context(F, D) as ctx:
+        ctx.iterate(1)
+        z = ctx.state(2)
+        i, j, k, n = [a.astype(np.int64) for a in tile_indices(N)]
+        per = N * (N - 1) ** 2
+        for a in slices:
+            sel = a * per + rng.integers(0, per, size=1000000)
+            rr = rng.integers(0, N - 2, size=sel.size)
+            ss = rng.integers(0, N - 2, size=sel.size)
+            lo, hi = np.minimum(i[sel], k[sel]), np.maximum(i[sel], k[sel])
+            p = rr + (rr >= lo)
+            p = p + (p >= hi)
+            lo, hi = np.minimum(j[sel], n[sel]), np.maximum(j[sel], n[sel])
+            q = ss + (ss >= lo)
+            q = q + (q >= hi)
+            ref = st.d[i[sel], j[sel], k[sel], n[sel], p, q]
+            got = z[(sel * (N - 2) + rr) * (N - 2) + ss]
+            assert (got == ref).all(), "D differs in slice i = %d" % a
+        st.close()
         hist = [ctx.bound()[1]]
         for t in range(3):
             ctx.iterate(1)
