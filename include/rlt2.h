@@ -54,6 +54,7 @@ extern "C" {
 #define RLT2_E_TIMEOUT    -5   /* a bounded device-side wait gave up                          */
 #define RLT2_E_STATE      -6   /* call out of order (e.g. history capacity exhausted)         */
 #define RLT2_E_INTERNAL   -7   /* a kernel's internal consistency check failed (a bug)        */
+#define RLT2_E_IO         -8   /* checkpoint file not writable / readable, or not a checkpoint */
 
 #define RLT2_MIN_N         3
 #define RLT2_MAX_N        64   /* the LAP kernels hold at most 64 columns per warp */
@@ -162,6 +163,27 @@ int rlt2_reset_stage_times(rlt2_ctx *ctx);
  * error. */
 void *rlt2_device_state(rlt2_ctx *ctx, int which);
 int rlt2_row_stride(int N);
+
+/*
+ * Checkpoint and resume of a dual ascent (no counterpart in the paper, whose
+ * runs are not interrupted; it serves long branch-and-bound runs).
+ *
+ * rlt2_save waits for the context's stream and writes its whole state to the
+ * file `path` (created or truncated): LB, passes done, the stopping flag, the
+ * LB history, B, C and the tile store of D as laid out on the device (about
+ * the device memory of the context: 2.7 GB at N = 30).  Errors:
+ * RLT2_E_INVAL, RLT2_E_IO (cannot write), RLT2_E_TIMEOUT / RLT2_E_INTERNAL
+ * (a pending device error; nothing written), RLT2_E_CUDA.
+ *
+ * rlt2_load creates a new context from such a file; opts as for rlt2_create
+ * (ub, min_progress, stream, graph and profile settings are taken from opts;
+ * rlt1_only and the instance come from the file; opts->max_iters must be at
+ * least the passes already done).  Passes after the load continue exactly as
+ * the saved context would have.  Errors: RLT2_E_INVAL, RLT2_E_IO (unreadable,
+ * truncated or not a checkpoint), RLT2_E_OOM, RLT2_E_CUDA.
+ */
+int rlt2_save(rlt2_ctx *ctx, const char *path);
+int rlt2_load(const char *path, const rlt2_opts *opts, rlt2_ctx **out);
 
 /* Bytes of device memory rlt2_create allocates for an instance of size N
  * (0 for N out of range); max_iters <= 0 means the default. */

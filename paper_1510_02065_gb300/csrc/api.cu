@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -190,6 +191,7 @@ struct rlt2_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int enqueued = 0;
+    long long U = 0;       // the int32 guard's bound of the instance (kept for checkpoints)
     // profiling: 5 events per pass, recorded on the stream between the stages
     std::vector<cudaEvent_t> events;
     size_t ev_used = 0;
@@ -228,6 +230,7 @@ const char *rlt2_strerror(int code)
     case RLT2_E_TIMEOUT: return "a bounded device-side wait gave up";
     case RLT2_E_STATE: return "call out of order or capacity exhausted";
     case RLT2_E_INTERNAL: return "an internal consistency check of a kernel failed";
+    case RLT2_E_IO: return "checkpoint file could not be written or read, or is not a checkpoint";
     default: return "unknown error";
     }
 }
@@ -236,37 +239,24 @@ int rlt2_row_stride(int N) { return (N + 3) & ~3; }
 
 void rlt2_destroy(rlt2_ctx *c) { free_ctx(c); }
 
-int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin, int64_t lb_const,
-                const rlt2_opts *opts, rlt2_ctx **out)
-{
-    if (!out) return RLT2_E_INVAL;
-    *out = nullptr;
-    long long U = 0;
-    int rc = check_instance(F, D, N, B_lin, &U);
-    if (rc != RLT2_OK) return rc;
+}  // extern "C"
 
-    rlt2_ctx *c = new (std::nothrow) rlt2_ctx();
-    if (!c) return RLT2_E_OOM;
-    if (opts) c->opts = *opts;
-    else rlt2_default_opts(&c->opts);
-    if (c->opts.max_iters <= 0) c->opts.max_iters = 65536;
-    auto fail = [&](int code) {
-        free_ctx(c);
-        return code;
-    };
+// Allocate and describe the device state of a context of size N (no
+// initialisation of the costs): stream, one arena, the instance descriptor,
+// the group of one, the triple table, zeroed status and work counter.
+// *stage receives 3 N^2 ints of device staging memory.
+static int setup_ctx(rlt2_ctx *c, int N, bool with_d, long long U, int32_t **stage)
+{
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return fail(RLT2_E_CUDA);
+    if (cudaGetDevice(&dev) != cudaSuccess) return RLT2_E_CUDA;
     if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return fail(RLT2_E_CUDA);
+        return RLT2_E_CUDA;
     if (c->opts.stream) {
         c->stream = (cudaStream_t)c->opts.stream;
     } else {
-        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
-            return fail(RLT2_E_CUDA);
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return RLT2_E_CUDA;
         c->own_stream = true;
     }
-
-    const bool with_d = !c->opts.rlt1_only;
     const int JC = p1_chunk(N);
     const std::vector<int4> tri = triple_table(N);
     Arena a;
@@ -280,7 +270,7 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
     if (e != cudaSuccess) {
         cudaGetLastError();
         c->mem = nullptr;
-        return fail(cuda_code(e));
+        return cuda_code(e);
     }
     char *base = c->mem;
     NodeDesc &nd = c->node;
@@ -306,6 +296,7 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
     g.triples = reinterpret_cast<const int4 *>(base + o_tri);
     g.first = nd;
+    c->U = U;
 
     e = cudaMemcpyAsync(base + o_node, &nd, sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
@@ -313,10 +304,164 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
                             c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.status, 0, sizeof(DevStatus), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.counter, 0, 4, c->stream);
-    if (e == cudaSuccess)
-        e = init_node(nd, F, D, B_lin, lb_const, reinterpret_cast<int32_t *>(base + o_stage), c->stream);
+    // the table must outlive its asynchronous copy
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return fail(cuda_code(e));
+    if (e != cudaSuccess) return cuda_code(e);
+    *stage = reinterpret_cast<int32_t *>(base + o_stage);
+    return RLT2_OK;
+}
+
+static rlt2_ctx *new_ctx(const rlt2_opts *opts)
+{
+    rlt2_ctx *c = new (std::nothrow) rlt2_ctx();
+    if (!c) return nullptr;
+    if (opts) c->opts = *opts;
+    else rlt2_default_opts(&c->opts);
+    if (c->opts.max_iters <= 0) c->opts.max_iters = 65536;
+    return c;
+}
+
+// Checkpoint file: this header, then the LB history (iter int64), B (N^2
+// int32), C after its last concentration (tiles int32) and, with D, the tile
+// store as laid out on the device (tiles x (N-2) x round_up(N,4) int32).
+struct CkptHeader {
+    char magic[8];
+    int32_t version, N, with_d, iter, stop, pad;
+    int64_t LB, U, tiles, z_ints;
+};
+static const char kCkptMagic[8] = {'R', 'L', 'T', '2', 'C', 'K', 'P', 'T'};
+
+// Move `bytes` between a FILE and device memory through a bounded host buffer.
+static int file_device(FILE *f, char *dev, size_t bytes, bool to_file, cudaStream_t s)
+{
+    const size_t chunk = (size_t)64 << 20;
+    std::vector<char> buf(std::min(bytes, chunk));
+    for (size_t off = 0; off < bytes; off += chunk) {
+        const size_t n = std::min(chunk, bytes - off);
+        if (to_file) {
+            if (cudaMemcpyAsync(buf.data(), dev + off, n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return RLT2_E_CUDA;
+            if (std::fwrite(buf.data(), 1, n, f) != n) return RLT2_E_IO;
+        } else {
+            if (std::fread(buf.data(), 1, n, f) != n) return RLT2_E_IO;
+            if (cudaMemcpyAsync(dev + off, buf.data(), n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return RLT2_E_CUDA;
+        }
+    }
+    return RLT2_OK;
+}
+
+extern "C" {
+
+int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin, int64_t lb_const,
+                const rlt2_opts *opts, rlt2_ctx **out)
+{
+    if (!out) return RLT2_E_INVAL;
+    *out = nullptr;
+    long long U = 0;
+    int rc = check_instance(F, D, N, B_lin, &U);
+    if (rc != RLT2_OK) return rc;
+    rlt2_ctx *c = new_ctx(opts);
+    if (!c) return RLT2_E_OOM;
+    int32_t *stage = nullptr;
+    rc = setup_ctx(c, N, !c->opts.rlt1_only, U, &stage);
+    if (rc != RLT2_OK) {
+        free_ctx(c);
+        return rc;
+    }
+    cudaError_t e = init_node(c->node, F, D, B_lin, lb_const, stage, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return cuda_code(e);
+    }
+    *out = c;
+    return RLT2_OK;
+}
+
+int rlt2_save(rlt2_ctx *c, const char *path)
+{
+    if (!c || !path) return RLT2_E_INVAL;
+    int64_t lb = 0;
+    int it = 0;
+    int rc = rlt2_bound(c, nullptr, &lb, &it);  // synchronises; reports device errors
+    if (rc != RLT2_OK) return rc;
+    const NodeDesc &nd = c->node;
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.N = nd.N;
+    h.with_d = nd.p.z != nullptr;
+    h.iter = it;
+    CK(cudaMemcpy(&h.stop, nd.p.stop, 4, cudaMemcpyDeviceToHost));
+    h.LB = lb;
+    h.U = c->U;
+    h.tiles = nd.tiles;
+    h.z_ints = h.with_d ? nd.tiles * nd.TS : 0;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return RLT2_E_IO;
+    const int nh = std::min(it, c->opts.max_iters);
+    rc = std::fwrite(&h, sizeof(h), 1, f) == 1 ? RLT2_OK : RLT2_E_IO;
+    if (rc == RLT2_OK) rc = file_device(f, (char *)nd.p.hist, (size_t)nh * 8, true, c->stream);
+    if (rc == RLT2_OK) rc = file_device(f, (char *)nd.p.x, (size_t)nd.N * nd.N * 4, true, c->stream);
+    if (rc == RLT2_OK) rc = file_device(f, (char *)nd.p.yC, (size_t)nd.tiles * 4, true, c->stream);
+    if (rc == RLT2_OK && h.with_d) rc = file_device(f, (char *)nd.p.z, (size_t)h.z_ints * 4, true, c->stream);
+    if (std::fclose(f) != 0 && rc == RLT2_OK) rc = RLT2_E_IO;
+    return rc;
+}
+
+int rlt2_load(const char *path, const rlt2_opts *opts, rlt2_ctx **out)
+{
+    if (!path || !out) return RLT2_E_INVAL;
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return RLT2_E_IO;
+    CkptHeader h{};
+    int rc = RLT2_OK;
+    rlt2_ctx *c = nullptr;
+    do {
+        if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1 ||
+            h.N < RLT2_MIN_N || h.N > RLT2_MAX_N || h.iter < 0 || h.U < 0 || h.U > RLT2_LAP_MAX_ENTRY ||
+            h.tiles != make_geom(h.N).tiles ||
+            h.z_ints != (h.with_d ? h.tiles * (long long)make_geom(h.N).TS : 0)) {
+            rc = RLT2_E_IO;
+            break;
+        }
+        c = new_ctx(opts);
+        if (!c) {
+            rc = RLT2_E_OOM;
+            break;
+        }
+        c->opts.rlt1_only = !h.with_d;
+        if (h.iter > c->opts.max_iters) {  // the history must fit
+            rc = RLT2_E_INVAL;
+            break;
+        }
+        int32_t *stage = nullptr;
+        if ((rc = setup_ctx(c, h.N, h.with_d != 0, h.U, &stage)) != RLT2_OK) break;
+        const NodeDesc &nd = c->node;
+        if ((rc = file_device(f, (char *)nd.p.hist, (size_t)h.iter * 8, false, c->stream)) != RLT2_OK) break;
+        if ((rc = file_device(f, (char *)nd.p.x, (size_t)h.N * h.N * 4, false, c->stream)) != RLT2_OK) break;
+        if ((rc = file_device(f, (char *)nd.p.yC, (size_t)h.tiles * 4, false, c->stream)) != RLT2_OK) break;
+        if (h.with_d && (rc = file_device(f, (char *)nd.p.z, (size_t)h.z_ints * 4, false, c->stream)) != RLT2_OK)
+            break;
+        cudaError_t e = cudaMemcpyAsync(nd.p.LB, &h.LB, 8, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(nd.p.iter, &h.iter, 4, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(nd.p.stop, &h.stop, 4, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_code(e);
+            break;
+        }
+        c->enqueued = h.iter;
+    } while (false);
+    std::fclose(f);
+    if (rc != RLT2_OK) {
+        free_ctx(c);
+        return rc;
+    }
     *out = c;
     return RLT2_OK;
 }

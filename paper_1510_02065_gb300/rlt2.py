@@ -27,6 +27,7 @@ RLT2_E_CUDA = -4
 RLT2_E_TIMEOUT = -5
 RLT2_E_STATE = -6
 RLT2_E_INTERNAL = -7
+RLT2_E_IO = -8
 RLT2_MIN_N = 3
 RLT2_MAX_N = 64
 RLT2_LAP_MAX_ENTRY = 536870911
@@ -83,6 +84,8 @@ def lib():
         "rlt2_lap_batch": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "rlt2_lap_batch_static": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "rlt2_state_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+        "rlt2_save": (C.c_int, [_vp, C.c_char_p]),
+        "rlt2_load": (C.c_int, [C.c_char_p, C.POINTER(rlt2_opts), C.POINTER(_vp)]),
         "rlt2_group_create": (C.c_int, [C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)]),
         "rlt2_group_iterate": (C.c_int, [_vp, C.c_int]),
         "rlt2_group_sync": (C.c_int, [_vp]),
@@ -150,6 +153,17 @@ def rlt2_create(F, D, N=None, B_lin=None, lb_const=0, opts=None):
 
 def rlt2_destroy(ctx):
     lib().rlt2_destroy(_vp(ctx))
+
+
+def rlt2_save(ctx, path):
+    _chk(lib().rlt2_save(_vp(ctx), os.fsencode(path)), "rlt2_save")
+
+
+def rlt2_load(path, opts=None):
+    out = _vp()
+    _chk(lib().rlt2_load(os.fsencode(path), C.byref(opts) if opts is not None else None, C.byref(out)),
+         "rlt2_load")
+    return out.value
 
 
 def rlt2_iterate(ctx, k: int):
@@ -289,6 +303,13 @@ class Context:
 
     def __init__(self, F, D, B_lin=None, lb_const=0, rlt1_only=False, use_graph=True,
                  profile=False, max_iters=65536, ub=0.0, min_progress=0.0, stream=0):
+        o = self._opts(rlt1_only, use_graph, profile, max_iters, ub, min_progress, stream)
+        self.N = int(np.asarray(F).shape[0])
+        self.ctx = rlt2_create(F, D, self.N, B_lin, lb_const, o)
+
+    @staticmethod
+    def _opts(rlt1_only=False, use_graph=True, profile=False, max_iters=65536, ub=0.0,
+              min_progress=0.0, stream=0):
         o = rlt2_default_opts()
         o.rlt1_only = int(rlt1_only)
         o.use_graph = int(use_graph)
@@ -297,8 +318,19 @@ class Context:
         o.ub = float(ub)
         o.min_progress = float(min_progress)
         o.stream = stream or None
-        self.N = int(np.asarray(F).shape[0])
-        self.ctx = rlt2_create(F, D, self.N, B_lin, lb_const, o)
+        return o
+
+    @classmethod
+    def load(cls, path, **kw):
+        """A context resumed from a checkpoint written by save()."""
+        self = cls.__new__(cls)
+        self.ctx = rlt2_load(path, cls._opts(**kw))
+        with open(path, "rb") as f:   # N: the int32 after the magic and the version
+            self.N = int(np.frombuffer(f.read(16), np.int32)[3])
+        return self
+
+    def save(self, path):
+        rlt2_save(self.ctx, path)
 
     def iterate(self, k=1):
         rlt2_iterate(self.ctx, k)
