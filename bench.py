@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--batch-iters", type=int, default=100)
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving measurement (0: skip)")
+    ap.add_argument("--store", default="tiles", choices=["tiles", "classes"],
+                    help="store of D for the headline run (results are identical)")
     ap.add_argument("--n35-steps", type=int, default=30,
                     help="timed passes of the 35-facility root bound (0: skip)")
     return ap.parse_args()
@@ -87,11 +89,12 @@ def serve_measure(instances, torch, count, passes=50, rate=50.0):
     return out
 
 
-def n35_measure(rlt2, instances, torch, steps, warmup=3):
-    """Root bound of the 35-facility clustered instance (dense D store)."""
+def n35_measure(rlt2, instances, torch, steps, store, warmup=3):
+    """Root bound of the 35-facility clustered instance."""
     F, D, _ = instances.instance("clustered_n35")
     s = torch.cuda.Stream()
-    with rlt2.Context(F, D, profile=True, max_iters=steps + warmup + 1, stream=s.cuda_stream) as c:
+    with rlt2.Context(F, D, profile=True, max_iters=steps + warmup + 1, stream=s.cuda_stream,
+                      store=store) as c:
         c.iterate(warmup)
         torch.cuda.synchronize()
         rlt2.rlt2_reset_stage_times(c.ctx)
@@ -109,7 +112,9 @@ def n35_measure(rlt2, instances, torch, steps, warmup=3):
             "stages_ms": {"spread_complementary_D": ms[0] / n, "concentrate_D_to_C": ms[1] / n,
                           "complementary_C_concentrate_C_to_B": ms[2] / n,
                           "concentrate_B_to_LB": ms[3] / n},
-            "store": "dense (%.2f GB)" % (rlt2.rlt2_state_bytes(35) / 1e9)}
+            "store": "%s (%.2f GB on the device)" % (
+                "class sums" if store == rlt2.RLT2_STORE_CLASSES else "tiles",
+                rlt2.rlt2_state_bytes(35, store=store) / 1e9)}
 
 
 def batch_measure(rlt2, instances, torch, nodes_count, iters):
@@ -319,8 +324,9 @@ def main():
     peaks, peaks_kind = load_peaks()
     props = torch.cuda.get_device_properties(local)
 
+    store = rlt2.RLT2_STORE_CLASSES if args.store == "classes" else rlt2.RLT2_STORE_TILES
     ctx = rlt2.Context(F, D, profile=True, use_graph=True, max_iters=K + W + 16,
-                       stream=stream.cuda_stream)
+                       stream=stream.cuda_stream, store=store)
     ctx.iterate(W)
     torch.cuda.synchronize()
     rlt2.rlt2_reset_stage_times(ctx.ctx)
@@ -371,7 +377,7 @@ def main():
     p1_bytes = 2 * z_bytes + n_tiles * 4 + N * N * 4
     p1_gbs = p1_bytes / (t_p1 / 1e3) / 1e9
     traffic = None
-    if args.workload == DLAP_TRAFFIC["workload"]:
+    if args.workload == DLAP_TRAFFIC["workload"] and args.store == "tiles":
         import hashlib
         h = hashlib.sha1()
         for f in ("lap_kernels.cu", "device.cuh", "kernels.h"):
@@ -384,7 +390,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "N": N, "seed": 0, "tiles": n_tiles,
+        "config": {"workload": args.workload, "N": N, "seed": 0, "tiles": n_tiles, "store": args.store,
                    "laps_per_iter": int(round(laps_per_pass)), "z_bytes": z_bytes,
                    "l2": "inputs larger than L2 (D store %.2f GB)" % (z_bytes / 1e9),
                    "parallelism": "replicas x%d" % world if world > 1 else "1 GPU"},
@@ -417,7 +423,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c2 = rlt2.Context(Fp, Dp, max_iters=K + 4, stream=stream.cuda_stream)
+        c2 = rlt2.Context(Fp, Dp, max_iters=K + 4, stream=stream.cuda_stream, store=store)
         for _ in range(K):
             c2.iterate(1)
             c2.bound()
@@ -435,7 +441,8 @@ def main():
     if args.batch_nodes > 0:
         line["batch"] = batch_measure(rlt2, instances, torch, args.batch_nodes, args.batch_iters)
     if args.n35_steps > 0:
-        line["n35"] = n35_measure(rlt2, instances, torch, args.n35_steps)
+        line["n35"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_CLASSES)
+        line["n35_tiles"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_TILES)
     if args.serve_requests > 0:
         line["serve"] = serve_measure(instances, torch, args.serve_requests)
 

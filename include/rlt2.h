@@ -73,7 +73,22 @@ typedef struct {
     double min_progress;  /* K of Algorithm 1: stop once LB'/UB < K; 0: never     */
     void *stream;         /* cudaStream_t to run on; NULL = a non-blocking stream
                              created for (and owned by) the context              */
+    int store;            /* how D is kept: RLT2_STORE_TILES (default) or
+                             RLT2_STORE_CLASSES; results are identical          */
 } rlt2_opts;
+
+/*
+ * Stores of D.  RLT2_STORE_TILES keeps every reduced cost d_ijknpq in the tile
+ * layout of rlt2_device_state (about 4 B N^2 (N-1)^2 (N-2)^2; 2.7 GB at N =
+ * 30, 6.7 GB at N = 35).  RLT2_STORE_CLASSES keeps one int per class
+ * {(i,j),(k,n),(p,q)} -- the class sum T after the transfer between
+ * complementary costs, whose six members are floor(T/6) + [rank < T mod 6]
+ * (Eq. (11)) -- plus the duals (u, v) of every tile's last LAP, from which
+ * every reduced cost follows as member - u_p - v_q (about 4 B C(N,3) N^3 +
+ * 4 B N^2 (N-1)^2 (2N); 0.6 GB at N = 30, 1.5 GB at N = 35, 52 GB at N = 64).
+ */
+#define RLT2_STORE_TILES   0
+#define RLT2_STORE_CLASSES 1
 
 typedef struct rlt2_ctx rlt2_ctx;
 
@@ -95,8 +110,9 @@ const char *rlt2_strerror(int code);
  * Errors: RLT2_E_INVAL, RLT2_E_OVERFLOW when U = sum_{i!=k} F_ik * max_{j!=n}
  * D_jn + sum_i max_j B_lin[i][j] exceeds RLT2_LAP_MAX_ENTRY (every reduced
  * cost, class sum and Hungarian potential is then bounded by 3U and fits
- * int32), RLT2_E_OOM, RLT2_E_CUDA.  Device memory: about 4 B * N^2 (N-1)^2
- * (N-2)^2 for D plus 12 B * N^2 (N-1)^2.
+ * int32), RLT2_E_OOM, RLT2_E_CUDA; RLT2_E_INVAL also for an unknown
+ * opts->store.  Device memory: D in the chosen store (see RLT2_STORE_*) plus
+ * 12 B * N^2 (N-1)^2; rlt2_state_bytes() gives the exact figure.
  */
 int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
                 int64_t lb_const, const rlt2_opts *opts, rlt2_ctx **out);
@@ -156,11 +172,15 @@ int rlt2_work(rlt2_ctx *ctx, int64_t out[6]);
 int rlt2_stage_times(rlt2_ctx *ctx, double out[4], int *passes);
 int rlt2_reset_stage_times(rlt2_ctx *ctx);
 
-/* Device pointer of the context's state: which 0 = x, 1 = y (C), 2 = z.  On
- * the device, tile t of z holds N-2 rows (facilities p not in {i,k}) of
- * rlt2_row_stride(N) = round_up(N, 4) ints indexed by the location q itself;
- * columns j and n of the tile and q >= N hold no coefficient.  Returns NULL on
- * error. */
+/* Device pointer of the context's state: which 0 = x, 1 = y (C), 2 = z, 3 =
+ * the tile duals of the class-sum store.  In the tile store, tile t of z
+ * holds N-2 rows (facilities p not in {i,k}) of rlt2_row_stride(N) =
+ * round_up(N, 4) ints indexed by the location q itself; columns j and n of
+ * the tile and q >= N hold no coefficient.  In the class-sum store, which 2
+ * is the class sums T[tau(x,y,z) N^3 + lx N^2 + ly N + lz] (facilities x < y
+ * < z at locations lx, ly, lz; tau = C(z,3) + C(y,2) + x) and which 3 the
+ * duals, per tile round_up(N-2, 4) ints of u then round_up(N, 4) of v by
+ * location.  Returns NULL on error or for a part the context does not have. */
 void *rlt2_device_state(rlt2_ctx *ctx, int which);
 int rlt2_row_stride(int N);
 
@@ -186,8 +206,8 @@ int rlt2_save(rlt2_ctx *ctx, const char *path);
 int rlt2_load(const char *path, const rlt2_opts *opts, rlt2_ctx **out);
 
 /* Bytes of device memory rlt2_create allocates for an instance of size N
- * (0 for N out of range); max_iters <= 0 means the default. */
-size_t rlt2_state_bytes(int N, int rlt1_only, int max_iters);
+ * with D in `store` (0 for N out of range); max_iters <= 0 means the default. */
+size_t rlt2_state_bytes(int N, int rlt1_only, int max_iters, int store);
 
 /*
  * Groups: several live contexts advanced together, every stage of every pass

@@ -85,14 +85,19 @@ struct Arena {
 
 // One instance's state inside an arena (byte offsets).
 struct NodeOffsets {
-    size_t z, yS, yC, x, LB, hist, iter, stop;
+    size_t z, T, du, yS, yC, x, LB, hist, iter, stop;
 };
 
-NodeOffsets plan_node(Arena &a, int N, bool with_d, int hist_cap)
+constexpr size_t kNone = (size_t)-1;
+
+// D in the tile store (with_d, !sym) or in the class-sum store (with_d, sym).
+NodeOffsets plan_node(Arena &a, int N, bool with_d, bool sym, int hist_cap)
 {
     const Geom g = make_geom(N);
     NodeOffsets o;
-    o.z = with_d ? a.take((size_t)g.tiles * g.TS * 4) : (size_t)-1;
+    o.z = with_d && !sym ? a.take((size_t)g.tiles * g.TS * 4) : kNone;
+    o.T = with_d && sym ? a.take((size_t)g.classes_ints * 4) : kNone;
+    o.du = with_d && sym ? a.take((size_t)g.tiles * g.DS * 4) : kNone;
     o.yS = a.take((size_t)g.tiles * 4);
     o.yC = a.take((size_t)g.tiles * 4);
     o.x = a.take((size_t)N * N * 4);
@@ -106,7 +111,9 @@ NodeOffsets plan_node(Arena &a, int N, bool with_d, int hist_cap)
 PassState node_state(char *base, const NodeOffsets &o, int hist_cap, const rlt2_opts &opts)
 {
     PassState p{};
-    p.z = o.z == (size_t)-1 ? nullptr : reinterpret_cast<int *>(base + o.z);
+    p.z = o.z == kNone ? nullptr : reinterpret_cast<int *>(base + o.z);
+    p.T = o.T == kNone ? nullptr : reinterpret_cast<int *>(base + o.T);
+    p.du = o.du == kNone ? nullptr : reinterpret_cast<int *>(base + o.du);
     p.yS = reinterpret_cast<int *>(base + o.yS);
     p.yC = reinterpret_cast<int *>(base + o.yC);
     p.x = reinterpret_cast<int *>(base + o.x);
@@ -245,7 +252,7 @@ void rlt2_destroy(rlt2_ctx *c) { free_ctx(c); }
 // initialisation of the costs): stream, one arena, the instance descriptor,
 // the group of one, the triple table, zeroed status and work counter.
 // *stage receives 3 N^2 ints of device staging memory.
-static int setup_ctx(rlt2_ctx *c, int N, bool with_d, long long U, int32_t **stage)
+static int setup_ctx(rlt2_ctx *c, int N, bool with_d, bool sym, long long U, int32_t **stage)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RLT2_E_CUDA;
@@ -260,7 +267,7 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, long long U, int32_t **sta
     const int JC = p1_chunk(N);
     const std::vector<int4> tri = triple_table(N);
     Arena a;
-    const NodeOffsets no = plan_node(a, N, with_d, c->opts.max_iters);
+    const NodeOffsets no = plan_node(a, N, with_d, sym, c->opts.max_iters);
     const size_t o_node = a.take(sizeof(NodeDesc));
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
     const size_t o_cnt = a.take(4);
@@ -292,6 +299,7 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, long long U, int32_t **sta
     g.JC = JC;
     g.pack = 3 * U < (1LL << 25);
     g.rlt1_only = !with_d;
+    g.sym = with_d && sym;
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
     g.triples = reinterpret_cast<const int4 *>(base + o_tri);
@@ -323,10 +331,11 @@ static rlt2_ctx *new_ctx(const rlt2_opts *opts)
 
 // Checkpoint file: this header, then the LB history (iter int64), B (N^2
 // int32), C after its last concentration (tiles int32) and, with D, the tile
-// store as laid out on the device (tiles x (N-2) x round_up(N,4) int32).
+// store as laid out on the device (tiles x (N-2) x round_up(N,4) int32) or
+// the class sums (C(N,3) N^3 int32) and the tile duals (tiles x DS int32).
 struct CkptHeader {
     char magic[8];
-    int32_t version, N, with_d, iter, stop, pad;
+    int32_t version, N, with_d, iter, stop, sym;
     int64_t LB, U, tiles, z_ints;
 };
 static const char kCkptMagic[8] = {'R', 'L', 'T', '2', 'C', 'K', 'P', 'T'};
@@ -366,7 +375,11 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
     rlt2_ctx *c = new_ctx(opts);
     if (!c) return RLT2_E_OOM;
     int32_t *stage = nullptr;
-    rc = setup_ctx(c, N, !c->opts.rlt1_only, U, &stage);
+    if (c->opts.store != RLT2_STORE_TILES && c->opts.store != RLT2_STORE_CLASSES) {
+        free_ctx(c);
+        return RLT2_E_INVAL;
+    }
+    rc = setup_ctx(c, N, !c->opts.rlt1_only, c->opts.store == RLT2_STORE_CLASSES, U, &stage);
     if (rc != RLT2_OK) {
         free_ctx(c);
         return rc;
@@ -393,13 +406,14 @@ int rlt2_save(rlt2_ctx *c, const char *path)
     std::memcpy(h.magic, kCkptMagic, 8);
     h.version = 1;
     h.N = nd.N;
-    h.with_d = nd.p.z != nullptr;
+    h.with_d = nd.p.z != nullptr || nd.p.T != nullptr;
+    h.sym = nd.p.T != nullptr;
     h.iter = it;
     CK(cudaMemcpy(&h.stop, nd.p.stop, 4, cudaMemcpyDeviceToHost));
     h.LB = lb;
     h.U = c->U;
     h.tiles = nd.tiles;
-    h.z_ints = h.with_d ? nd.tiles * nd.TS : 0;
+    h.z_ints = !h.with_d ? 0 : h.sym ? make_geom(nd.N).classes_ints + nd.tiles * nd.DS : nd.tiles * nd.TS;
     FILE *f = std::fopen(path, "wb");
     if (!f) return RLT2_E_IO;
     const int nh = std::min(it, c->opts.max_iters);
@@ -407,7 +421,11 @@ int rlt2_save(rlt2_ctx *c, const char *path)
     if (rc == RLT2_OK) rc = file_device(f, (char *)nd.p.hist, (size_t)nh * 8, true, c->stream);
     if (rc == RLT2_OK) rc = file_device(f, (char *)nd.p.x, (size_t)nd.N * nd.N * 4, true, c->stream);
     if (rc == RLT2_OK) rc = file_device(f, (char *)nd.p.yC, (size_t)nd.tiles * 4, true, c->stream);
-    if (rc == RLT2_OK && h.with_d) rc = file_device(f, (char *)nd.p.z, (size_t)h.z_ints * 4, true, c->stream);
+    if (rc == RLT2_OK && h.with_d && !h.sym)
+        rc = file_device(f, (char *)nd.p.z, (size_t)h.z_ints * 4, true, c->stream);
+    if (rc == RLT2_OK && h.sym)
+        rc = file_device(f, (char *)nd.p.T, (size_t)make_geom(nd.N).classes_ints * 4, true, c->stream);
+    if (rc == RLT2_OK && h.sym) rc = file_device(f, (char *)nd.p.du, (size_t)nd.tiles * nd.DS * 4, true, c->stream);
     if (std::fclose(f) != 0 && rc == RLT2_OK) rc = RLT2_E_IO;
     return rc;
 }
@@ -424,8 +442,10 @@ int rlt2_load(const char *path, const rlt2_opts *opts, rlt2_ctx **out)
     do {
         if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1 ||
             h.N < RLT2_MIN_N || h.N > RLT2_MAX_N || h.iter < 0 || h.U < 0 || h.U > RLT2_LAP_MAX_ENTRY ||
-            h.tiles != make_geom(h.N).tiles ||
-            h.z_ints != (h.with_d ? h.tiles * (long long)make_geom(h.N).TS : 0)) {
+            h.tiles != make_geom(h.N).tiles || (h.sym != 0 && h.sym != 1) || (h.sym && !h.with_d) ||
+            h.z_ints != (!h.with_d ? 0
+                         : h.sym ? make_geom(h.N).classes_ints + h.tiles * (long long)make_geom(h.N).DS
+                                 : h.tiles * (long long)make_geom(h.N).TS)) {
             rc = RLT2_E_IO;
             break;
         }
@@ -435,17 +455,25 @@ int rlt2_load(const char *path, const rlt2_opts *opts, rlt2_ctx **out)
             break;
         }
         c->opts.rlt1_only = !h.with_d;
+        c->opts.store = h.sym ? RLT2_STORE_CLASSES : RLT2_STORE_TILES;
         if (h.iter > c->opts.max_iters) {  // the history must fit
             rc = RLT2_E_INVAL;
             break;
         }
         int32_t *stage = nullptr;
-        if ((rc = setup_ctx(c, h.N, h.with_d != 0, h.U, &stage)) != RLT2_OK) break;
+        if ((rc = setup_ctx(c, h.N, h.with_d != 0, h.sym != 0, h.U, &stage)) != RLT2_OK) break;
         const NodeDesc &nd = c->node;
         if ((rc = file_device(f, (char *)nd.p.hist, (size_t)h.iter * 8, false, c->stream)) != RLT2_OK) break;
         if ((rc = file_device(f, (char *)nd.p.x, (size_t)h.N * h.N * 4, false, c->stream)) != RLT2_OK) break;
         if ((rc = file_device(f, (char *)nd.p.yC, (size_t)h.tiles * 4, false, c->stream)) != RLT2_OK) break;
-        if (h.with_d && (rc = file_device(f, (char *)nd.p.z, (size_t)h.z_ints * 4, false, c->stream)) != RLT2_OK)
+        if (h.with_d && !h.sym &&
+            (rc = file_device(f, (char *)nd.p.z, (size_t)h.z_ints * 4, false, c->stream)) != RLT2_OK)
+            break;
+        if (h.sym && (rc = file_device(f, (char *)nd.p.T, (size_t)make_geom(h.N).classes_ints * 4, false,
+                                       c->stream)) != RLT2_OK)
+            break;
+        if (h.sym &&
+            (rc = file_device(f, (char *)nd.p.du, (size_t)h.tiles * nd.DS * 4, false, c->stream)) != RLT2_OK)
             break;
         cudaError_t e = cudaMemcpyAsync(nd.p.LB, &h.LB, 8, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(nd.p.iter, &h.iter, 4, cudaMemcpyHostToDevice, c->stream);
@@ -530,16 +558,31 @@ int rlt2_get_state(rlt2_ctx *c, int level, int32_t *host, size_t count)
         if (count != (size_t)nd.tiles) return RLT2_E_INVAL;
         CK(cudaMemcpyAsync(host, nd.p.yC, count * 4, cudaMemcpyDeviceToHost, c->stream));
     } else if (level == 2) {
-        if (!nd.p.z || count != (size_t)nd.tiles * n * n) return RLT2_E_INVAL;
+        if ((!nd.p.z && !nd.p.T) || count != (size_t)nd.tiles * n * n) return RLT2_E_INVAL;
         // the store's rows are indexed by location: drop the tile's own two
-        // locations (and the padding) to reach the compact layout
+        // locations (and the padding) to reach the compact layout; the
+        // class-sum store is first expanded to that layout on the device
         std::vector<int32_t> tmp;
         try {
             tmp.resize((size_t)nd.tiles * nd.TS);
         } catch (...) {
             return RLT2_E_OOM;
         }
-        CK(cudaMemcpyAsync(tmp.data(), nd.p.z, tmp.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+        if (nd.p.z) {
+            CK(cudaMemcpyAsync(tmp.data(), nd.p.z, tmp.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+        } else {
+            int *dz = nullptr;
+            cudaError_t e = cudaMallocAsync((void **)&dz, tmp.size() * 4, c->stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return cuda_code(e);
+            }
+            e = launch_materialize(nd, dz, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(tmp.data(), dz, tmp.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+            cudaFreeAsync(dz, c->stream);
+            if (e != cudaSuccess) return cuda_code(e);
+        }
         CK(cudaStreamSynchronize(c->stream));
         const int m = N - 1, W = nd.W;
         size_t o = 0;
@@ -603,17 +646,18 @@ void *rlt2_device_state(rlt2_ctx *c, int which)
     switch (which) {
     case 0: return c->node.p.x;
     case 1: return c->node.p.yC;
-    case 2: return c->node.p.z;
+    case 2: return c->node.p.z ? (void *)c->node.p.z : (void *)c->node.p.T;
+    case 3: return c->node.p.du;
     default: return nullptr;
     }
 }
 
-size_t rlt2_state_bytes(int N, int rlt1_only, int max_iters)
+size_t rlt2_state_bytes(int N, int rlt1_only, int max_iters, int store)
 {
     if (N < RLT2_MIN_N || N > RLT2_MAX_N) return 0;
     if (max_iters <= 0) max_iters = 65536;
     Arena a;
-    plan_node(a, N, !rlt1_only, max_iters);
+    plan_node(a, N, !rlt1_only, store == RLT2_STORE_CLASSES, max_iters);
     a.take(sizeof(NodeDesc));
     a.take((size_t)n_triples(N) * sizeof(int4));
     a.take(4);
@@ -657,7 +701,8 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     if (!out || !ctxs || count < 1) return RLT2_E_INVAL;
     *out = nullptr;
     for (int b = 0; b < count; b++)
-        if (!ctxs[b] || ctxs[b]->g.rlt1_only != ctxs[0]->g.rlt1_only) return RLT2_E_INVAL;
+        if (!ctxs[b] || ctxs[b]->g.rlt1_only != ctxs[0]->g.rlt1_only || ctxs[b]->g.sym != ctxs[0]->g.sym)
+            return RLT2_E_INVAL;
     rlt2_group *gr = new (std::nothrow) rlt2_group();
     if (!gr) return RLT2_E_OOM;
     auto fail = [&](int code) {
@@ -722,6 +767,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     g.JC = JC;
     g.pack = pack;
     g.rlt1_only = ctxs[0]->g.rlt1_only;
+    g.sym = ctxs[0]->g.sym;
     g.counter = reinterpret_cast<unsigned *>(gr->mem + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(gr->mem + o_st);
     g.triples = reinterpret_cast<const int4 *>(gr->mem + o_tri);
@@ -856,7 +902,9 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     // one allocation for the whole group
     Arena a;
     std::vector<NodeOffsets> no(B);
-    for (int b = 0; b < B; b++) no[b] = plan_node(a, in[b].Np, true, hist_cap);
+    if (o.store != RLT2_STORE_TILES && o.store != RLT2_STORE_CLASSES) return RLT2_E_INVAL;
+    const bool sym = o.store == RLT2_STORE_CLASSES;
+    for (int b = 0; b < B; b++) no[b] = plan_node(a, in[b].Np, true, sym, hist_cap);
     const std::vector<int4> tri = triple_table(maxN);
     const size_t o_nodes = a.take((size_t)B * sizeof(NodeDesc));
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
@@ -911,6 +959,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     g.JC = JC;
     g.pack = pack;
     g.rlt1_only = false;
+    g.sym = sym;
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
     g.triples = reinterpret_cast<const int4 *>(base + o_tri);

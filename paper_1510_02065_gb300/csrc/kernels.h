@@ -26,7 +26,10 @@ struct Geom {
     int n;            // N - 2: rows (and coefficients per row) of a tile
     int W;            // row width in ints, round_up(N, 4)
     int TS;           // tile stride, ints (n * W)
+    int U0;           // class-sum store: offset of v in a tile's duals, round_up(n, 4)
+    int DS;           // class-sum store: ints of duals per tile, U0 + W
     long long tiles;  // N^2 (N-1)^2
+    long long classes_ints;  // class-sum store: C(N,3) N^3 ints
 };
 
 inline Geom make_geom(int N)
@@ -36,13 +39,66 @@ inline Geom make_geom(int N)
     g.n = N - 2;
     g.W = (N + 3) & ~3;
     g.TS = g.n * g.W;
+    g.U0 = (g.n + 3) & ~3;
+    g.DS = g.U0 + g.W;
     g.tiles = (long long)N * N * (N - 1) * (N - 1);
+    g.classes_ints = (long long)N * (N - 1) * (N - 2) / 6 * N * N * N;
     return g;
+}
+
+// Class-sum store of D (the alternative to the tile store): the six members
+// of a class {(x,lx),(y,ly),(z,lz)}, facilities x < y < z, hold after the
+// transfer between complementary costs floor(T/6) + [rank < T mod 6] of its
+// sum T (rank = lexicographic rank of the member, Eq. (11)), so one int per
+// class, T[tri_index(x,y,z) N^3 + lx N^2 + ly N + lz], and the duals (u, v) of
+// each tile's last LAP determine every reduced cost of D: d = member - u_r - v_q.
+__host__ __device__ inline long long tri_index(int x, int y, int z)
+{
+    return (long long)z * (z - 1) * (z - 2) / 6 + y * (y - 1) / 2 + x;
+}
+
+// Row of tile (i,j,k,n) held by facility e (e not in {i,k}) in the class-sum
+// store: the member at column (location) f is T[base + f * stride]; rank is
+// the lexicographic rank of the member ordering (i, k, e) of its class.
+struct SymRow {
+    long long base;
+    int stride, rank;
+};
+
+__host__ __device__ inline SymRow sym_row(int N, int i, int j, int k, int n, int e)
+{
+    const int a = i < k ? i : k, c = i < k ? k : i, la = i < k ? j : n, lc = i < k ? n : j;
+    const long long N2 = (long long)N * N, N3 = N2 * N;
+    SymRow s;
+    if (e < a) {
+        s.base = tri_index(e, a, c) * N3 + (long long)la * N + lc;
+        s.stride = (int)N2;
+    } else if (e < c) {
+        s.base = tri_index(a, e, c) * N3 + (long long)la * N2 + lc;
+        s.stride = N;
+    } else {
+        s.base = tri_index(a, c, e) * N3 + (long long)la * N2 + (long long)lc * N;
+        s.stride = 1;
+    }
+    // positions of i, k, e among the sorted three; orderings of (x, y, z) in
+    // lexicographic order have ranks 2 * (position of the first) + [second > third]
+    const int pi = (i > k) + (i > e), pk = (k > i) + (k > e), pe = (e > i) + (e > k);
+    s.rank = 2 * pi + (pk > pe ? 1 : 0);
+    return s;
+}
+
+// Member of rank `rank` of a class with sum T >= 0 (Eq. (11), equal split).
+__host__ __device__ inline int sym_member(int T, int rank)
+{
+    const int q = (int)((unsigned)T / 6u);
+    return q + (rank < T - 6 * q ? 1 : 0);
 }
 
 // Device state of one instance.
 struct PassState {
-    int *z;            // tile store of D (null without D)
+    int *z;            // tile store of D (null without D or with the class-sum store)
+    int *T;            // class-sum store (null unless it is used)
+    int *du;           // per tile: u of its N-2 rows (padded to U0), then v of its W location columns
     int *yS;           // per tile: c' before D->C, then S of the tile's LAP
     int *yC;           // reduced C after concentration C->B
     int *x;            // reduced B
@@ -62,10 +118,11 @@ struct NodeDesc {
     // moves them (valid when zmap_ok; m = N - 1, the box overhang m|1 > m only
     // pads the shared-memory pitch and is out of bounds, zero-filled on load
     // and skipped on store).
-    CUtensorMap zmap;
+    CUtensorMap zmap;     // class-sum store: the same box over the v part of the tile duals
     int zmap_ok;
     PassState p;
     int N, W, TS;
+    int U0, DS;           // class-sum store: dual offsets (Geom)
     int nchunks;          // location chunks of the fused pass over D
     long long tiles;
     long long tile_base;  // first group-wide tile index of this instance
@@ -80,6 +137,8 @@ inline void fill_node(NodeDesc &d, int N, int JC)
     d.N = N;
     d.W = g.W;
     d.TS = g.TS;
+    d.U0 = g.U0;
+    d.DS = g.DS;
     d.tiles = g.tiles;
     d.nchunks = (N + JC - 1) / JC;
     d.fN = make_fastdiv(N);
@@ -100,6 +159,7 @@ struct Group {
     int JC;                 // locations per fused-pass CTA (one value for the group)
     bool pack;              // every instance's keys fit the packed reduction
     bool rlt1_only;
+    bool sym;               // D in the class-sum store (every instance of the group)
     unsigned *counter;      // D->C work counter
     DevStatus *status;      // error bits and work counters of the group
     const int4 *triples;    // facility triples i<k<p ordered by p: the first C(N,3) serve N
@@ -117,6 +177,9 @@ size_t p1_smem_bytes(int N, int JC);   // its dynamic shared memory
 cudaError_t launch_init(const NodeDesc &node, const int32_t *F, const int32_t *D,
                         const int32_t *Blin, long long lb_const, cudaStream_t s);
 cudaError_t launch_spread_x(const Group &g, cudaStream_t s);
+// Reduced costs of D of a class-sum-store instance in the tile-store layout
+// (tiles x (N-2) x W ints at out; columns without coefficient 0).
+cudaError_t launch_materialize(const NodeDesc &nd, int *out, cudaStream_t s);
 cudaError_t launch_p1(const Group &g, cudaStream_t s);
 cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s);
 cudaError_t launch_clap(const Group &g, cudaStream_t s);

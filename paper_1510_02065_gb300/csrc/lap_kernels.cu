@@ -71,13 +71,71 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
     return true;
 }
 
+// The same for an instance in the class-sum store: the tile is gathered from
+// the class sums (one 4-byte asynchronous copy per coefficient, all in flight
+// at once), each coefficient becomes its member value in place, and the LAP's
+// duals (u of every row, v of every location column) go to du instead of a
+// residual tile.
+template <int NS, bool PACK>
+__device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, int *buf, int *uRow,
+                                              int lane, unsigned &steps, unsigned &relax,
+                                              DevStatus *status)
+{
+    const int N = nd.N, W = nd.W, n = N - 2, m = N - 1;
+    const unsigned ij = fdiv(t, nd.fmm);
+    const unsigned rem = t - ij * (unsigned)(m * m);
+    const int kk = (int)fdiv(rem, nd.fm), nn = (int)rem - kk * m;
+    const int i = (int)fdiv(ij, nd.fN), j = (int)ij - i * N;
+    const int k = kk + (kk >= i), nl = nn + (nn >= j);
+    const int lo = min(i, k), hi = max(i, k);
+    const int *T = nd.p.T;
+    for (int r = 0; r < n; ++r) {
+        int e = r + (r >= lo);
+        e += (e >= hi);
+        const SymRow sr = sym_row(N, i, j, k, nl, e);
+        if (lane == 0) uRow[r] = sr.rank;  // parked until the conversion below
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int f = lane + 32 * s;
+            if (f < N && f != j && f != nl) cp_async4(buf + r * W + f, T + sr.base + (long long)f * sr.stride);
+        }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    for (int r = 0; r < n; ++r) {
+        const int rank = uRow[r];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int f = lane + 32 * s;
+            if (f < N && f != j && f != nl) buf[r * W + f] = sym_member(buf[r * W + f], rank);
+        }
+    }
+    __syncwarp();
+    int rowOf[NS], uM[NS], v[NS];
+    if (!warp_hungarian<NS, PACK>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
+        atomicOr(&status->err, kDevInternal);
+    scatter_rows<NS>(n, N, j, nl, rowOf, uM, uRow, nullptr);
+    __syncwarp();
+    int *du = nd.p.du + (size_t)t * nd.DS;
+    for (int r = lane; r < n; r += 32) du[r] = uRow[r];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int f = lane + 32 * s;
+        if (f < W) du[nd.U0 + f] = (f < N && f != j && f != nl) ? v[s] : 0;
+    }
+    const long long S = lap_value<NS>(N, j, nl, uM, v);
+    if (lane == 0) nd.p.yS[t] = (int)S;
+    __syncwarp();
+    return true;
+}
+
 // One tile buffer per warp; a warp takes group-wide tile indices from a global
 // counter, finds the tile's instance and solves the tile's LAP.  Tiles of one
 // instance are consecutive in the group-wide order, so the instance found for
 // the previous tile is tried first.  ONE (a group of one instance): the
 // instance is the kernel parameter g.first, read from parameter space, and the
 // stopping rule is checked once.
-template <int NS, bool PACK, bool ONE>
+template <int NS, bool PACK, bool ONE, bool SYM>
 __global__ void __launch_bounds__(kDlapWarps * 32, 16) dlap_kernel(Group g)
 {
     if (ONE && *g.first.p.stop) return;
@@ -104,7 +162,16 @@ __global__ void __launch_bounds__(kDlapWarps * 32, 16) dlap_kernel(Group g)
         T = __shfl_sync(kFull, T, 0);
         if (T >= ntiles) break;
         bool ok;
-        if constexpr (ONE) {
+        if constexpr (SYM && ONE) {
+            ok = dlap_tile_sym<NS, PACK>(g.first, T, buf, uRow, lane, steps, relax, g.status);
+        } else if constexpr (SYM) {
+            if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
+                b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
+            const NodeDesc &nd = g.nodes[b];
+            if (*nd.p.stop) continue;
+            ok = dlap_tile_sym<NS, PACK>(nd, T - (unsigned)nd.tile_base, buf, uRow, lane, steps, relax,
+                                         g.status);
+        } else if constexpr (ONE) {
             ok = dlap_tile<NS, PACK>(g.first, T, buf, bar, parity, uRow, lane, steps, relax, g.status);
         } else {
             if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
@@ -295,11 +362,11 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
 
 // ---------------------------------------------------------------- launchers
 
-template <int NS, bool PACK, bool ONE>
+template <int NS, bool PACK, bool ONE, bool SYM>
 static cudaError_t dlap_go(const Group &g, int sm_count, cudaStream_t s)
 {
     const size_t smem = (size_t)kDlapWarps * ((size_t)g.maxTS * 4 + 8 + 256);
-    auto k = dlap_kernel<NS, PACK, ONE>;
+    auto k = dlap_kernel<NS, PACK, ONE, SYM>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -315,16 +382,18 @@ static cudaError_t dlap_go(const Group &g, int sm_count, cudaStream_t s)
 }
 
 // The work counter is reset by the fused pass over D, which precedes this kernel.
+template <bool ONE, bool SYM>
+static cudaError_t dlap_pick(const Group &g, int sm_count, cudaStream_t s)
+{
+    if (g.maxN <= 32)
+        return g.pack ? dlap_go<1, true, ONE, SYM>(g, sm_count, s) : dlap_go<1, false, ONE, SYM>(g, sm_count, s);
+    return g.pack ? dlap_go<2, true, ONE, SYM>(g, sm_count, s) : dlap_go<2, false, ONE, SYM>(g, sm_count, s);
+}
+
 cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s)
 {
-    if (g.B == 1) {
-        if (g.maxN <= 32)
-            return g.pack ? dlap_go<1, true, true>(g, sm_count, s) : dlap_go<1, false, true>(g, sm_count, s);
-        return g.pack ? dlap_go<2, true, true>(g, sm_count, s) : dlap_go<2, false, true>(g, sm_count, s);
-    }
-    if (g.maxN <= 32)
-        return g.pack ? dlap_go<1, true, false>(g, sm_count, s) : dlap_go<1, false, false>(g, sm_count, s);
-    return g.pack ? dlap_go<2, true, false>(g, sm_count, s) : dlap_go<2, false, false>(g, sm_count, s);
+    if (g.sym) return g.B == 1 ? dlap_pick<true, true>(g, sm_count, s) : dlap_pick<false, true>(g, sm_count, s);
+    return g.B == 1 ? dlap_pick<true, false>(g, sm_count, s) : dlap_pick<false, false>(g, sm_count, s);
 }
 
 template <int NS, bool PACK>

@@ -114,15 +114,20 @@ bool encode_zmap(NodeDesc &nd, int JC)
 {
     nd.zmap_ok = 0;
     std::memset(&nd.zmap, 0, sizeof(nd.zmap));
-    if (JC != 4 || !nd.p.z) return false;
+    if (JC != 4 || (!nd.p.z && !nd.p.du)) return false;
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t N = (cuuint64_t)nd.N, m = N - 1, W = (cuuint64_t)nd.W, n = N - 2;
-    const cuuint64_t dim[5] = {W, n, m, m, N * N};
-    const cuuint64_t stride[4] = {W * 4, W * n * 4, W * n * m * 4, W * n * m * m * 4};
+    // tile store: (column, row, n', k', i*N + j); class-sum store: the v row of
+    // every tile as (column, -, n', k', i*N + j) with the tile's dual stride
+    const cuuint64_t R = nd.p.z ? W : (cuuint64_t)nd.DS;  // ints per row step
+    const cuuint64_t rows = nd.p.z ? n : 1;
+    const cuuint64_t dim[5] = {W, rows, m, m, N * N};
+    const cuuint64_t stride[4] = {R * 4, R * rows * 4, R * rows * m * 4, R * rows * m * m * 4};
     const cuuint32_t box[5] = {4, 1, (cuuint32_t)(m | 1), 1, (cuuint32_t)N};
     const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
-    if (fn(&nd.zmap, CU_TENSOR_MAP_DATA_TYPE_INT32, 5, nd.p.z, dim, stride, box, estride,
+    void *base = nd.p.z ? (void *)nd.p.z : (void *)(nd.p.du + nd.U0);
+    if (fn(&nd.zmap, CU_TENSOR_MAP_DATA_TYPE_INT32, 5, base, dim, stride, box, estride,
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
@@ -205,13 +210,12 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
     const PassState p = nd.p;
     if (*p.stop) return;
     const int N = nd.N, W = nd.W, nchunks = nd.nchunks;
-    const FastDiv fN = nd.fN, fW4 = nd.fW4, fn = nd.fn;
+    const FastDiv fN = nd.fN, fn = nd.fn;
     const int bid = blockIdx.x - nd.cta_base;
     extern __shared__ __align__(128) int sm[];
     const P1Layout L = p1_layout(N, W, JC);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t TS = (size_t)(N - 2) * W;
-    const int W4 = W >> 2;
     const int4 tr = g.triples[bid / nchunks];
     const int i = tr.x, k = tr.y, pp = tr.z;
     const int j0 = (bid % nchunks) * JC;
@@ -355,6 +359,165 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
     bulk_wait_read_all();  // shared memory stays valid until the bulk stores have read it
 }
 
+// The same pass for an instance in the class-sum store.  The reduced cost of a
+// member is (its value from the class sum) - u_row - v_col of its tile's last
+// LAP, and the six values of a class sum back to T (the split is lossless), so
+// spread C -> D followed by the transfer between complementary costs is
+//   T <- T + sum over the six members of (share of c' - u_row) - v_col,
+// the split itself being implicit in the store.  The CTA stages the v rows and
+// v pieces of the member tiles exactly as the tile-store pass stages tile rows
+// (same layout, bulk and tensor copies from du instead of z) and the per-tile
+// (share - u_row) terms in the H arrays; T is read and written in place.
+template <int JC, bool ONE>
+__global__ void __launch_bounds__(kP1Threads, 2) p1_sym_kernel(const __grid_constant__ Group g)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *g.counter = 0;  // work counter of the D -> C sweep
+    const NodeDesc &nd =
+        ONE ? g.first
+            : g.nodes[find_node(g.nodes, g.B, blockIdx.x, [](const NodeDesc &d) { return (long long)d.cta_base; })];
+    const PassState p = nd.p;
+    if (*p.stop) return;
+    const int N = nd.N, W = nd.W, nchunks = nd.nchunks;
+    const FastDiv fN = nd.fN, fn = nd.fn;
+    const int bid = blockIdx.x - nd.cta_base;
+    extern __shared__ __align__(128) int sm[];
+    const P1Layout L = p1_layout(N, W, JC);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tri = bid / nchunks;
+    const int4 tr = g.triples[tri];
+    const int i = tr.x, k = tr.y, pp = tr.z;
+    const int j0 = (bid % nchunks) * JC;
+    const int jc = min(JC, N - j0);
+    const int *__restrict__ yS = p.yS;
+    const int *__restrict__ du = p.du;
+    const int DS = nd.DS, U0 = nd.U0;
+    const int NN = N * N;
+    int *__restrict__ Tb = p.T + (long long)tri * NN * N;  // this triple's classes [j][n][q]
+
+    __shared__ __align__(8) uint64_t bar;
+    const bool tma = JC == 4 && nd.zmap_ok;
+    const void *zmap = &nd.zmap;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (!ONE && tma) tensormap_acquire(zmap);
+    }
+    __syncthreads();
+    const unsigned rowBytes = (unsigned)W * 4u;
+    if (threadIdx.x == 0) {
+        const unsigned pieceBytes = tma ? 2u * (unsigned)(N * L.P46) * 4u : 0u;
+        mbar_arrive_expect_tx(&bar, (unsigned)(4 * jc * (N - 1)) * rowBytes + pieceBytes);
+        if (tma) {
+            tensor_load5(sm + L.A4, zmap, j0, 0, 0, pp - 1, k * N, &bar);  // v of tiles (k,a,p,l)
+            tensor_load5(sm + L.A6, zmap, j0, 0, 0, k, pp * N, &bar);      // v of tiles (p,a,k,l)
+        }
+    }
+    for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
+        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
+        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
+        if (jj >= jc || x == j) continue;
+        int t, row;
+        full_row(q, N, i, k, pp, j, x, t, row);
+        const int base = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
+        const int pitch = q < 2 ? L.S13 : L.S25;
+        bulk_load_tx(sm + base + (jj * N + x) * pitch, du + (size_t)t * DS + U0, rowBytes, &bar);
+    }
+    for (int e = tma ? 2 * NN : threadIdx.x; e < 2 * NN; e += kP1Threads) {
+        const int kind = e >= NN, r2 = e - kind * NN;
+        const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
+        if (l == a) continue;
+        const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
+        cp_async_piece<JC>(sm + (kind ? L.A6 : L.A4) + a * L.P46 + (l - (l > a)) * JC,
+                           du + (size_t)t * DS + U0 + j0);
+    }
+
+    // ---- (share of c' - u) of every member tile at the member's row
+    for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
+        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
+        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
+        if (jj >= jc || x == j) continue;
+        int t, row;
+        full_row(q, N, i, k, pp, j, x, t, row);
+        const int hb = q == 0 ? L.H1 : q == 1 ? L.H3 : q == 2 ? L.H2 : L.H5;
+        sm[hb + jj * N + x] = share(yS[t], fn, row) - du[(size_t)t * DS + row];
+    }
+    for (int e = threadIdx.x; e < 2 * NN; e += kP1Threads) {
+        const int kind = e >= NN, r2 = e - kind * NN;
+        const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
+        if (l == a) continue;
+        const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
+        sm[(kind ? L.H6 + a * L.H6p : L.H4 + a * N) + l] = share(yS[t], fn, i) - du[(size_t)t * DS + i];
+    }
+
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (__syncthreads_or(!mbar_wait(&bar, 0))) {
+        if (threadIdx.x == 0) atomicOr(&g.status->err, kDevTimeout);
+        mbar_wait(&bar, 0);
+        __syncthreads();
+        return;
+    }
+
+    // ---- new class sums: warp per location n, lanes over q, each lane the
+    // chunk's classes of its (n, q)
+    for (int nn = warp; nn < N; nn += kP1Warps) {
+        const int *h4 = sm + L.H4 + nn * N, *h6 = sm + L.H6 + nn;
+        for (int qq = lane; qq < N; qq += 32) {
+            if (qq == nn) continue;
+            int p4[JC], p6[JC];
+            load_piece<JC>(p4, sm + L.A4 + nn * L.P46 + (qq - (qq > nn)) * JC);
+            load_piece<JC>(p6, sm + L.A6 + qq * L.P46 + (nn - (nn > qq)) * JC);
+            const int h46 = (int)((unsigned)h4[qq] + (unsigned)h6[qq * L.H6p]);
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj) {
+                const int j = j0 + jj;
+                if (jj >= jc || j == nn || j == qq) continue;
+                const int rn = jj * N + nn, rq = jj * N + qq;
+                // modular (unsigned) sums: the partial sums may leave int32,
+                // the new class sum (a sum of six reduced costs) does not
+                const unsigned vsum = (unsigned)sm[L.A1 + rn * L.S13 + qq] + (unsigned)sm[L.A3 + rn * L.S13 + qq] +
+                                      (unsigned)sm[L.A2 + rq * L.S25 + nn] + (unsigned)sm[L.A5 + rq * L.S25 + nn] +
+                                      (unsigned)p4[jj] + (unsigned)p6[jj];
+                const unsigned hsum = (unsigned)sm[L.H1 + rn] + (unsigned)sm[L.H3 + rn] + (unsigned)sm[L.H2 + rq] +
+                                      (unsigned)sm[L.H5 + rq] + (unsigned)h46;
+                int *Tc = Tb + (j * N + nn) * N + qq;
+                *Tc = (int)((unsigned)*Tc + hsum - vsum);
+            }
+        }
+    }
+}
+
+// Reduced costs of D of a class-sum-store instance in the tile-store layout.
+__global__ void materialize_kernel(const NodeDesc nd, int *out)
+{
+    const int N = nd.N, n = N - 2, m = N - 1, W = nd.W;
+    const long long total = nd.tiles * n;  // (tile, row) pairs
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long t = e / n;
+        const int r = (int)(e - t * n);
+        const int nn = (int)(t % m), kk = (int)((t / m) % m), ij = (int)(t / ((long long)m * m));
+        const int i = ij / N, j = ij % N, k = kk + (kk >= i), nl = nn + (nn >= j);
+        const int lo = min(i, k), hi = max(i, k);
+        int ep = r + (r >= lo);
+        ep += (ep >= hi);
+        const SymRow sr = sym_row(N, i, j, k, nl, ep);
+        const int *d = nd.p.du + t * nd.DS;
+        int *o = out + t * nd.TS + (long long)r * W;
+        for (int f = 0; f < W; ++f)
+            o[f] = (f < N && f != j && f != nl)
+                       ? sym_member(nd.p.T[sr.base + (long long)f * sr.stride], sr.rank) - d[r] - d[nd.U0 + f]
+                       : 0;
+    }
+}
+
+cudaError_t launch_materialize(const NodeDesc &nd, int *out, cudaStream_t s)
+{
+    long long blocks = (nd.tiles * (nd.N - 2) + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    materialize_kernel<<<(unsigned)blocks, 256, 0, s>>>(nd, out);
+    return cudaGetLastError();
+}
+
 // Costs spreading from B to C (Sec. 4.2): c'_ijkn = c_ijkn + the share of b_ij
 // of row k (k' = rank of k among the facilities != i), written to yS.  One
 // thread per tile of the group.
@@ -412,6 +575,8 @@ cudaError_t launch_init(const NodeDesc &nd, const int32_t *F, const int32_t *D,
     const PassState &p = nd.p;
     cudaError_t e = cudaSuccess;
     if (p.z) e = cudaMemsetAsync(p.z, 0, (size_t)nd.tiles * nd.TS * 4, s);
+    if (e == cudaSuccess && p.T) e = cudaMemsetAsync(p.T, 0, (size_t)make_geom(nd.N).classes_ints * 4, s);
+    if (e == cudaSuccess && p.du) e = cudaMemsetAsync(p.du, 0, (size_t)nd.tiles * nd.DS * 4, s);
     if (e != cudaSuccess) return e;
     long long grid = (nd.tiles + 255) / 256;
     if (grid > 8192) grid = 8192;
@@ -428,7 +593,8 @@ template <int JC>
 static cudaError_t p1_go(const Group &g, cudaStream_t s)
 {
     const size_t smem = p1_smem_bytes(g.maxN, JC);
-    auto k = g.B == 1 ? p1_kernel<JC, true> : p1_kernel<JC, false>;
+    auto k = g.sym ? (g.B == 1 ? p1_sym_kernel<JC, true> : p1_sym_kernel<JC, false>)
+                   : (g.B == 1 ? p1_kernel<JC, true> : p1_kernel<JC, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<g.ctas, kP1Threads, smem, s>>>(g);

@@ -28,6 +28,8 @@ RLT2_E_TIMEOUT = -5
 RLT2_E_STATE = -6
 RLT2_E_INTERNAL = -7
 RLT2_E_IO = -8
+RLT2_STORE_TILES = 0
+RLT2_STORE_CLASSES = 1
 RLT2_MIN_N = 3
 RLT2_MAX_N = 64
 RLT2_LAP_MAX_ENTRY = 536870911
@@ -46,7 +48,7 @@ class rlt2_node(C.Structure):
 class rlt2_opts(C.Structure):
     _fields_ = [("rlt1_only", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
                 ("max_iters", C.c_int), ("ub", C.c_double), ("min_progress", C.c_double),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("store", C.c_int)]
 
 
 _lib = None
@@ -83,7 +85,7 @@ def lib():
         "rlt2_row_stride": (C.c_int, [C.c_int]),
         "rlt2_lap_batch": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "rlt2_lap_batch_static": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
-        "rlt2_state_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+        "rlt2_state_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int]),
         "rlt2_save": (C.c_int, [_vp, C.c_char_p]),
         "rlt2_load": (C.c_int, [C.c_char_p, C.POINTER(rlt2_opts), C.POINTER(_vp)]),
         "rlt2_group_create": (C.c_int, [C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)]),
@@ -237,8 +239,8 @@ def rlt2_lap_batch_static(M_ptr, n, count, S_ptr, assign_ptr=0, u_ptr=0, v_ptr=0
                                        _vp(stream or None))
 
 
-def rlt2_state_bytes(N, rlt1_only=False, max_iters=65536) -> int:
-    return int(lib().rlt2_state_bytes(int(N), int(rlt1_only), int(max_iters)))
+def rlt2_state_bytes(N, rlt1_only=False, max_iters=65536, store=RLT2_STORE_TILES) -> int:
+    return int(lib().rlt2_state_bytes(int(N), int(rlt1_only), int(max_iters), int(store)))
 
 
 def rlt2_group_create(ctxs, stream=0):
@@ -277,7 +279,7 @@ def rlt2_subproblem(F, D, fac, loc):
     return Fp, Dp, Bl, cst.value
 
 
-def rlt2_batch_bound(F, D, nodes, iters, stream=0):
+def rlt2_batch_bound(F, D, nodes, iters, stream=0, store=RLT2_STORE_TILES):
     """nodes: list of (fac, loc) arrays -> (LB per node as int64 array, device ms)."""
     F = np.ascontiguousarray(F, np.int32)
     D = np.ascontiguousarray(D, np.int32)
@@ -289,6 +291,7 @@ def rlt2_batch_bound(F, D, nodes, iters, stream=0):
         arr[b].loc = _p32(l)
     o = rlt2_default_opts()
     o.stream = stream or None
+    o.store = int(store)
     out = np.zeros(len(keep), np.int64)
     ms = C.c_double()
     _chk(lib().rlt2_batch_bound(_p32(F), _p32(D), F.shape[0], arr, len(keep), int(iters), C.byref(o),
@@ -302,15 +305,17 @@ class Context:
     """Owning wrapper of an rlt2_ctx (same calls, released on close/exit)."""
 
     def __init__(self, F, D, B_lin=None, lb_const=0, rlt1_only=False, use_graph=True,
-                 profile=False, max_iters=65536, ub=0.0, min_progress=0.0, stream=0):
-        o = self._opts(rlt1_only, use_graph, profile, max_iters, ub, min_progress, stream)
+                 profile=False, max_iters=65536, ub=0.0, min_progress=0.0, stream=0,
+                 store=RLT2_STORE_TILES):
+        o = self._opts(rlt1_only, use_graph, profile, max_iters, ub, min_progress, stream, store)
         self.N = int(np.asarray(F).shape[0])
         self.ctx = rlt2_create(F, D, self.N, B_lin, lb_const, o)
 
     @staticmethod
     def _opts(rlt1_only=False, use_graph=True, profile=False, max_iters=65536, ub=0.0,
-              min_progress=0.0, stream=0):
+              min_progress=0.0, stream=0, store=RLT2_STORE_TILES):
         o = rlt2_default_opts()
+        o.store = int(store)
         o.rlt1_only = int(rlt1_only)
         o.use_graph = int(use_graph)
         o.profile = int(profile)

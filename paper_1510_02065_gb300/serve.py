@@ -54,7 +54,8 @@ class BoundServer:
     """Admit by memory, bound in shared launches, release on completion."""
 
     def __init__(self, mem_budget: int, max_slots: int = 64, passes_per_round: int = 1,
-                 stream: int = 0):
+                 stream: int = 0, store: int = rlt2.RLT2_STORE_TILES):
+        self.store = int(store)
         self.mem_budget = int(mem_budget)
         self.max_slots = int(max_slots)
         self.passes_per_round = max(1, int(passes_per_round))
@@ -64,7 +65,7 @@ class BoundServer:
         self.slot_rounds = 0
 
     def _bytes(self, req: Request) -> int:
-        return rlt2.rlt2_state_bytes(req.N, False, req.iters + 1)
+        return rlt2.rlt2_state_bytes(req.N, False, req.iters + 1, self.store)
 
     def serve(self, requests: List[Request], realtime: bool = True) -> dict:
         """Serve every request; returns latency / throughput statistics.
@@ -99,7 +100,7 @@ class BoundServer:
                 pending.popleft()
                 try:
                     ctx = rlt2.Context(req.F, req.D, B_lin=req.B_lin, lb_const=req.lb_const,
-                                       max_iters=req.iters + 1, stream=self.stream)
+                                       max_iters=req.iters + 1, stream=self.stream, store=self.store)
                 except rlt2.Rlt2Error as e:
                     req.error = str(e)
                     finished.append(req)

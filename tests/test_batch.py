@@ -54,7 +54,8 @@ def gpu():
 
 
 @pytest.mark.gpu
-def test_batch_equals_single_contexts_and_oracle(gpu, orc):
+@pytest.mark.parametrize("store", [rlt2.RLT2_STORE_TILES, rlt2.RLT2_STORE_CLASSES])
+def test_batch_equals_single_contexts_and_oracle(gpu, orc, store):
     F, D = I.clustered_euclid(12, seed=3)
     nodes = []
     rng = np.random.default_rng(5)
@@ -62,7 +63,7 @@ def test_batch_equals_single_contexts_and_oracle(gpu, orc):
         k = int(rng.integers(0, 8))           # residual sizes 4..12, ragged
         nodes.append((rng.choice(12, size=k, replace=False), rng.choice(12, size=k, replace=False)))
     iters = 7
-    lbs, ms = rlt2.rlt2_batch_bound(F, D, nodes, iters)
+    lbs, ms = rlt2.rlt2_batch_bound(F, D, nodes, iters, store=store)
     assert ms > 0
     for b, (fac, loc) in enumerate(nodes):
         Fp, Dp, Bl, cst = rlt2.rlt2_subproblem(F, D, fac, loc)

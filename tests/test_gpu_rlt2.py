@@ -27,6 +27,7 @@ from tests.layout import compact_y, compact_z, state_hash, tile_indices
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+STORES = [rlt2.RLT2_STORE_TILES, rlt2.RLT2_STORE_CLASSES]
 
 
 @pytest.fixture(scope="module")
@@ -54,11 +55,12 @@ def assert_same_state(ctx, st, where=""):
     assert ctx.bound()[1] == st.LB, where
 
 
+@pytest.mark.parametrize("store", STORES)
 @pytest.mark.parametrize("name", ["uniform_n8", "grid_n12"])
-def test_full_state_every_pass(gpu, orc, name):
+def test_full_state_every_pass(gpu, orc, name, store):
     F, D, iters = I.instance(name)
     st = orc.State(F, D)
-    with rlt2.Context(F, D) as ctx:
+    with rlt2.Context(F, D, store=store) as ctx:
         assert_same_state(ctx, st, "at init")
         for t in range(iters):
             ctx.iterate(1)
@@ -71,14 +73,15 @@ def test_full_state_every_pass(gpu, orc, name):
         assert (w["laps"], w["steps"], w["relaxations"]) == (ow["laps"], ow["steps"], ow["relaxations"])
 
 
+@pytest.mark.parametrize("store", STORES)
 @pytest.mark.parametrize("N,seed", [(3, 0), (4, 1), (5, 2), (6, 3), (7, 4)])
-def test_small_ragged_asymmetric_with_linear_term(gpu, orc, N, seed):
+def test_small_ragged_asymmetric_with_linear_term(gpu, orc, N, seed, store):
     rng = np.random.default_rng(seed)
     F = rng.integers(0, 12, size=(N, N)).astype(np.int32)
     D = rng.integers(0, 12, size=(N, N)).astype(np.int32)
     Bl = rng.integers(0, 40, size=(N, N)).astype(np.int32)
     st = orc.State(F, D, B_lin=Bl, lb_const=123)
-    with rlt2.Context(F, D, B_lin=Bl, lb_const=123, use_graph=(seed % 2 == 0)) as ctx:
+    with rlt2.Context(F, D, B_lin=Bl, lb_const=123, use_graph=(seed % 2 == 0), store=store) as ctx:
         assert_same_state(ctx, st, "at init")
         for t in range(8):
             ctx.iterate(1)
@@ -113,11 +116,12 @@ def test_graph_nograph_profile_agree(gpu, orc):
     assert hs[0] == hs[1] == hs[2] == hs[3] == list(orc.State(F, D).run(5))
 
 
-def test_clustered_n20_against_oracle_and_golden(gpu, orc):
+@pytest.mark.parametrize("store", STORES)
+def test_clustered_n20_against_oracle_and_golden(gpu, orc, store):
     F, D, iters = I.instance("clustered_n20")
     gold = json.load(open(os.path.join(GOLDEN, "lb_clustered_n20.json")))
     st = orc.State(F, D)
-    with rlt2.Context(F, D) as ctx:
+    with rlt2.Context(F, D, store=store) as ctx:
         for t in range(2):
             ctx.iterate(1)
             st.iterate()
@@ -197,7 +201,7 @@ def _conservation_sample(F, D, N, LB, x, y, z, perms):
     return worst
 
 
-def _first_pass_then_properties(orc, F, D, N, seed):
+def _first_pass_then_properties(orc, F, D, N, seed, store=rlt2.RLT2_STORE_TILES):
     """First pass against the oracle (LB, all of B and C, 200,000 sampled D
     entries), then three passes checked through properties that hold at any
     size: non-negative reduced costs, monotone LB, conservation on 100
@@ -205,7 +209,7 @@ def _first_pass_then_properties(orc, F, D, N, seed):
     rng = np.random.default_rng(seed)
     perms = [rng.permutation(N) for _ in range(100)]
     st = orc.State(F, D)
-    with rlt2.Context(F, D) as ctx:
+    with rlt2.Context(F, D, store=store) as ctx:
         ctx.iterate(1)
         st.iterate()
         assert ctx.bound()[1] == st.LB
@@ -237,14 +241,16 @@ def _first_pass_then_properties(orc, F, D, N, seed):
 
 
 @pytest.mark.slow
-def test_headline_n30(gpu, orc):
+@pytest.mark.parametrize("store", STORES)
+def test_headline_n30(gpu, orc, store):
     """The 30-facility workload in the launch configuration the benchmark times."""
     F, D, _ = I.instance("clustered_n30")
-    _first_pass_then_properties(orc, F, D, 30, 30)
+    _first_pass_then_properties(orc, F, D, 30, 30, store)
 
 
 @pytest.mark.slow
-def test_two_slot_lanes_n34(gpu, orc):
+@pytest.mark.parametrize("store", STORES)
+def test_two_slot_lanes_n34(gpu, orc, store):
     """N = 34: LAPs of size 32 and 33 take two column slots per lane, and the
     fused pass over D works on chunks of two locations with per-piece copies.
     The oracle takes the spreading and complementary operations in full and the
@@ -262,7 +268,7 @@ def test_two_slot_lanes_n34(gpu, orc):
     slices = (0, N // 2, N - 1)
     for a in slices:
         st.concentrate_D_to_C_range(a, a + 1)
-    with rlt2.Context(F, D) as ctx:
+    with rlt2.Context(F, D, store=store) as ctx:
         ctx.iterate(1)
         z = ctx.state(2)
         i, j, k, n = [a.astype(np.int64) for a in tile_indices(N)]
@@ -289,3 +295,27 @@ def test_two_slot_lanes_n34(gpu, orc):
         assert x.min() >= 0 and y.min() >= 0 and z.min() >= 0
         assert all(a <= b for a, b in zip(hist, hist[1:]))
         assert _conservation_sample(F, D, N, hist[-1], x, y, z, perms) == 0
+
+
+def test_stores_agree_and_sizes(gpu, orc):
+    """Both stores give the same trajectory (LB history, B, C, D) on an
+    instance with a linear term; the class-sum store is the smaller one."""
+    F, D = I.clustered_euclid(16, seed=3)
+    Bl = np.random.default_rng(3).integers(0, 50, size=(16, 16)).astype(np.int32)
+    res = []
+    for store in STORES:
+        with rlt2.Context(F, D, B_lin=Bl, lb_const=7, store=store) as ctx:
+            ctx.iterate(12)
+            res.append((list(ctx.history()), ctx.state(0), ctx.state(1), ctx.state(2)))
+    assert res[0][0] == res[1][0] == list(orc.State(F, D, B_lin=Bl, lb_const=7).run(12))
+    for a, b in zip(res[0][1:], res[1][1:]):
+        assert (a == b).all()
+    for N in (16, 30, 35, 64):
+        assert rlt2.rlt2_state_bytes(N, store=rlt2.RLT2_STORE_CLASSES) < rlt2.rlt2_state_bytes(N)
+
+
+def test_unknown_store_rejected(gpu):
+    F, D = I.uniform_symmetric(6, seed=1)
+    with pytest.raises(rlt2.Rlt2Error) as e:
+        rlt2.Context(F, D, store=2)
+    assert e.value.code == rlt2.RLT2_E_INVAL

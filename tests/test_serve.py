@@ -33,11 +33,12 @@ def _requests(seed, count):
     return reqs
 
 
-def test_mix_equals_alone_and_budget_holds(gpu, orc):
+@pytest.mark.parametrize("store", [rlt2.RLT2_STORE_TILES, rlt2.RLT2_STORE_CLASSES])
+def test_mix_equals_alone_and_budget_holds(gpu, orc, store):
     reqs = _requests(1, 14)
-    biggest = max(rlt2.rlt2_state_bytes(r.N, False, r.iters + 1) for r in reqs)
+    biggest = max(rlt2.rlt2_state_bytes(r.N, False, r.iters + 1, store) for r in reqs)
     budget = int(2.5 * biggest)
-    srv = BoundServer(mem_budget=budget, max_slots=6, passes_per_round=2)
+    srv = BoundServer(mem_budget=budget, max_slots=6, passes_per_round=2, store=store)
     stats = srv.serve(reqs, realtime=False)
     assert stats["completed"] == len(reqs) and stats["rejected"] == 0
     assert srv.peak_bytes <= budget
@@ -69,3 +70,16 @@ def test_realtime_latency_stats(gpu):
     assert stats["completed"] == 6
     assert 0 < stats["p50_latency"] <= stats["p99_latency"]
     assert stats["throughput"] > 0
+
+
+def test_group_rejects_mixed_stores(gpu):
+    F, D = I.clustered_euclid(7, seed=1)
+    a = rlt2.Context(F, D)
+    b = rlt2.Context(F, D, store=rlt2.RLT2_STORE_CLASSES)
+    try:
+        with pytest.raises(rlt2.Rlt2Error) as e:
+            rlt2.rlt2_group_create([a.ctx, b.ctx])
+        assert e.value.code == rlt2.RLT2_E_INVAL
+    finally:
+        a.close()
+        b.close()
