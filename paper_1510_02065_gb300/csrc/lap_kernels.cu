@@ -87,28 +87,50 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
     const int kk = (int)fdiv(rem, nd.fm), nn = (int)rem - kk * m;
     const int i = (int)fdiv(ij, nd.fN), j = (int)ij - i * N;
     const int k = kk + (kk >= i), nl = nn + (nn >= j);
-    const int lo = min(i, k), hi = max(i, k);
+    // Rows are the facilities e not in {i,k}, ascending; with a < c the tile's
+    // two facilities (at locations la, lc), the rows fall in three ranges whose
+    // classes are (e,a,c), (a,e,c), (a,c,e).  Within a range the member rank is
+    // fixed and the class index tau = C(z,3) + C(y,2) + x grows by 1, e, C(e,2)
+    // from one row to the next, so row addresses advance without division.
+    const bool ik = i < k;
+    const int a = ik ? i : k, c = ik ? k : i, la = ik ? j : nl, lc = ik ? nl : j;
+    const int R0 = ik ? 3 : 5, R1 = ik ? 1 : 4, R2 = ik ? 0 : 2;
+    const long long N3 = (long long)N * N * N;
+    const int N2 = N * N;
+    const int C3c = c * (c - 1) * (c - 2) / 6, C2c = c * (c - 1) / 2, C2a = a * (a - 1) / 2;
     const int *T = nd.p.T;
-    for (int r = 0; r < n; ++r) {
-        int e = r + (r >= lo);
-        e += (e >= hi);
-        const SymRow sr = sym_row(N, i, j, k, nl, e);
-        if (lane == 0) uRow[r] = sr.rank;  // parked until the conversion below
+    bool valid[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const int f = lane + 32 * s;
-            if (f < N && f != j && f != nl) cp_async4(buf + r * W + f, T + sr.base + (long long)f * sr.stride);
-        }
+    for (int s = 0; s < NS; ++s) {
+        const int f = lane + 32 * s;
+        valid[s] = f < N && f != j && f != nl;
+    }
+    int r = 0;
+    long long base = (long long)(C3c + C2a) * N3 + (long long)la * N + lc;        // e = 0: (e, a, c)
+    for (int e = 0; e < a; ++e, ++r, base += N3) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if (valid[s]) cp_async4(buf + r * W + lane + 32 * s, T + base + (long long)(lane + 32 * s) * N2);
+    }
+    base = (long long)(C3c + (a + 1) * a / 2 + a) * N3 + (long long)la * N2 + lc;  // e = a + 1: (a, e, c)
+    for (int e = a + 1; e < c; base += (long long)e * N3, ++e, ++r) {  // step C(e+1,2) - C(e,2) = e
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if (valid[s]) cp_async4(buf + r * W + lane + 32 * s, T + base + (long long)(lane + 32 * s) * N);
+    }
+    base = (long long)((c + 1) * c * (c - 1) / 6 + C2c + a) * N3 + (long long)la * N2 + (long long)lc * N;
+    for (int e = c + 1; e < N; base += (long long)(e * (e - 1) / 2) * N3, ++e, ++r) {  // (a, c, e); step C(e,2)
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if (valid[s]) cp_async4(buf + r * W + lane + 32 * s, T + base + lane + 32 * s);
     }
     cp_async_wait_all();
     __syncwarp();
-    for (int r = 0; r < n; ++r) {
-        const int rank = uRow[r];
+    for (int rr = 0; rr < n; ++rr) {
+        const int rank = rr < a ? R0 : rr < c - 1 ? R1 : R2;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const int f = lane + 32 * s;
-            if (f < N && f != j && f != nl) buf[r * W + f] = sym_member(buf[r * W + f], rank);
-        }
+        for (int s = 0; s < NS; ++s)
+            if (valid[s]) buf[rr * W + lane + 32 * s] = sym_member(buf[rr * W + lane + 32 * s], rank);
     }
     __syncwarp();
     int rowOf[NS], uM[NS], v[NS];
