@@ -401,14 +401,14 @@ __device__ __forceinline__ long long lap_value(int width, int dead0, int dead1, 
 template <int NS>
 __device__ __forceinline__ void scatter_rows(int n, int width, int dead0, int dead1,
                                              const int (&rowOf)[NS], const int (&uM)[NS],
-                                             int *uRow, int *colOf)
+                                             int *uRow, int *colOf, int ustride = 1)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
         const int c = lane + 32 * k;
         if (c < width && c != dead0 && c != dead1 && rowOf[k] >= 0 && rowOf[k] < n) {
-            uRow[rowOf[k]] = uM[k];
+            uRow[rowOf[k] * ustride] = uM[k];
             if (colOf) colOf[rowOf[k]] = c;
         }
     }

@@ -16,7 +16,6 @@
 
 namespace rlt2 {
 
-constexpr int kDlapWarps = 4;
 constexpr int kClapWarps = 4;
 constexpr int kXlapWarps = 4;
 constexpr int kBatchWarps = 4;
@@ -29,8 +28,8 @@ constexpr int kBatchWarps = 4;
 // status; the copy in flight has landed or been waited for, bounded).
 template <int NS, bool PACK>
 __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *buf, uint64_t *bar,
-                                          unsigned &parity, int *uRow, int lane, unsigned &steps,
-                                          unsigned &relax, DevStatus *status)
+                                          unsigned &parity, int lane, unsigned &steps, unsigned &relax,
+                                          DevStatus *status)
 {
     const int N = nd.N, W = nd.W, n = N - 2, m = N - 1, TS = nd.TS;
     if (lane == 0) {
@@ -54,11 +53,12 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
     int rowOf[NS], uM[NS], v[NS];
     if (!warp_hungarian<NS, PACK>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
         atomicOr(&status->err, kDevInternal);
-    scatter_rows<NS>(n, N, j, nl, rowOf, uM, uRow, nullptr);
+    // u of every row goes to the row's column j, which holds no coefficient
+    scatter_rows<NS>(n, N, j, nl, rowOf, uM, buf + j, nullptr, W);
     __syncwarp();
     int *gz = nd.p.z + (size_t)t * TS;
     for (int r = 0; r < n; ++r) {
-        const int ur = uRow[r];
+        const int ur = buf[r * W + j];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int c = lane + 32 * s;
@@ -67,6 +67,9 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
     }
     const long long S = lap_value<NS>(N, j, nl, uM, v);
     if (lane == 0) nd.p.yS[t] = (int)S;
+    // the generic writes of column j above precede the next tile's bulk copy
+    // into this buffer (async proxy)
+    fence_proxy_async_smem();
     __syncwarp();
     return true;
 }
@@ -77,9 +80,8 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
 // duals (u of every row, v of every location column) go to du instead of a
 // residual tile.
 template <int NS, bool PACK>
-__device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, int *buf, int *uRow,
-                                              int lane, unsigned &steps, unsigned &relax,
-                                              DevStatus *status)
+__device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, int *buf, int lane,
+                                              unsigned &steps, unsigned &relax, DevStatus *status)
 {
     const int N = nd.N, W = nd.W, n = N - 2, m = N - 1;
     const unsigned ij = fdiv(t, nd.fmm);
@@ -136,10 +138,10 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
     int rowOf[NS], uM[NS], v[NS];
     if (!warp_hungarian<NS, PACK>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
         atomicOr(&status->err, kDevInternal);
-    scatter_rows<NS>(n, N, j, nl, rowOf, uM, uRow, nullptr);
+    scatter_rows<NS>(n, N, j, nl, rowOf, uM, buf + j, nullptr, W);  // u to the free column j
     __syncwarp();
     int *du = nd.p.du + (size_t)t * nd.DS;
-    for (int r = lane; r < n; r += 32) du[r] = uRow[r];
+    for (int r = lane; r < n; r += 32) du[r] = buf[r * W + j];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int f = lane + 32 * s;
@@ -151,22 +153,23 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
     return true;
 }
 
-// One tile buffer per warp; a warp takes group-wide tile indices from a global
-// counter, finds the tile's instance and solves the tile's LAP.  Tiles of one
-// instance are consecutive in the group-wide order, so the instance found for
-// the previous tile is tried first.  ONE (a group of one instance): the
-// instance is the kernel parameter g.first, read from parameter space, and the
-// stopping rule is checked once.
-template <int NS, bool PACK, bool ONE, bool SYM>
-__global__ void __launch_bounds__(kDlapWarps * 32, 16) dlap_kernel(Group g)
+// One tile buffer per warp (and one mbarrier: WARPS * (TS * 4 + 8) bytes of
+// shared memory per CTA of WARPS warps); a warp takes group-wide tile indices
+// from a global counter, finds the tile's instance and solves the tile's LAP.
+// Tiles of one instance are consecutive in the group-wide order, so the
+// instance found for the previous tile is tried first.  ONE (a group of one
+// instance): the instance is the kernel parameter g.first, read from
+// parameter space, and the stopping rule is checked once.  Every CTA size
+// caps registers at 32 per thread (64 warps per SM).
+template <int NS, bool PACK, bool ONE, bool SYM, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 64 / WARPS) dlap_kernel(Group g)
 {
     if (ONE && *g.first.p.stop) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * g.maxTS;
-    unsigned char *tail = smem + (size_t)kDlapWarps * g.maxTS * 4;
+    unsigned char *tail = smem + (size_t)WARPS * g.maxTS * 4;
     uint64_t *bar = reinterpret_cast<uint64_t *>(tail) + warp;
-    int *uRow = reinterpret_cast<int *>(tail + kDlapWarps * 8) + warp * 64;
 
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -185,23 +188,22 @@ __global__ void __launch_bounds__(kDlapWarps * 32, 16) dlap_kernel(Group g)
         if (T >= ntiles) break;
         bool ok;
         if constexpr (SYM && ONE) {
-            ok = dlap_tile_sym<NS, PACK>(g.first, T, buf, uRow, lane, steps, relax, g.status);
+            ok = dlap_tile_sym<NS, PACK>(g.first, T, buf, lane, steps, relax, g.status);
         } else if constexpr (SYM) {
             if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
                 b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
             const NodeDesc &nd = g.nodes[b];
             if (*nd.p.stop) continue;
-            ok = dlap_tile_sym<NS, PACK>(nd, T - (unsigned)nd.tile_base, buf, uRow, lane, steps, relax,
-                                         g.status);
+            ok = dlap_tile_sym<NS, PACK>(nd, T - (unsigned)nd.tile_base, buf, lane, steps, relax, g.status);
         } else if constexpr (ONE) {
-            ok = dlap_tile<NS, PACK>(g.first, T, buf, bar, parity, uRow, lane, steps, relax, g.status);
+            ok = dlap_tile<NS, PACK>(g.first, T, buf, bar, parity, lane, steps, relax, g.status);
         } else {
             if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
                 b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
             const NodeDesc &nd = g.nodes[b];
             if (*nd.p.stop) continue;
-            ok = dlap_tile<NS, PACK>(nd, T - (unsigned)nd.tile_base, buf, bar, parity, uRow, lane, steps,
-                                     relax, g.status);
+            ok = dlap_tile<NS, PACK>(nd, T - (unsigned)nd.tile_base, buf, bar, parity, lane, steps, relax,
+                                     g.status);
         }
         if (!ok) return;
         ++laps;
@@ -384,26 +386,53 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
 
 // ---------------------------------------------------------------- launchers
 
-template <int NS, bool PACK, bool ONE, bool SYM>
-static cudaError_t dlap_go(const Group &g, int sm_count, cudaStream_t s)
+// Resident warps per SM of the D->C kernel with CTAs of WARPS warps.
+template <int NS, bool PACK, bool ONE, bool SYM, int WARPS>
+static cudaError_t dlap_fit(const Group &g, int &warps_per_sm)
 {
-    const size_t smem = (size_t)kDlapWarps * ((size_t)g.maxTS * 4 + 8 + 256);
-    auto k = dlap_kernel<NS, PACK, ONE, SYM>;
+    const size_t smem = (size_t)WARPS * ((size_t)g.maxTS * 4 + 8);
+    auto k = dlap_kernel<NS, PACK, ONE, SYM, WARPS>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDlapWarps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WARPS * 32, smem);
+    warps_per_sm = per_sm * WARPS;
+    return e;
+}
+
+template <int NS, bool PACK, bool ONE, bool SYM, int WARPS>
+static cudaError_t dlap_run(const Group &g, int sm_count, cudaStream_t s)
+{
+    const size_t smem = (size_t)WARPS * ((size_t)g.maxTS * 4 + 8);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dlap_kernel<NS, PACK, ONE, SYM, WARPS>,
+                                                                  WARPS * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)per_sm * sm_count;
-    const long long need = (g.tiles + kDlapWarps - 1) / kDlapWarps;
+    const long long need = (g.tiles + WARPS - 1) / WARPS;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k<<<(unsigned)grid, kDlapWarps * 32, smem, s>>>(g);
+    dlap_kernel<NS, PACK, ONE, SYM, WARPS><<<(unsigned)grid, WARPS * 32, smem, s>>>(g);
     return cudaGetLastError();
 }
 
-// The work counter is reset by the fused pass over D, which precedes this kernel.
+// CTA size: the one of 4, 16 or 32 warps that keeps the most warps resident
+// (shared memory decides: at N = 30 two CTAs of 32 warps fit where fourteen
+// of 4 do), the smaller on a tie.
+template <int NS, bool PACK, bool ONE, bool SYM>
+static cudaError_t dlap_go(const Group &g, int sm_count, cudaStream_t s)
+{
+    int w4 = 0, w16 = 0, w32 = 0;
+    cudaError_t e;
+    if ((e = dlap_fit<NS, PACK, ONE, SYM, 4>(g, w4)) != cudaSuccess) return e;
+    if ((e = dlap_fit<NS, PACK, ONE, SYM, 16>(g, w16)) != cudaSuccess) return e;
+    if ((e = dlap_fit<NS, PACK, ONE, SYM, 32>(g, w32)) != cudaSuccess) return e;
+    if (w32 > w4 && w32 > w16) return dlap_run<NS, PACK, ONE, SYM, 32>(g, sm_count, s);
+    if (w16 > w4) return dlap_run<NS, PACK, ONE, SYM, 16>(g, sm_count, s);
+    return dlap_run<NS, PACK, ONE, SYM, 4>(g, sm_count, s);
+}
+
 template <bool ONE, bool SYM>
 static cudaError_t dlap_pick(const Group &g, int sm_count, cudaStream_t s)
 {
