@@ -264,7 +264,7 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, bool sym, long long U, int
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return RLT2_E_CUDA;
         c->own_stream = true;
     }
-    const int JC = p1_chunk(N);
+    const int JC = p1_chunk(N, with_d && sym);
     const std::vector<int4> tri = triple_table(N);
     Arena a;
     const NodeOffsets no = plan_node(a, N, with_d, sym, c->opts.max_iters);
@@ -726,7 +726,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
         maxN = std::max(maxN, c->node.N);
         pack = pack && c->g.pack;
     }
-    const int JC = p1_chunk(maxN);
+    const int JC = p1_chunk(maxN, ctxs[0]->g.sym);
     const std::vector<int4> tri = triple_table(maxN);
     Arena a;
     const size_t o_nodes = a.take((size_t)count * sizeof(NodeDesc));
@@ -896,7 +896,8 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
         pack = pack && 3 * U < (1LL << 25);
         maxN = std::max(maxN, I.Np);
     }
-    const int JC = p1_chunk(maxN);
+    if (o.store != RLT2_STORE_TILES && o.store != RLT2_STORE_CLASSES) return RLT2_E_INVAL;
+    const int JC = p1_chunk(maxN, o.store == RLT2_STORE_CLASSES);
     const int hist_cap = std::max(iters, 1);
 
     // one allocation for the whole group

@@ -166,11 +166,11 @@ struct Group {
     NodeDesc first;         // copy of nodes[0]: kernels of a group of one read it as a parameter
 };
 
-int p1_chunk(int N);                   // locations per CTA of the fused pass over D
+int p1_chunk(int N, bool sym);         // locations per CTA of the fused pass over D
 // Encode nd.zmap for the fused pass with location chunk JC (sets zmap_ok;
 // false leaves the pieces to per-piece copies).  nd.p.z and the geometry must be set.
 bool encode_zmap(NodeDesc &nd, int JC);
-size_t p1_smem_bytes(int N, int JC);   // its dynamic shared memory
+size_t p1_smem_bytes(int N, int JC, bool sym);  // its dynamic shared memory
 
 // Initialise instance `node` of the group (index b) from device copies of its
 // F, D and linear costs (Blin may be null).

@@ -57,12 +57,14 @@ __device__ __forceinline__ int share(int x, const FastDiv &fm, int t)
 // zmap, and a conflict-free 16-byte read of pieces (qq, nn) across lanes qq.
 struct P1Layout {
     int S13, S25, P46, H6p;
-    int A1, A3, A2, A5, A4, A6, H1, H3, H2, H5, H4, H6, total;
+    int A1, A3, A2, A5, A4, A6, H1, H3, H2, H5, H4, H6;
+    int HU;     // class-sum store: u of each H entry's tile row, same offsets from HU as from H1
+    int total;
 };
 
 __host__ __device__ inline int up4(int x) { return (x + 3) & ~3; }
 
-__host__ __device__ inline P1Layout p1_layout(int N, int W, int JC)
+__host__ __device__ inline P1Layout p1_layout(int N, int W, int JC, bool sym)
 {
     P1Layout L;
     L.S13 = W;
@@ -83,11 +85,13 @@ __host__ __device__ inline P1Layout p1_layout(int N, int W, int JC)
     L.H5 = o; o += up4(JC * N);
     L.H4 = o; o += up4(N * N);
     L.H6 = o; o += up4(N * L.H6p);
+    L.HU = o;
+    if (sym) o += o - L.H1;
     L.total = o;
     return L;
 }
 
-size_t p1_smem_bytes(int N, int JC) { return (size_t)p1_layout(N, up4(N), JC).total * 4; }
+size_t p1_smem_bytes(int N, int JC, bool sym) { return (size_t)p1_layout(N, up4(N), JC, sym).total * 4; }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
@@ -135,12 +139,12 @@ bool encode_zmap(NodeDesc &nd, int JC)
     return true;
 }
 
-int p1_chunk(int N)
+int p1_chunk(int N, bool sym)
 {
 #ifdef RLT2_P1_JC
-    if (p1_smem_bytes(N, RLT2_P1_JC) <= 200 * 1024) return RLT2_P1_JC;  // build-time override
+    if (p1_smem_bytes(N, RLT2_P1_JC, sym) <= 200 * 1024) return RLT2_P1_JC;  // build-time override
 #endif
-    for (int jc : {4, 2}) if (p1_smem_bytes(N, jc) <= 110 * 1024) return jc;
+    for (int jc : {4, 2}) if (p1_smem_bytes(N, jc, sym) <= 112 * 1024) return jc;
     return 1;
 }
 
@@ -197,6 +201,52 @@ __device__ __forceinline__ void store_piece(int *dst, const int (&r)[JC])
     else *dst = r[0];
 }
 
+// Gather, for every member tile of the work unit, c' (yS) into its H slot
+// and, with the class-sum store, u of the member's row into the HU slot at the
+// same offset: one 4-byte cp.async each, all in flight with the bulk copies.
+template <int JC, bool SYM>
+__device__ __forceinline__ void p1_gather_c(const P1Layout &L, int N, int i, int k, int pp, int j0, int jc,
+                                            const FastDiv &fN, const int *yS, const int *du, int DS, int *sm)
+{
+    const int NN = N * N;
+    for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
+        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
+        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
+        if (jj >= jc || x == j) continue;
+        int t, row;
+        full_row(q, N, i, k, pp, j, x, t, row);
+        const int h = (q == 0 ? L.H1 : q == 1 ? L.H3 : q == 2 ? L.H2 : L.H5) + jj * N + x;
+        cp_async4(sm + h, yS + t);
+        if constexpr (SYM) cp_async4(sm + L.HU + (h - L.H1), du + (size_t)t * DS + row);
+    }
+    for (int e = threadIdx.x; e < 2 * NN; e += kP1Threads) {
+        const int kind = e >= NN, r2 = e - kind * NN;
+        const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
+        if (l == a) continue;
+        const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
+        const int h = (kind ? L.H6 + a * L.H6p : L.H4 + a * N) + l;
+        cp_async4(sm + h, yS + t);
+        if constexpr (SYM) cp_async4(sm + L.HU + (h - L.H1), du + (size_t)t * DS + i);
+    }
+}
+
+// Turn every H slot into the share of its c' for the member's row (kinds 1, 3:
+// row p - 2 of the tile; kinds 2, 5: row k - 1; kinds 4, 6: row i), minus u of
+// that row with the class-sum store.  Slots never gathered hold garbage and
+// stay unused.
+template <bool SYM>
+__device__ __forceinline__ void p1_shares(const P1Layout &L, int N, int i, int k, int pp, const FastDiv &fn,
+                                          int *sm)
+{
+    const int end = L.HU;
+    for (int h = L.H1 + threadIdx.x; h < end; h += kP1Threads) {
+        const int row = h < L.H2 ? pp - 2 : h < L.H4 ? k - 1 : i;
+        int val = share(sm[h], fn, row);
+        if constexpr (SYM) val -= sm[L.HU + (h - L.H1)];
+        sm[h] = val;
+    }
+}
+
 // One CTA per (instance, facility triple, location chunk) of the group; yS
 // holds c' (C plus the spread of B) per tile.  ONE (a group of one instance):
 // the instance is the kernel parameter g.first.
@@ -213,7 +263,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
     const FastDiv fN = nd.fN, fn = nd.fn;
     const int bid = blockIdx.x - nd.cta_base;
     extern __shared__ __align__(128) int sm[];
-    const P1Layout L = p1_layout(N, W, JC);
+    const P1Layout L = p1_layout(N, W, JC, false);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t TS = (size_t)(N - 2) * W;
     const int4 tr = g.triples[bid / nchunks];
@@ -266,23 +316,9 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
                            z + t * TS + (size_t)i * W + j0);
     }
 
-    // ---- shares while the copies fly: c' of the tile spread over its rows
-    for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
-        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
-        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
-        if (jj >= jc || x == j) continue;
-        int t, row;
-        full_row(q, N, i, k, pp, j, x, t, row);
-        const int hb = q == 0 ? L.H1 : q == 1 ? L.H3 : q == 2 ? L.H2 : L.H5;
-        sm[hb + jj * N + x] = share(yS[t], fn, row);
-    }
-    for (int e = threadIdx.x; e < 2 * NN; e += kP1Warps * 32) {
-        const int kind = e >= NN, r2 = e - kind * NN;
-        const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
-        if (l == a) continue;
-        const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
-        sm[(kind ? L.H6 + a * L.H6p : L.H4 + a * N) + l] = share(yS[t], fn, i);
-    }
+    // ---- c' of every member tile, gathered while the copies fly (4-byte
+    // asynchronous copies into the H arrays, turned into shares below)
+    p1_gather_c<JC, false>(L, N, i, k, pp, j0, jc, fN, yS, nullptr, 0, sm);
 
     asm volatile("cp.async.wait_all;" ::: "memory");
     if (__syncthreads_or(!mbar_wait(&bar, 0))) {
@@ -292,6 +328,8 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
         __syncthreads();
         return;
     }
+    p1_shares<false>(L, N, i, k, pp, fn, sm);
+    __syncthreads();
 
     // ---- split every class {(i,j),(k,nn),(p,qq)}, j in the chunk: one warp
     // per nn, lanes over qq, each lane the JC classes of its (nn, qq).  Their
@@ -381,7 +419,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_sym_kernel(const __grid_cons
     const FastDiv fN = nd.fN, fn = nd.fn;
     const int bid = blockIdx.x - nd.cta_base;
     extern __shared__ __align__(128) int sm[];
-    const P1Layout L = p1_layout(N, W, JC);
+    const P1Layout L = p1_layout(N, W, JC, true);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tri = bid / nchunks;
     const int4 tr = g.triples[tri];
@@ -431,23 +469,9 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_sym_kernel(const __grid_cons
                            du + (size_t)t * DS + U0 + j0);
     }
 
-    // ---- (share of c' - u) of every member tile at the member's row
-    for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
-        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
-        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
-        if (jj >= jc || x == j) continue;
-        int t, row;
-        full_row(q, N, i, k, pp, j, x, t, row);
-        const int hb = q == 0 ? L.H1 : q == 1 ? L.H3 : q == 2 ? L.H2 : L.H5;
-        sm[hb + jj * N + x] = share(yS[t], fn, row) - du[(size_t)t * DS + row];
-    }
-    for (int e = threadIdx.x; e < 2 * NN; e += kP1Threads) {
-        const int kind = e >= NN, r2 = e - kind * NN;
-        const int a = (int)fdiv((unsigned)r2, fN), l = r2 - a * N;
-        if (l == a) continue;
-        const int t = kind ? tidx_n(N, pp, a, k, l) : tidx_n(N, k, a, pp, l);
-        sm[(kind ? L.H6 + a * L.H6p : L.H4 + a * N) + l] = share(yS[t], fn, i) - du[(size_t)t * DS + i];
-    }
+    // ---- c' and u of every member tile at the member's row, gathered while
+    // the copies fly; H <- share of c' - u below
+    p1_gather_c<JC, true>(L, N, i, k, pp, j0, jc, fN, yS, du, DS, sm);
 
     asm volatile("cp.async.wait_all;" ::: "memory");
     if (__syncthreads_or(!mbar_wait(&bar, 0))) {
@@ -456,6 +480,8 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_sym_kernel(const __grid_cons
         __syncthreads();
         return;
     }
+    p1_shares<true>(L, N, i, k, pp, fn, sm);
+    __syncthreads();
 
     // ---- new class sums: warp per location n, lanes over q, each lane the
     // chunk's classes of its (n, q)
@@ -592,7 +618,7 @@ cudaError_t launch_init(const NodeDesc &nd, const int32_t *F, const int32_t *D,
 template <int JC>
 static cudaError_t p1_go(const Group &g, cudaStream_t s)
 {
-    const size_t smem = p1_smem_bytes(g.maxN, JC);
+    const size_t smem = p1_smem_bytes(g.maxN, JC, g.sym);
     auto k = g.sym ? (g.B == 1 ? p1_sym_kernel<JC, true> : p1_sym_kernel<JC, false>)
                    : (g.B == 1 ? p1_kernel<JC, true> : p1_kernel<JC, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
