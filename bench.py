@@ -32,8 +32,26 @@ OPS_PER_RELAXATION = 9   # textbook int ops of one relaxation
 # DRAM bytes per launch of the D->C kernel on the 30-facility workload, from one
 # ncu capture (profiles/dram_dlap_p1_clustered_n30.md); reported only while the
 # kernel's sources hash to the captured version.
-DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2713586688 + 2651447040,
-                "sources_sha1": "6423efcfc8cdba8cee046210275d6e8083e704da"}
+# DRAM bytes per launch from one ncu capture of the headline workload (tile
+# store), valid while the kernel's sources hash to the captured version
+DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2714539520 + 2652155392,
+                "files": ("lap_kernels.cu", "device.cuh", "kernels.h"),
+                "sources_sha1": "76c11698ddcf23be8e1c476821c8e7dd164d4a5f"}
+P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2741079296 + 2655531008,
+              "files": ("sweep_kernels.cu", "device.cuh", "kernels.h"),
+              "sources_sha1": "53452b72dd6ae9663eb74d4361faa2ff2b4cc69f"}
+
+
+def captured_traffic(rec, workload, store):
+    """rec["bytes"] if the workload and the kernel sources match the capture."""
+    if workload != rec["workload"] or store != "tiles":
+        return None
+    import hashlib
+    h = hashlib.sha1()
+    for f in rec["files"]:
+        with open(os.path.join(ROOT, "paper_1510_02065_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest() == rec["sources_sha1"] else None
 
 
 def parse():
@@ -373,18 +391,20 @@ def main():
     n_tiles = N * N * (N - 1) ** 2
     m = N - 2
     z_bytes = n_tiles * m * m * 4
-    dlap_hbm_gbs = 2 * z_bytes / (t_dlap / 1e3) / 1e9
-    p1_bytes = 2 * z_bytes + n_tiles * 4 + N * N * 4
+    if args.store == "tiles":
+        # D read and written once by each kernel (+ C and B read by the fused pass)
+        dlap_bytes = 2 * z_bytes
+        p1_bytes = 2 * z_bytes + n_tiles * 4 + N * N * 4
+    else:
+        # class sums (one per class) and per-tile duals (u: N-2, v: N-2 coefficients)
+        classes = N * (N - 1) * (N - 2) // 6 * N * (N - 1) * (N - 2)
+        duals = n_tiles * 2 * m * 4
+        dlap_bytes = classes * 4 + duals                      # class sums read, duals written
+        p1_bytes = 2 * classes * 4 + duals + n_tiles * 4 + N * N * 4
+    dlap_hbm_gbs = dlap_bytes / (t_dlap / 1e3) / 1e9
     p1_gbs = p1_bytes / (t_p1 / 1e3) / 1e9
-    traffic = None
-    if args.workload == DLAP_TRAFFIC["workload"] and args.store == "tiles":
-        import hashlib
-        h = hashlib.sha1()
-        for f in ("lap_kernels.cu", "device.cuh", "kernels.h"):
-            with open(os.path.join(ROOT, "paper_1510_02065_gb300", "csrc", f), "rb") as fh:
-                h.update(fh.read())
-        if h.hexdigest() == DLAP_TRAFFIC["sources_sha1"]:
-            traffic = DLAP_TRAFFIC["bytes"]
+    traffic = captured_traffic(DLAP_TRAFFIC, args.workload, args.store)
+    p1_traffic = captured_traffic(P1_TRAFFIC, args.workload, args.store)
 
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": K,
@@ -392,7 +412,7 @@ def main():
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "seed": 0, "tiles": n_tiles, "store": args.store,
                    "laps_per_iter": int(round(laps_per_pass)), "z_bytes": z_bytes,
-                   "l2": "inputs larger than L2 (D store %.2f GB)" % (z_bytes / 1e9),
+                   "l2": "inputs larger than L2 (D %.2f GB of coefficients)" % (z_bytes / 1e9),
                    "parallelism": "replicas x%d" % world if world > 1 else "1 GPU"},
         "laps_per_s": world * laps_per_pass * K / (ms / 1000.0),
         "bound": {"LB": lb_exact, "iterations": iters},
@@ -409,6 +429,7 @@ def main():
         "p1_roofline": {"bound": "hbm", "kernel": "p1_kernel (spread + complementary D)",
                         "achieved": p1_gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                         "frac": p1_gbs / float(peaks["hbm_gbs"]), "bytes_per_launch": p1_bytes,
+                        "traffic": p1_traffic,
                         "peak_kind": peaks_kind},
         "gpu_launches": 5 * K,
         "clocks": clk,
