@@ -149,7 +149,7 @@ def batch_measure(rlt2, instances, torch, nodes_count, iters):
     nodes = instances.subproblem_nodes(25, nodes_count)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lbs, dev_ms = rlt2.rlt2_batch_bound(F, D, nodes, iters)
+    lbs, dev_ms, lanes = rlt2.rlt2_batch_bound(F, D, nodes, iters, return_lanes=True)
     t_batch = time.perf_counter() - t0
     s = torch.cuda.Stream()
     plain = []
@@ -167,6 +167,7 @@ def batch_measure(rlt2, instances, torch, nodes_count, iters):
             "speedup": t_plain / t_batch, "identical_bounds": list(plain) == [int(x) for x in lbs],
             "nodes": nodes_count, "iters": iters, "residual_N": [min(sizes), max(sizes)],
             "batched_device_ms": dev_ms, "graph_launches": 1,
+            "autotuned_lanes_per_lap_small_nodes": lanes,
             "config": "clustered N=25 seed 0, node s fixes 1-15 pairs from default_rng(1000+s)"}
 
 

@@ -75,6 +75,10 @@ typedef struct {
                              created for (and owned by) the context              */
     int store;            /* how D is kept: RLT2_STORE_TILES (default) or
                              RLT2_STORE_CLASSES; results are identical          */
+    int lanes;            /* lanes per D->C LAP of instances with N <= 16: 32 (a
+                             warp each) or 16 (two per warp); 0 (default) =
+                             16 for a context or group, chosen by timing for
+                             rlt2_batch_bound; results are identical           */
 } rlt2_opts;
 
 /*
@@ -264,13 +268,22 @@ int rlt2_subproblem(const int32_t *F, const int32_t *D, int N, int k, const int3
  *   lb_out    host, B int64: each node's LB (lb_const included)
  *   ms_out    (may be NULL) milliseconds of device work from the first
  *             initialisation to the last pass (CUDA events)
- *   opts      stream (NULL: a stream created for the call); rlt1_only must be 0
+ *   opts      stream (NULL: a stream created for the call), store, lanes;
+ *             rlt1_only must be 0
+ *   lanes_out (may be NULL) lanes per D->C LAP used for the nodes with
+ *             N - k <= 16 (32 when there are none)
+ * Autotuning (opts->lanes == 0, iters >= 3): the first pass solves the small
+ * nodes' D->C LAPs on whole warps, the second on half-warps, and the form with
+ * the lower time per relaxation of the Hungarian runs the remaining passes
+ * (the two forms give identical results).  Nodes of N' <= 16 are placed first
+ * internally; lb_out keeps the caller's order.
  * One device allocation holds every node's state (about 4 B * N'^2 (N'-1)^2
  * (N'-2) * round_up(N',4) each) and is freed before returning; synchronises.
  * Errors: as rlt2_create, per node.
  */
 int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node *nodes, int B,
-                     int iters, const rlt2_opts *opts, int64_t *lb_out, double *ms_out);
+                     int iters, const rlt2_opts *opts, int64_t *lb_out, double *ms_out,
+                     int *lanes_out);
 
 /*
  * Batched linear assignment with the library's Hungarian kernel (the LAP of

@@ -61,6 +61,10 @@ int check_instance(const int32_t *F, const int32_t *D, int N, const int32_t *B_l
 
 long long n_triples(int N) { return (long long)N * (N - 1) * (N - 2) / 6; }
 
+// Largest instance whose D->C LAPs (width N <= 16 location columns) can run
+// on half-warps.
+constexpr int kSmallN = 16;
+
 // Facility triples i < k < p ordered by p, then k, then i: the first C(N,3)
 // of the table for any larger N are exactly the triples of N.
 std::vector<int4> triple_table(int N)
@@ -270,7 +274,7 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, bool sym, long long U, int
     const NodeOffsets no = plan_node(a, N, with_d, sym, c->opts.max_iters);
     const size_t o_node = a.take(sizeof(NodeDesc));
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
-    const size_t o_cnt = a.take(4);
+    const size_t o_cnt = a.take(8);
     const size_t o_st = a.take(sizeof(DevStatus));
     const size_t o_stage = a.take((size_t)3 * N * N * 4);
     cudaError_t e = cudaMalloc((void **)&c->mem, a.used);
@@ -300,6 +304,9 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, bool sym, long long U, int
     g.pack = 3 * U < (1LL << 25);
     g.rlt1_only = !with_d;
     g.sym = with_d && sym;
+    // instances with N <= 16: D->C LAPs on half-warps unless opts ask for whole warps
+    g.small_tiles = with_d && N <= kSmallN && c->opts.lanes != 32 ? (int)nd.tiles : 0;
+    g.smallTS = nd.TS;
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
     g.triples = reinterpret_cast<const int4 *>(base + o_tri);
@@ -311,7 +318,7 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, bool sym, long long U, int
         e = cudaMemcpyAsync(base + o_tri, tri.data(), tri.size() * sizeof(int4), cudaMemcpyHostToDevice,
                             c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.status, 0, sizeof(DevStatus), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g.counter, 0, 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.counter, 0, 8, c->stream);
     // the table must outlive its asynchronous copy
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_code(e);
@@ -375,7 +382,8 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
     rlt2_ctx *c = new_ctx(opts);
     if (!c) return RLT2_E_OOM;
     int32_t *stage = nullptr;
-    if (c->opts.store != RLT2_STORE_TILES && c->opts.store != RLT2_STORE_CLASSES) {
+    if ((c->opts.store != RLT2_STORE_TILES && c->opts.store != RLT2_STORE_CLASSES) ||
+        (c->opts.lanes != 0 && c->opts.lanes != 16 && c->opts.lanes != 32)) {
         free_ctx(c);
         return RLT2_E_INVAL;
     }
@@ -731,7 +739,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     Arena a;
     const size_t o_nodes = a.take((size_t)count * sizeof(NodeDesc));
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
-    const size_t o_cnt = a.take(4);
+    const size_t o_cnt = a.take(8);
     const size_t o_st = a.take(sizeof(DevStatus));
     cudaError_t e = cudaMalloc((void **)&gr->mem, a.used);
     if (e != cudaSuccess) {
@@ -739,12 +747,21 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
         gr->mem = nullptr;
         return fail(cuda_code(e));
     }
+    // instances with N <= 16 first: their tiles form the half-warp range of D->C
+    bool halves = !ctxs[0]->g.rlt1_only;
+    for (rlt2_ctx *c : gr->ctxs) halves = halves && c->opts.lanes != 32;
+    std::vector<int> order(count);
+    for (int b = 0; b < count; b++) order[b] = b;
+    if (halves)
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return (gr->ctxs[x]->node.N <= kSmallN) > (gr->ctxs[y]->node.N <= kSmallN);
+        });
     std::vector<NodeDesc> hn(count);
-    long long tiles = 0;
-    int ctas = 0, probs = 0, maxTS = 0;
+    long long tiles = 0, small_tiles = 0;
+    int ctas = 0, probs = 0, maxTS = 0, smallTS = 4;
     for (int b = 0; b < count; b++) {
         NodeDesc &nd = hn[b];
-        nd = gr->ctxs[b]->node;            // the context's own state, shared
+        nd = gr->ctxs[order[b]]->node;     // the context's own state, shared
         fill_node(nd, nd.N, JC);           // the group's location chunk
         encode_zmap(nd, JC);
         nd.tile_base = tiles;
@@ -754,9 +771,15 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
         ctas += (int)(n_triples(nd.N) * nd.nchunks);
         probs += nd.N * nd.N;
         maxTS = std::max(maxTS, nd.TS);
+        if (halves && nd.N <= kSmallN) {
+            small_tiles += nd.tiles;
+            smallTS = std::max(smallTS, nd.TS);
+        }
     }
     if (tiles >= (1LL << 31)) return fail(RLT2_E_INVAL);
     Group &g = gr->g;
+    g.small_tiles = (int)small_tiles;
+    g.smallTS = smallTS;
     g.nodes = reinterpret_cast<const NodeDesc *>(gr->mem + o_nodes);
     g.B = count;
     g.tiles = tiles;
@@ -784,7 +807,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
         e = cudaMemcpyAsync(gr->mem + o_tri, tri.data(), tri.size() * sizeof(int4),
                             cudaMemcpyHostToDevice, gr->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.status, 0, sizeof(DevStatus), gr->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g.counter, 0, 4, gr->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.counter, 0, 8, gr->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(gr->stream);  // host copies are on the stack
     if (e != cudaSuccess) return fail(cuda_code(e));
     *out = gr;
@@ -855,7 +878,7 @@ int rlt2_subproblem(const int32_t *F, const int32_t *D, int N, int k, const int3
 }
 
 int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node *nodes, int B,
-                     int iters, const rlt2_opts *opts, int64_t *lb_out, double *ms_out)
+                     int iters, const rlt2_opts *opts, int64_t *lb_out, double *ms_out, int *lanes_out)
 {
     if (!F || !D || N < RLT2_MIN_N || N > RLT2_MAX_N || !nodes || B < 1 || iters < 0 || !lb_out)
         return RLT2_E_INVAL;
@@ -863,6 +886,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     if (opts) o = *opts;
     else rlt2_default_opts(&o);
     if (o.rlt1_only) return RLT2_E_INVAL;  // the batch runs the full RLT2 dual ascent
+    if (o.lanes != 0 && o.lanes != 16 && o.lanes != 32) return RLT2_E_INVAL;
     int dev = 0, sm_count = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -909,7 +933,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     const std::vector<int4> tri = triple_table(maxN);
     const size_t o_nodes = a.take((size_t)B * sizeof(NodeDesc));
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
-    const size_t o_cnt = a.take(4);
+    const size_t o_cnt = a.take(8);
     const size_t o_st = a.take(sizeof(DevStatus));
     const size_t o_stage = a.take((size_t)3 * maxN * maxN * 4 * B);
     // stream capture needs a stream other than the legacy default one
@@ -936,12 +960,23 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
         if (own) cudaStreamDestroy(own);
         return RLT2_E_INVAL;
     }
-    int ctas = 0, probs = 0, maxTS = 0;
+    // nodes with N' <= 16 first: their tiles form the half-warp range of D->C
+    std::vector<int> order(B);
+    for (int b = 0; b < B; b++) order[b] = b;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return (in[x].Np <= kSmallN) > (in[y].Np <= kSmallN); });
+    int ctas = 0, probs = 0, maxTS = 0, smallTS = 4;
+    long long small_tiles = 0;
     for (int b = 0; b < B; b++) {
         NodeDesc &nd = hn[b];
-        fill_node(nd, in[b].Np, JC);
-        nd.p = node_state(base, no[b], hist_cap, o);
+        const int ob = order[b];
+        fill_node(nd, in[ob].Np, JC);
+        nd.p = node_state(base, no[ob], hist_cap, o);
         encode_zmap(nd, JC);
+        if (nd.N <= kSmallN) {
+            small_tiles += nd.tiles;
+            smallTS = std::max(smallTS, nd.TS);
+        }
         nd.tile_base = tiles;
         nd.cta_base = ctas;
         nd.prob_base = probs;
@@ -961,12 +996,20 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     g.pack = pack;
     g.rlt1_only = false;
     g.sym = sym;
+    g.small_tiles = 0;
+    g.smallTS = smallTS;
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
     g.triples = reinterpret_cast<const int4 *>(base + o_tri);
     g.first = hn[0];
+    // D->C of the small nodes: whole warps (g) or half-warps (g16); opts.lanes
+    // forces one, 0 lets the first passes decide (below)
+    Group g16 = g;
+    g16.small_tiles = (int)small_tiles;
+    int lanes = small_tiles == 0 ? 32 : o.lanes;
 
     cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaEvent_t tev[10] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int rc = RLT2_OK;
@@ -979,22 +1022,49 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
                                  cudaMemcpyHostToDevice, s)) != cudaSuccess)
             break;
         if ((e = cudaMemsetAsync(g.status, 0, sizeof(DevStatus), s)) != cudaSuccess) break;
-        if ((e = cudaMemsetAsync(g.counter, 0, 4, s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(g.counter, 0, 8, s)) != cudaSuccess) break;
         if ((e = cudaEventRecord(t0, s)) != cudaSuccess) break;
         int32_t *stage = reinterpret_cast<int32_t *>(base + o_stage);
-        for (int b = 0; b < B && e == cudaSuccess; b++)
-            e = init_node(hn[b], in[b].F.data(), in[b].D.data(), in[b].B.data(), in[b].cst,
-                          stage + (size_t)b * 3 * maxN * maxN, s);
+        for (int b = 0; b < B && e == cudaSuccess; b++) {
+            const Inst &I = in[order[b]];
+            e = init_node(hn[b], I.F.data(), I.D.data(), I.B.data(), I.cst, stage + (size_t)b * 3 * maxN * maxN, s);
+        }
         if (e != cudaSuccess) break;
-        // all passes of all nodes: one captured graph, one launch
-        if (iters > 0) {
-            if ((e = capture_passes(g, sm_count, s, iters, &graph, &exec)) != cudaSuccess) break;
+        // Autotuning of the lanes per D->C LAP of the small nodes: the first
+        // two passes (real passes: both forms give identical results) run one
+        // with whole warps, one with half-warps; the D->C time per relaxation
+        // of the Hungarian decides the form of the remaining passes.
+        int done = 0;
+        if (lanes == 0 && iters >= 3) {
+            for (int k = 0; k < 10 && e == cudaSuccess; k++) e = cudaEventCreate(&tev[k]);
+            DevStatus st[3];
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&st[0], g.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = enqueue_pass(g, sm_count, s, tev);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&st[1], g.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = enqueue_pass(g16, sm_count, s, tev + 5);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&st[2], g.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) break;
+            float m32 = 0.f, m16 = 0.f;
+            if ((e = cudaEventElapsedTime(&m32, tev[1], tev[2])) != cudaSuccess) break;
+            if ((e = cudaEventElapsedTime(&m16, tev[6], tev[7])) != cudaSuccess) break;
+            const double r32 = (double)(st[1].drelax - st[0].drelax), r16 = (double)(st[2].drelax - st[1].drelax);
+            lanes = (r16 > 0 && r32 > 0 && m16 / r16 < m32 / r32) ? 16 : 32;
+            done = 2;
+        } else if (lanes == 0) {
+            lanes = 16;
+        }
+        const Group &gb = lanes == 16 ? g16 : g;
+        // all (remaining) passes of all nodes: one captured graph, one launch
+        if (iters > done) {
+            if ((e = capture_passes(gb, sm_count, s, iters - done, &graph, &exec)) != cudaSuccess) break;
             if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
         }
+        if (lanes_out) *lanes_out = small_tiles == 0 ? 32 : lanes;
         if ((e = cudaEventRecord(t1, s)) != cudaSuccess) break;
         rc = group_status(g, s);
         for (int b = 0; b < B && e == cudaSuccess; b++)
-            e = cudaMemcpyAsync(&lb_out[b], hn[b].p.LB, 8, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(&lb_out[order[b]], hn[b].p.LB, 8, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e == cudaSuccess && ms_out) {
             float ms = 0.f;
@@ -1008,6 +1078,8 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     if (graph) cudaGraphDestroy(graph);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
+    for (cudaEvent_t ev : tev)
+        if (ev) cudaEventDestroy(ev);
     cudaFree(base);
     if (own) cudaStreamDestroy(own);
     return rc;

@@ -218,6 +218,29 @@ __device__ __forceinline__ long long warp_sum64(long long x)
     return x;
 }
 
+// Lane segments: SEG = 32 (a warp per LAP) or 16 (two LAPs per warp, one per
+// half).  sl = lane within the segment, mask = the segment's lanes.
+template <int SEG>
+struct Seg {
+    int sl, base;
+    unsigned mask;
+    __device__ __forceinline__ Seg()
+    {
+        const int lane = threadIdx.x & 31;
+        sl = SEG == 32 ? lane : (lane & (SEG - 1));
+        base = lane - sl;
+        mask = SEG == 32 ? kFull : (((1u << SEG) - 1u) << base);
+    }
+};
+
+template <int SEG>
+__device__ __forceinline__ long long seg_sum64(long long x, unsigned mask)
+{
+#pragma unroll
+    for (int o = SEG / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o);
+    return x;
+}
+
 // ------------------------------------------------------- Hungarian method
 //
 // Shortest-augmenting-path Hungarian method with row and column potentials,
@@ -249,6 +272,10 @@ __device__ __forceinline__ long long warp_sum64(long long x)
 // steps_out / relax_out accumulate the LAP's work (32-bit: a caller sums at
 // most one launch's LAPs of one warp, far below 2^32 for n <= 64).
 //
+// SEG = 16 runs the same method on a half-warp (width <= 16, NS = 1): each
+// half of a warp solves its own LAP, every warp-wide primitive restricted to
+// the half's lanes; the halves may diverge and reconverge freely.
+//
 // M: shared memory, row r at M + r * ld (rows 0..n-1).  The n columns are the
 // indices c < width other than dead0 and dead1 (width <= 32 * NS); a column's
 // lane and slot follow its index, so ties still go to the smallest column.
@@ -257,14 +284,16 @@ __device__ __forceinline__ long long warp_sum64(long long x)
 // latest when every column is labelled, and an augmenting path is at most as
 // long as the phase.  If an invariant fails (it cannot for entries in range)
 // the function stops and returns false instead of spinning.
-template <int NS, bool PACK>
+template <int NS, bool PACK, int SEG = 32>
 __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld, int n, int width,
                                                int dead0, int dead1, int (&rowOf)[NS],
                                                int (&uM)[NS], int (&v)[NS],
                                                unsigned &steps_out, unsigned &relax_out)
 {
+    static_assert(SEG == 32 || (SEG == 16 && NS == 1), "a half-warp LAP has one column per lane");
     constexpr unsigned kDone = 0x80000000u;  // key of a labelled (or absent) column
-    const int lane = threadIdx.x & 31;
+    const Seg<SEG> g;
+    const int lane = g.sl;  // the lane's place in its segment
     bool valid[NS];
     int way[NS], dlab[NS];
     unsigned key[NS];
@@ -310,23 +339,23 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
             }
             unsigned lmin = key[0];
             if constexpr (NS == 2) lmin = min(lmin, key[1]);
-            mm = __reduce_min_sync(kFull, lmin);
+            mm = __reduce_min_sync(g.mask, lmin);
             if constexpr (PACK) {
                 Dk = (int)(mm >> 6);
                 j1 = (int)(mm & 63u);
             } else {
                 Dk = (int)mm;
-                const unsigned b0 = __ballot_sync(kFull, key[0] == mm);
+                const unsigned b0 = __ballot_sync(g.mask, key[0] == mm) >> g.base;
                 if constexpr (NS == 1) {
                     j1 = __ffs(b0) - 1;
                 } else {
-                    const unsigned b1 = __ballot_sync(kFull, key[1] == mm);
+                    const unsigned b1 = __ballot_sync(g.mask, key[1] == mm);
                     j1 = b0 ? __ffs(b0) - 1 : 31 + __ffs(b1);
                 }
             }
             const int src = j1 & 31, sl = j1 >> 5;
-            const int rj = __shfl_sync(kFull, pick<NS>(rowOf, sl), src);
-            const int uj = __shfl_sync(kFull, pick<NS>(uM, sl), src);
+            const int rj = __shfl_sync(g.mask, pick<NS>(rowOf, sl), g.base + src);
+            const int uj = __shfl_sync(g.mask, pick<NS>(uM, sl), g.base + src);
             if (rj < 0 || mm == kDone) break;  // free column: augmenting path found
             if (lane == src) {
                 put<NS>(key, sl, kDone);
@@ -344,7 +373,7 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const bool lab = valid[s] && key[s] == kDone;
-            K += __popc(__ballot_sync(kFull, lab));
+            K += __popc(__ballot_sync(g.mask, lab));
             if (lab) {
                 const int dd = Dend - dlab[s];
                 v[s] -= dd;
@@ -359,11 +388,11 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
         for (int hop = 0;; ++hop) {
             if (hop > K) return false;
             const int cs = c >> 5, cl = c & 31;
-            const int w = __shfl_sync(kFull, pick<NS>(way, cs), cl);
+            const int w = __shfl_sync(g.mask, pick<NS>(way, cs), g.base + cl);
             int nr = r, nu = Dend;
             const int ws = (w < 0 ? 0 : w) >> 5, wl = (w < 0 ? 0 : w) & 31;
-            const int pr = __shfl_sync(kFull, pick<NS>(rowOf, ws), wl);
-            const int pu = __shfl_sync(kFull, pick<NS>(uM, ws), wl);
+            const int pr = __shfl_sync(g.mask, pick<NS>(rowOf, ws), g.base + wl);
+            const int pu = __shfl_sync(g.mask, pick<NS>(uM, ws), g.base + wl);
             if (w >= 0) {
                 nr = pr;
                 nu = pu;
@@ -382,31 +411,31 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
 }
 
 // S = sum of the row and column potentials = cost of the assignment.
-template <int NS>
+template <int NS, int SEG = 32>
 __device__ __forceinline__ long long lap_value(int width, int dead0, int dead1, const int (&uM)[NS],
                                                const int (&v)[NS])
 {
-    const int lane = threadIdx.x & 31;
+    const Seg<SEG> g;
     long long s = 0;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-        const int c = lane + 32 * k;
+        const int c = g.sl + 32 * k;
         if (c < width && c != dead0 && c != dead1) s += (long long)uM[k] + v[k];
     }
-    return warp_sum64(s);
+    return seg_sum64<SEG>(s, g.mask);
 }
 
 // Row potentials by row index into shared uRow[n] (and the column of each row
 // into colOf[n] when non-null); the caller syncs the warp afterwards.
-template <int NS>
+template <int NS, int SEG = 32>
 __device__ __forceinline__ void scatter_rows(int n, int width, int dead0, int dead1,
                                              const int (&rowOf)[NS], const int (&uM)[NS],
                                              int *uRow, int *colOf, int ustride = 1)
 {
-    const int lane = threadIdx.x & 31;
+    const Seg<SEG> g;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-        const int c = lane + 32 * k;
+        const int c = g.sl + 32 * k;
         if (c < width && c != dead0 && c != dead1 && rowOf[k] >= 0 && rowOf[k] < n) {
             uRow[rowOf[k] * ustride] = uM[k];
             if (colOf) colOf[rowOf[k]] = c;

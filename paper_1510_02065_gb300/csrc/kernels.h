@@ -160,7 +160,10 @@ struct Group {
     bool pack;              // every instance's keys fit the packed reduction
     bool rlt1_only;
     bool sym;               // D in the class-sum store (every instance of the group)
-    unsigned *counter;      // D->C work counter
+    int small_tiles;        // D->C: the first small_tiles tiles (instances with N <= 16, which
+                            // come first in the group) are solved two per warp, 16 lanes each
+    int smallTS;            // largest tile stride (ints) among those instances
+    unsigned *counter;      // D->C work counters: [0] one tile per warp, [1] pairs of small tiles
     DevStatus *status;      // error bits and work counters of the group
     const int4 *triples;    // facility triples i<k<p ordered by p: the first C(N,3) serve N
     NodeDesc first;         // copy of nodes[0]: kernels of a group of one read it as a parameter

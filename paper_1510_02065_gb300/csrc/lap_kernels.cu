@@ -17,6 +17,7 @@
 namespace rlt2 {
 
 constexpr int kClapWarps = 4;
+constexpr int kDlap16Warps = 4;
 constexpr int kXlapWarps = 4;
 constexpr int kBatchWarps = 4;
 
@@ -26,20 +27,22 @@ constexpr int kBatchWarps = 4;
 // solve its LAP, write the residual tile back in place and S to yS.  Returns
 // false if the copy did not complete within the spin limit (recorded in
 // status; the copy in flight has landed or been waited for, bounded).
-template <int NS, bool PACK>
+// SEG = 16: the calling half-warp solves the tile (N <= 16), lane = its lane in the half.
+template <int NS, bool PACK, int SEG = 32>
 __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *buf, uint64_t *bar,
                                           unsigned &parity, int lane, unsigned &steps, unsigned &relax,
                                           DevStatus *status)
 {
+    const Seg<SEG> sg;
     const int N = nd.N, W = nd.W, n = N - 2, m = N - 1, TS = nd.TS;
     if (lane == 0) {
         fence_proxy_async_smem();
         bulk_load(buf, nd.p.z + (size_t)t * TS, (unsigned)TS * 4u, bar);
     }
-    if (!__all_sync(kFull, mbar_wait(bar, parity))) {
+    if (!__all_sync(sg.mask, mbar_wait(bar, parity))) {
         if (lane == 0) atomicOr(&status->err, kDevTimeout);
         mbar_wait(bar, parity);
-        __syncwarp();
+        __syncwarp(sg.mask);
         return false;
     }
     parity ^= 1u;
@@ -51,11 +54,11 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
     const int j = (int)(ij - fdiv(ij, nd.fN) * (unsigned)N);
     const int nl = nn + (nn >= j);
     int rowOf[NS], uM[NS], v[NS];
-    if (!warp_hungarian<NS, PACK>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
+    if (!warp_hungarian<NS, PACK, SEG>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
         atomicOr(&status->err, kDevInternal);
     // u of every row goes to the row's column j, which holds no coefficient
-    scatter_rows<NS>(n, N, j, nl, rowOf, uM, buf + j, nullptr, W);
-    __syncwarp();
+    scatter_rows<NS, SEG>(n, N, j, nl, rowOf, uM, buf + j, nullptr, W);
+    __syncwarp(sg.mask);
     int *gz = nd.p.z + (size_t)t * TS;
     for (int r = 0; r < n; ++r) {
         const int ur = buf[r * W + j];
@@ -65,12 +68,12 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
             if (c < W) gz[r * W + c] = (c < N && c != j && c != nl) ? buf[r * W + c] - ur - v[s] : 0;
         }
     }
-    const long long S = lap_value<NS>(N, j, nl, uM, v);
+    const long long S = lap_value<NS, SEG>(N, j, nl, uM, v);
     if (lane == 0) nd.p.yS[t] = (int)S;
     // the generic writes of column j above precede the next tile's bulk copy
     // into this buffer (async proxy)
     fence_proxy_async_smem();
-    __syncwarp();
+    __syncwarp(sg.mask);
     return true;
 }
 
@@ -79,10 +82,11 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
 // at once), each coefficient becomes its member value in place, and the LAP's
 // duals (u of every row, v of every location column) go to du instead of a
 // residual tile.
-template <int NS, bool PACK>
+template <int NS, bool PACK, int SEG = 32>
 __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, int *buf, int lane,
                                               unsigned &steps, unsigned &relax, DevStatus *status)
 {
+    const Seg<SEG> sg;
     const int N = nd.N, W = nd.W, n = N - 2, m = N - 1;
     const unsigned ij = fdiv(t, nd.fmm);
     const unsigned rem = t - ij * (unsigned)(m * m);
@@ -127,29 +131,29 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
             if (valid[s]) cp_async4(buf + r * W + lane + 32 * s, T + base + lane + 32 * s);
     }
     cp_async_wait_all();
-    __syncwarp();
+    __syncwarp(sg.mask);
     for (int rr = 0; rr < n; ++rr) {
         const int rank = rr < a ? R0 : rr < c - 1 ? R1 : R2;
 #pragma unroll
         for (int s = 0; s < NS; ++s)
             if (valid[s]) buf[rr * W + lane + 32 * s] = sym_member(buf[rr * W + lane + 32 * s], rank);
     }
-    __syncwarp();
+    __syncwarp(sg.mask);
     int rowOf[NS], uM[NS], v[NS];
-    if (!warp_hungarian<NS, PACK>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
+    if (!warp_hungarian<NS, PACK, SEG>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
         atomicOr(&status->err, kDevInternal);
-    scatter_rows<NS>(n, N, j, nl, rowOf, uM, buf + j, nullptr, W);  // u to the free column j
-    __syncwarp();
+    scatter_rows<NS, SEG>(n, N, j, nl, rowOf, uM, buf + j, nullptr, W);  // u to the free column j
+    __syncwarp(sg.mask);
     int *du = nd.p.du + (size_t)t * nd.DS;
-    for (int r = lane; r < n; r += 32) du[r] = buf[r * W + j];
+    for (int r = lane; r < n; r += SEG) du[r] = buf[r * W + j];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int f = lane + 32 * s;
         if (f < W) du[nd.U0 + f] = (f < N && f != j && f != nl) ? v[s] : 0;
     }
-    const long long S = lap_value<NS>(N, j, nl, uM, v);
+    const long long S = lap_value<NS, SEG>(N, j, nl, uM, v);
     if (lane == 0) nd.p.yS[t] = (int)S;
-    __syncwarp();
+    __syncwarp(sg.mask);
     return true;
 }
 
@@ -182,8 +186,8 @@ __global__ void __launch_bounds__(WARPS * 32, 64 / WARPS) dlap_kernel(Group g)
     const unsigned ntiles = (unsigned)g.tiles;  // < 2^31 for any group the host accepts
     int b = 0;
     for (;;) {
-        unsigned T = 0;
-        if (lane == 0) T = atomicAdd(g.counter, 1u);
+        unsigned T = 0;  // tiles [0, small_tiles) are the half-warp kernel's
+        if (lane == 0) T = atomicAdd(g.counter, 1u) + (unsigned)g.small_tiles;
         T = __shfl_sync(kFull, T, 0);
         if (T >= ntiles) break;
         bool ok;
@@ -209,6 +213,66 @@ __global__ void __launch_bounds__(WARPS * 32, 64 / WARPS) dlap_kernel(Group g)
         ++laps;
     }
     if (lane == 0 && laps) {
+        atomicAdd(&g.status->laps, (unsigned long long)laps);
+        atomicAdd(&g.status->steps, (unsigned long long)steps);
+        atomicAdd(&g.status->relax, (unsigned long long)relax);
+        atomicAdd(&g.status->dlaps, (unsigned long long)laps);
+        atomicAdd(&g.status->dsteps, (unsigned long long)steps);
+        atomicAdd(&g.status->drelax, (unsigned long long)relax);
+    }
+}
+
+// Tiles of instances with N <= 16 (the group's first small_tiles tiles): two
+// per warp, one per half-warp (LAPs of width <= 16 on 16 lanes), from the
+// second work counter.  Two buffers of smallTS ints and two mbarriers per
+// warp; half h always uses buffer and barrier h.
+template <bool PACK, bool ONE, bool SYM>
+__global__ void __launch_bounds__(kDlap16Warps * 32, 64 / kDlap16Warps) dlap16_kernel(Group g)
+{
+    if (ONE && *g.first.p.stop) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    int *buf = reinterpret_cast<int *>(smem) + ((size_t)warp * 2 + half) * g.smallTS;
+    unsigned char *tail = smem + (size_t)kDlap16Warps * 2 * g.smallTS * 4;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tail) + warp * 2 + half;
+
+    if (hl == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    unsigned parity = 0;
+    unsigned steps = 0, relax = 0, laps = 0;
+    const unsigned small = (unsigned)g.small_tiles, units = (small + 1u) / 2u;
+    int b = 0;
+    for (;;) {
+        unsigned U = 0;
+        if (lane == 0) U = atomicAdd(g.counter + 1, 1u);
+        U = __shfl_sync(kFull, U, 0);
+        if (U >= units) break;
+        const unsigned T = 2u * U + (unsigned)half;
+        bool ok = true;
+        if (T < small) {
+            if constexpr (ONE) {
+                if constexpr (SYM) ok = dlap_tile_sym<1, PACK, 16>(g.first, T, buf, hl, steps, relax, g.status);
+                else ok = dlap_tile<1, PACK, 16>(g.first, T, buf, bar, parity, hl, steps, relax, g.status);
+                laps += ok;
+            } else {
+                if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
+                    b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
+                const NodeDesc &nd = g.nodes[b];
+                if (!*nd.p.stop) {
+                    const unsigned t = T - (unsigned)nd.tile_base;
+                    if constexpr (SYM) ok = dlap_tile_sym<1, PACK, 16>(nd, t, buf, hl, steps, relax, g.status);
+                    else ok = dlap_tile<1, PACK, 16>(nd, t, buf, bar, parity, hl, steps, relax, g.status);
+                    laps += ok;
+                }
+            }
+        }
+        if (__any_sync(kFull, !ok)) return;  // a half gave up (recorded); leave together
+    }
+    if (hl == 0 && laps) {
         atomicAdd(&g.status->laps, (unsigned long long)laps);
         atomicAdd(&g.status->steps, (unsigned long long)steps);
         atomicAdd(&g.status->relax, (unsigned long long)relax);
@@ -441,8 +505,38 @@ static cudaError_t dlap_pick(const Group &g, int sm_count, cudaStream_t s)
     return g.pack ? dlap_go<2, true, ONE, SYM>(g, sm_count, s) : dlap_go<2, false, ONE, SYM>(g, sm_count, s);
 }
 
+template <bool PACK, bool ONE, bool SYM>
+static cudaError_t dlap16_go(const Group &g, int sm_count, cudaStream_t s)
+{
+    const size_t smem = (size_t)kDlap16Warps * ((size_t)g.smallTS * 2 * 4 + 16);
+    auto k = dlap16_kernel<PACK, ONE, SYM>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDlap16Warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)per_sm * sm_count;
+    const long long need = ((long long)g.small_tiles / 2 + 1 + kDlap16Warps - 1) / kDlap16Warps;
+    if (grid > need) grid = need;
+    k<<<(unsigned)grid, kDlap16Warps * 32, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+template <bool ONE, bool SYM>
+static cudaError_t dlap16_pick(const Group &g, int sm_count, cudaStream_t s)
+{
+    return g.pack ? dlap16_go<true, ONE, SYM>(g, sm_count, s) : dlap16_go<false, ONE, SYM>(g, sm_count, s);
+}
+
 cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s)
 {
+    cudaError_t e = cudaSuccess;
+    if (g.small_tiles > 0) {
+        if (g.sym) e = g.B == 1 ? dlap16_pick<true, true>(g, sm_count, s) : dlap16_pick<false, true>(g, sm_count, s);
+        else e = g.B == 1 ? dlap16_pick<true, false>(g, sm_count, s) : dlap16_pick<false, false>(g, sm_count, s);
+        if (e != cudaSuccess || g.small_tiles >= g.tiles) return e;
+    }
     if (g.sym) return g.B == 1 ? dlap_pick<true, true>(g, sm_count, s) : dlap_pick<false, true>(g, sm_count, s);
     return g.B == 1 ? dlap_pick<true, false>(g, sm_count, s) : dlap_pick<false, false>(g, sm_count, s);
 }

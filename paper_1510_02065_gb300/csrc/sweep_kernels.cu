@@ -253,7 +253,7 @@ __device__ __forceinline__ void p1_shares(const P1Layout &L, int N, int i, int k
 template <int JC, bool ONE>
 __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant__ Group g)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *g.counter = 0;  // work counter of the D -> C sweep
+    if (blockIdx.x == 0 && threadIdx.x < 2) g.counter[threadIdx.x] = 0;  // work counters of the D -> C sweep
     const NodeDesc &nd =
         ONE ? g.first
             : g.nodes[find_node(g.nodes, g.B, blockIdx.x, [](const NodeDesc &d) { return (long long)d.cta_base; })];
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
 template <int JC, bool ONE>
 __global__ void __launch_bounds__(kP1Threads, 2) p1_sym_kernel(const __grid_constant__ Group g)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *g.counter = 0;  // work counter of the D -> C sweep
+    if (blockIdx.x == 0 && threadIdx.x < 2) g.counter[threadIdx.x] = 0;  // work counters of the D -> C sweep
     const NodeDesc &nd =
         ONE ? g.first
             : g.nodes[find_node(g.nodes, g.B, blockIdx.x, [](const NodeDesc &d) { return (long long)d.cta_base; })];

@@ -48,7 +48,7 @@ class rlt2_node(C.Structure):
 class rlt2_opts(C.Structure):
     _fields_ = [("rlt1_only", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
                 ("max_iters", C.c_int), ("ub", C.c_double), ("min_progress", C.c_double),
-                ("stream", C.c_void_p), ("store", C.c_int)]
+                ("stream", C.c_void_p), ("store", C.c_int), ("lanes", C.c_int)]
 
 
 _lib = None
@@ -95,7 +95,7 @@ def lib():
         "rlt2_subproblem": (C.c_int, [_i32p, _i32p, C.c_int, C.c_int, _i32p, _i32p, _i32p, _i32p,
                                       _i32p, _i64p]),
         "rlt2_batch_bound": (C.c_int, [_i32p, _i32p, C.c_int, C.POINTER(rlt2_node), C.c_int, C.c_int,
-                                       C.POINTER(rlt2_opts), _i64p, _dblp]),
+                                       C.POINTER(rlt2_opts), _i64p, _dblp, _intp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -279,8 +279,9 @@ def rlt2_subproblem(F, D, fac, loc):
     return Fp, Dp, Bl, cst.value
 
 
-def rlt2_batch_bound(F, D, nodes, iters, stream=0, store=RLT2_STORE_TILES):
-    """nodes: list of (fac, loc) arrays -> (LB per node as int64 array, device ms)."""
+def rlt2_batch_bound(F, D, nodes, iters, stream=0, store=RLT2_STORE_TILES, lanes=0, return_lanes=False):
+    """nodes: list of (fac, loc) arrays -> (LB per node as int64 array, device ms)
+    [, lanes per D->C LAP used for the nodes with N' <= 16]."""
     F = np.ascontiguousarray(F, np.int32)
     D = np.ascontiguousarray(D, np.int32)
     keep = [(np.ascontiguousarray(f, np.int32), np.ascontiguousarray(l, np.int32)) for f, l in nodes]
@@ -292,11 +293,13 @@ def rlt2_batch_bound(F, D, nodes, iters, stream=0, store=RLT2_STORE_TILES):
     o = rlt2_default_opts()
     o.stream = stream or None
     o.store = int(store)
+    o.lanes = int(lanes)
     out = np.zeros(len(keep), np.int64)
     ms = C.c_double()
+    used = C.c_int()
     _chk(lib().rlt2_batch_bound(_p32(F), _p32(D), F.shape[0], arr, len(keep), int(iters), C.byref(o),
-                                _p64(out), C.byref(ms)), "rlt2_batch_bound")
-    return out, ms.value
+                                _p64(out), C.byref(ms), C.byref(used)), "rlt2_batch_bound")
+    return (out, ms.value, used.value) if return_lanes else (out, ms.value)
 
 
 # ------------------------------------------------------------ convenience
@@ -306,16 +309,17 @@ class Context:
 
     def __init__(self, F, D, B_lin=None, lb_const=0, rlt1_only=False, use_graph=True,
                  profile=False, max_iters=65536, ub=0.0, min_progress=0.0, stream=0,
-                 store=RLT2_STORE_TILES):
-        o = self._opts(rlt1_only, use_graph, profile, max_iters, ub, min_progress, stream, store)
+                 store=RLT2_STORE_TILES, lanes=0):
+        o = self._opts(rlt1_only, use_graph, profile, max_iters, ub, min_progress, stream, store, lanes)
         self.N = int(np.asarray(F).shape[0])
         self.ctx = rlt2_create(F, D, self.N, B_lin, lb_const, o)
 
     @staticmethod
     def _opts(rlt1_only=False, use_graph=True, profile=False, max_iters=65536, ub=0.0,
-              min_progress=0.0, stream=0, store=RLT2_STORE_TILES):
+              min_progress=0.0, stream=0, store=RLT2_STORE_TILES, lanes=0):
         o = rlt2_default_opts()
         o.store = int(store)
+        o.lanes = int(lanes)
         o.rlt1_only = int(rlt1_only)
         o.use_graph = int(use_graph)
         o.profile = int(profile)

@@ -91,3 +91,27 @@ def test_batch_rejects_too_small_residual(gpu):
     F, D = I.uniform_symmetric(6, seed=1)
     with pytest.raises(rlt2.Rlt2Error):
         rlt2.rlt2_batch_bound(F, D, [(np.arange(4), np.arange(4))], 2)   # N' = 2
+
+
+@pytest.mark.gpu
+def test_batch_lanes_autotuned_and_forced_agree(gpu):
+    """Nodes with N' <= 16 and larger ones in one batch: the autotuned run (first
+    two passes time whole- and half-warp LAPs) and both forced forms give the
+    same bounds; the choice is reported."""
+    F, D = I.clustered_euclid(20, seed=9)
+    rng = np.random.default_rng(9)
+    nodes = []
+    for s in range(12):
+        k = int(rng.integers(1, 12))          # N' from 9 to 19: both forms present
+        nodes.append((rng.choice(20, size=k, replace=False), rng.choice(20, size=k, replace=False)))
+    nodes.append((np.array([4]), np.array([7])))   # N' = 19
+    nodes.append((np.arange(8), np.arange(8)[::-1].copy()))   # N' = 12
+    lb_auto, _, lanes = rlt2.rlt2_batch_bound(F, D, nodes, 5, return_lanes=True)
+    assert lanes in (16, 32)
+    lb16, _, l16 = rlt2.rlt2_batch_bound(F, D, nodes, 5, lanes=16, return_lanes=True)
+    lb32, _, l32 = rlt2.rlt2_batch_bound(F, D, nodes, 5, lanes=32, return_lanes=True)
+    assert (l16, l32) == (16, 32)
+    assert list(lb_auto) == list(lb16) == list(lb32)
+    big = [(f, l) for f, l in nodes if 20 - len(f) > 16]
+    _, _, lanes_big = rlt2.rlt2_batch_bound(F, D, big, 3, return_lanes=True)
+    assert lanes_big == 32                    # no node small enough for half-warps

@@ -319,3 +319,30 @@ def test_unknown_store_rejected(gpu):
     with pytest.raises(rlt2.Rlt2Error) as e:
         rlt2.Context(F, D, store=2)
     assert e.value.code == rlt2.RLT2_E_INVAL
+
+
+@pytest.mark.parametrize("store", STORES)
+@pytest.mark.parametrize("N", [5, 8, 13, 16])
+def test_half_warp_and_whole_warp_lanes_agree(gpu, orc, N, store):
+    """D->C LAPs of N <= 16 on half-warps (the default) and on whole warps give
+    the same state after every pass, equal to the oracle's."""
+    F, D = I.clustered_euclid(N, seed=40 + N)
+    Bl = np.random.default_rng(N).integers(0, 30, size=(N, N)).astype(np.int32)
+    st = orc.State(F, D, B_lin=Bl, lb_const=3)
+    with rlt2.Context(F, D, B_lin=Bl, lb_const=3, store=store, lanes=16) as a, \
+            rlt2.Context(F, D, B_lin=Bl, lb_const=3, store=store, lanes=32) as b:
+        for t in range(6):
+            a.iterate(1)
+            b.iterate(1)
+            st.iterate()
+            assert_same_state(a, st, "16 lanes, pass %d" % (t + 1))
+            assert_same_state(b, st, "32 lanes, pass %d" % (t + 1))
+        wa, wb = a.work(), b.work()
+        assert (wa["d_laps"], wa["d_steps"], wa["d_relaxations"]) == (wb["d_laps"], wb["d_steps"], wb["d_relaxations"])
+
+
+def test_unknown_lanes_rejected(gpu):
+    F, D = I.uniform_symmetric(6, seed=1)
+    with pytest.raises(rlt2.Rlt2Error) as e:
+        rlt2.Context(F, D, lanes=8)
+    assert e.value.code == rlt2.RLT2_E_INVAL
