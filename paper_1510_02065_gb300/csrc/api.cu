@@ -147,7 +147,8 @@ cudaError_t init_node(const NodeDesc &nd, const int32_t *F, const int32_t *D, co
 }
 
 // One pass of Algorithm 1 for the whole group.  ev: 5 events around the stages.
-cudaError_t enqueue_pass(const Group &g, int sm_count, cudaStream_t s, cudaEvent_t *ev)
+cudaError_t enqueue_pass(const Group &g, int sm_count, cudaStream_t s, cudaEvent_t *ev,
+                         const SideStream *side = nullptr)
 {
     cudaError_t e;
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
@@ -155,7 +156,7 @@ cudaError_t enqueue_pass(const Group &g, int sm_count, cudaStream_t s, cudaEvent
     if (!g.rlt1_only) {
         if ((e = launch_p1(g, s)) != cudaSuccess) return e;
         if ((e = mark(1)) != cudaSuccess) return e;
-        if ((e = launch_dlap(g, sm_count, s)) != cudaSuccess) return e;
+        if ((e = launch_dlap(g, sm_count, s, side)) != cudaSuccess) return e;
     } else if ((e = mark(1)) != cudaSuccess) {
         return e;
     }
@@ -167,12 +168,12 @@ cudaError_t enqueue_pass(const Group &g, int sm_count, cudaStream_t s, cudaEvent
 }
 
 cudaError_t capture_passes(const Group &g, int sm_count, cudaStream_t s, int passes,
-                           cudaGraph_t *graph, cudaGraphExec_t *exec)
+                           cudaGraph_t *graph, cudaGraphExec_t *exec, const SideStream *side = nullptr)
 {
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t e2 = cudaSuccess;
-    for (int t = 0; t < passes && e2 == cudaSuccess; t++) e2 = enqueue_pass(g, sm_count, s, nullptr);
+    for (int t = 0; t < passes && e2 == cudaSuccess; t++) e2 = enqueue_pass(g, sm_count, s, nullptr, side);
     e = cudaStreamEndCapture(s, graph);
     if (e2 != cudaSuccess) return e2;
     if (e != cudaSuccess) return e;
@@ -688,7 +689,26 @@ struct rlt2_group {
     cudaEvent_t done = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    SideStream side{};     // the half-warp D->C kernel beside the whole-warp one
 };
+
+static int make_side(SideStream &sd)
+{
+    if (cudaStreamCreateWithFlags(&sd.s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming) != cudaSuccess)
+        return RLT2_E_CUDA;
+    return RLT2_OK;
+}
+
+static void free_side(SideStream &sd)
+{
+    if (sd.s2) cudaStreamSynchronize(sd.s2);
+    if (sd.fork) cudaEventDestroy(sd.fork);
+    if (sd.join) cudaEventDestroy(sd.join);
+    if (sd.s2) cudaStreamDestroy(sd.s2);
+    sd = SideStream{};
+}
 
 static void free_group(rlt2_group *gr)
 {
@@ -697,6 +717,7 @@ static void free_group(rlt2_group *gr)
     if (gr->exec) cudaGraphExecDestroy(gr->exec);
     if (gr->graph) cudaGraphDestroy(gr->graph);
     if (gr->done) cudaEventDestroy(gr->done);
+    free_side(gr->side);
     cudaFree(gr->mem);
     if (gr->own_stream && gr->stream) cudaStreamDestroy(gr->stream);
     delete gr;
@@ -728,6 +749,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     }
     if (cudaEventCreateWithFlags(&gr->done, cudaEventDisableTiming) != cudaSuccess)
         return fail(RLT2_E_CUDA);
+    if (make_side(gr->side) != RLT2_OK) return fail(RLT2_E_CUDA);
     int maxN = 0;
     bool pack = true;
     for (rlt2_ctx *c : gr->ctxs) {
@@ -820,7 +842,7 @@ int rlt2_group_iterate(rlt2_group *gr, int k)
     for (rlt2_ctx *c : gr->ctxs)
         if ((long long)c->enqueued + k > c->opts.max_iters) return RLT2_E_STATE;
     if (k == 0) return RLT2_OK;
-    if (!gr->exec) CK(capture_passes(gr->g, gr->sm_count, gr->stream, 1, &gr->graph, &gr->exec));
+    if (!gr->exec) CK(capture_passes(gr->g, gr->sm_count, gr->stream, 1, &gr->graph, &gr->exec, &gr->side));
     for (int t = 0; t < k; t++) CK(cudaGraphLaunch(gr->exec, gr->stream));
     for (rlt2_ctx *c : gr->ctxs) c->enqueued += k;
     // every context's later work starts after the group's passes
@@ -1010,11 +1032,16 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
 
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaEvent_t tev[10] = {};
+    SideStream side{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int rc = RLT2_OK;
     do {
         if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) break;
+        if (make_side(side) != RLT2_OK) {
+            e = cudaErrorUnknown;
+            break;
+        }
         if ((e = cudaMemcpyAsync(base + o_nodes, hn.data(), (size_t)B * sizeof(NodeDesc),
                                  cudaMemcpyHostToDevice, s)) != cudaSuccess)
             break;
@@ -1039,9 +1066,9 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
             for (int k = 0; k < 10 && e == cudaSuccess; k++) e = cudaEventCreate(&tev[k]);
             DevStatus st[3];
             if (e == cudaSuccess) e = cudaMemcpyAsync(&st[0], g.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = enqueue_pass(g, sm_count, s, tev);
+            if (e == cudaSuccess) e = enqueue_pass(g, sm_count, s, tev, &side);
             if (e == cudaSuccess) e = cudaMemcpyAsync(&st[1], g.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = enqueue_pass(g16, sm_count, s, tev + 5);
+            if (e == cudaSuccess) e = enqueue_pass(g16, sm_count, s, tev + 5, &side);
             if (e == cudaSuccess) e = cudaMemcpyAsync(&st[2], g.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) break;
@@ -1057,7 +1084,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
         const Group &gb = lanes == 16 ? g16 : g;
         // all (remaining) passes of all nodes: one captured graph, one launch
         if (iters > done) {
-            if ((e = capture_passes(gb, sm_count, s, iters - done, &graph, &exec)) != cudaSuccess) break;
+            if ((e = capture_passes(gb, sm_count, s, iters - done, &graph, &exec, &side)) != cudaSuccess) break;
             if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
         }
         if (lanes_out) *lanes_out = small_tiles == 0 ? 32 : lanes;
@@ -1080,6 +1107,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     if (t1) cudaEventDestroy(t1);
     for (cudaEvent_t ev : tev)
         if (ev) cudaEventDestroy(ev);
+    free_side(side);
     cudaFree(base);
     if (own) cudaStreamDestroy(own);
     return rc;

@@ -184,7 +184,14 @@ cudaError_t launch_spread_x(const Group &g, cudaStream_t s);
 // (tiles x (N-2) x W ints at out; columns without coefficient 0).
 cudaError_t launch_materialize(const NodeDesc &nd, int *out, cudaStream_t s);
 cudaError_t launch_p1(const Group &g, cudaStream_t s);
-cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s);
+// A second stream and fork/join events: with them, the half-warp D->C kernel
+// of a group that has both small and larger instances runs beside the
+// whole-warp one (in eager launches and in captured graphs alike).
+struct SideStream {
+    cudaStream_t s2;
+    cudaEvent_t fork, join;
+};
+cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s, const SideStream *side = nullptr);
 cudaError_t launch_clap(const Group &g, cudaStream_t s);
 cudaError_t launch_xlap(const Group &g, cudaStream_t s);
 cudaError_t launch_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,

@@ -529,16 +529,34 @@ static cudaError_t dlap16_pick(const Group &g, int sm_count, cudaStream_t s)
     return g.pack ? dlap16_go<true, ONE, SYM>(g, sm_count, s) : dlap16_go<false, ONE, SYM>(g, sm_count, s);
 }
 
-cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s)
+static cudaError_t dlap16_any(const Group &g, int sm_count, cudaStream_t s)
 {
-    cudaError_t e = cudaSuccess;
-    if (g.small_tiles > 0) {
-        if (g.sym) e = g.B == 1 ? dlap16_pick<true, true>(g, sm_count, s) : dlap16_pick<false, true>(g, sm_count, s);
-        else e = g.B == 1 ? dlap16_pick<true, false>(g, sm_count, s) : dlap16_pick<false, false>(g, sm_count, s);
-        if (e != cudaSuccess || g.small_tiles >= g.tiles) return e;
-    }
+    if (g.sym) return g.B == 1 ? dlap16_pick<true, true>(g, sm_count, s) : dlap16_pick<false, true>(g, sm_count, s);
+    return g.B == 1 ? dlap16_pick<true, false>(g, sm_count, s) : dlap16_pick<false, false>(g, sm_count, s);
+}
+
+static cudaError_t dlap_any(const Group &g, int sm_count, cudaStream_t s)
+{
     if (g.sym) return g.B == 1 ? dlap_pick<true, true>(g, sm_count, s) : dlap_pick<false, true>(g, sm_count, s);
     return g.B == 1 ? dlap_pick<true, false>(g, sm_count, s) : dlap_pick<false, false>(g, sm_count, s);
+}
+
+cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s, const SideStream *side)
+{
+    if (g.small_tiles <= 0) return dlap_any(g, sm_count, s);
+    if (g.small_tiles >= g.tiles) return dlap16_any(g, sm_count, s);
+    cudaError_t e;
+    if (!side) {
+        if ((e = dlap16_any(g, sm_count, s)) != cudaSuccess) return e;
+        return dlap_any(g, sm_count, s);
+    }
+    // fork: small tiles on the side stream, the rest here; join before returning
+    if ((e = cudaEventRecord(side->fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side->s2, side->fork, 0)) != cudaSuccess) return e;
+    if ((e = dlap16_any(g, sm_count, side->s2)) != cudaSuccess) return e;
+    if ((e = dlap_any(g, sm_count, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(side->join, side->s2)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, side->join, 0);
 }
 
 template <int NS, bool PACK>
