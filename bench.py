@@ -34,12 +34,12 @@ OPS_PER_RELAXATION = 9   # textbook int ops of one relaxation
 # kernel's sources hash to the captured version.
 # DRAM bytes per launch from one ncu capture of the headline workload (tile
 # store), valid while the kernel's sources hash to the captured version
-DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2714539520 + 2652155392,
+DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2714420480 + 2651898624,
                 "files": ("lap_kernels.cu", "device.cuh", "kernels.h"),
-                "sources_sha1": "76c11698ddcf23be8e1c476821c8e7dd164d4a5f"}
-P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2741079296 + 2655531008,
+                "sources_sha1": "9c540a01643cd88ebd7d51cd1d615c54fa4f2649"}
+P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2741275648 + 2655557376,
               "files": ("sweep_kernels.cu", "device.cuh", "kernels.h"),
-              "sources_sha1": "53452b72dd6ae9663eb74d4361faa2ff2b4cc69f"}
+              "sources_sha1": "41184b3d8ba7e186eb461cde31bdb07a2430a53d"}
 
 
 def captured_traffic(rec, workload, store):
