@@ -135,6 +135,19 @@ def n35_measure(rlt2, instances, torch, steps, store, warmup=3):
                 rlt2.rlt2_state_bytes(35, store=store) / 1e9)}
 
 
+def bnb_measure(instances, torch):
+    """Branch-and-bound to proven optimality on the 12-facility grid workload:
+    every node's children bounded by one batched RLT2 call (12 passes),
+    strong branching on RLT1 at the root, local-search incumbent."""
+    from paper_1510_02065_gb300 import bnb
+    F, D, _ = instances.instance("grid_n12")
+    torch.cuda.synchronize()
+    r = bnb.BranchAndBound(F, D, iters=12, root_iters=30, strong_depth=1).solve()
+    r.pop("perm", None)
+    r["workload"] = "grid_n12"
+    return r
+
+
 def batch_measure(rlt2, instances, torch, nodes_count, iters):
     """Batched B&B bounding against the plain one-node-at-a-time path.
 
@@ -467,6 +480,8 @@ def main():
         line["n35_tiles"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_TILES)
     if args.serve_requests > 0:
         line["serve"] = serve_measure(instances, torch, args.serve_requests)
+    if args.batch_nodes > 0:
+        line["bnb"] = bnb_measure(instances, torch)
 
     if rank == 0 and world == 1 and args.cpu_budget > 0:
         t_pass, nslices, rest = oracle_sample(F, D, args.cpu_budget)

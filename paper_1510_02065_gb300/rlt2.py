@@ -279,7 +279,8 @@ def rlt2_subproblem(F, D, fac, loc):
     return Fp, Dp, Bl, cst.value
 
 
-def rlt2_batch_bound(F, D, nodes, iters, stream=0, store=RLT2_STORE_TILES, lanes=0, return_lanes=False):
+def rlt2_batch_bound(F, D, nodes, iters, stream=0, store=RLT2_STORE_TILES, lanes=0, return_lanes=False,
+                     ub=0.0):
     """nodes: list of (fac, loc) arrays -> (LB per node as int64 array, device ms)
     [, lanes per D->C LAP used for the nodes with N' <= 16]."""
     F = np.ascontiguousarray(F, np.int32)
@@ -294,6 +295,7 @@ def rlt2_batch_bound(F, D, nodes, iters, stream=0, store=RLT2_STORE_TILES, lanes
     o.stream = stream or None
     o.store = int(store)
     o.lanes = int(lanes)
+    o.ub = float(ub)
     out = np.zeros(len(keep), np.int64)
     ms = C.c_double()
     used = C.c_int()
