@@ -27,6 +27,8 @@ def lib():
         L.orc_lap_batch.argtypes = [C.c_int, C.c_int, _i64p, _i64p, _i64p, _i64p, _i32p, _i64p]
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.c_int, _i32p, _i32p, _i64p, C.c_int64, C.c_int]
+        L.orc_set_paired.restype = None
+        L.orc_set_paired.argtypes = [C.c_void_p, C.c_int]
         L.orc_destroy.argtypes = [C.c_void_p]
         for name in ("orc_spread_B_to_C", "orc_spread_C_to_D", "orc_complementary_D",
                      "orc_concentrate_D_to_C", "orc_complementary_C", "orc_concentrate_C_to_B"):
@@ -110,7 +112,7 @@ def subproblem(F, D, fac, loc):
 class State:
     """RLT2 dual-ascent state of the oracle (Algorithm 1)."""
 
-    def __init__(self, F, D, B_lin=None, lb_const=0, rlt1_only=False):
+    def __init__(self, F, D, B_lin=None, lb_const=0, rlt1_only=False, paired=False):
         F = np.ascontiguousarray(F, np.int32)
         D = np.ascontiguousarray(D, np.int32)
         self.N = N = F.shape[0]
@@ -122,6 +124,9 @@ class State:
         if not self._h:
             raise MemoryError("oracle state allocation failed (N=%d)" % N)
         self.rlt1_only = rlt1_only
+        self.paired = paired
+        if paired:
+            lib().orc_set_paired(self._h, 1)
 
     def close(self):
         if self._h:

@@ -37,6 +37,18 @@
  *       order, the next column is the unlabelled one of least reduced
  *       distance with ties going to the smallest column index, a distance
  *       label (and its predecessor) changes only on a strict improvement.
+ *   R13 (paired mode, the complementary submatrices of Sec. 6) each
+ *       coefficient (d_ijkn)_pq has the complementary coefficient
+ *       (d_knij)_pq (the same variable by the symmetry constraints), so the
+ *       pair is kept as one sum in the submatrix with i < k and the other is
+ *       held at 0: spreading C -> D adds the shares of c_knij to D_ijkn
+ *       (same rows p, same ranks); the transfer between complementary costs
+ *       of D splits a class sum over its three members of that kind,
+ *       d_ijknpq, d_ijpqkn, d_knpqij (i < k < p, lexicographic order), equally
+ *       as in R4 with s = 3; and D -> C concentrates only the submatrices
+ *       with i < k, adding S to c_ijkn.  Half of D and half of the D -> C LAPs
+ *       remain; the bound differs from the full form (a LAP of a sum is at
+ *       least the sum of the LAPs).
  *
  * Parity pins for every function live in tests/ (N!-enumeration and scipy for
  * the LAP, brute-force QAP optima, the conservation identity
@@ -52,6 +64,7 @@
 typedef struct {
     int N;
     int rlt1_only;     /* strong-branching dual of Sec. 6: Algorithm 1 without D */
+    int paired;        /* complementary submatrices of Sec. 6 kept as one (reading R13) */
     int64_t LB;
     int64_t iters;
     int64_t *b, *c, *d;
@@ -188,6 +201,7 @@ orc_state *orc_create(int N, const int32_t *F, const int32_t *Dist,
     orc_state *st = calloc(1, sizeof(orc_state));
     st->N = N;
     st->rlt1_only = rlt1_only;
+    st->paired = 0;
     st->LB = lb_const;
     size_t n2 = (size_t)N * N, n4 = n2 * n2;
     st->b = calloc(n2, sizeof(int64_t));
@@ -209,6 +223,9 @@ orc_state *orc_create(int N, const int32_t *F, const int32_t *Dist,
                             (int64_t)F[ix2(N, i, k)] * (int64_t)Dist[ix2(N, j, n)];
     return st;
 }
+
+/* Switch a freshly created state to the paired form of reading R13. */
+void orc_set_paired(orc_state *st, int paired) { st->paired = paired; }
 
 void orc_destroy(orc_state *st)
 {
@@ -263,12 +280,17 @@ void orc_spread_C_to_D_range(orc_state *st, int i_lo, int i_hi)
                 for (int n = 0; n < N; n++) {
                     if (n == j) continue;
                     int64_t x = st->c[ix4(N, i, j, k, n)];
+                    /* paired (R13): the shares of c_knij (k < i) go to D_ijkn's complement */
+                    const int up = !st->paired || i < k;
                     int t = 0;
                     for (int p = 0; p < N; p++) {
                         if (p == i || p == k) continue;
                         int64_t sh = row_share(x, m, t++);
-                        for (int q = 0; q < N; q++)
-                            if (q != j && q != n) st->d[ix6(N, i, j, k, n, p, q)] += sh;
+                        for (int q = 0; q < N; q++) {
+                            if (q == j || q == n) continue;
+                            if (up) st->d[ix6(N, i, j, k, n, p, q)] += sh;
+                            else st->d[ix6(N, k, n, i, j, p, q)] += sh;
+                        }
                     }
                     st->c[ix4(N, i, j, k, n)] = 0;
                 }
@@ -309,7 +331,17 @@ void orc_complementary_D_range(orc_state *st, int i_lo, int i_hi)
                             int64_t T = 0;
                             for (int t = 0; t < 6; t++) T += d[mem[t]];
                             track(st, T);
-                            for (int t = 0; t < 6; t++) d[mem[t]] = T / 6 + (t < T % 6 ? 1 : 0);
+                            if (!st->paired) {
+                                for (int t = 0; t < 6; t++) d[mem[t]] = T / 6 + (t < T % 6 ? 1 : 0);
+                            } else {
+                                /* R13: the members with first facility below the second,
+                                 * d_ijknpq, d_ijpqkn, d_knpqij, share T; the others stay 0 */
+                                const int upper[3] = {0, 1, 3}, lower[3] = {2, 4, 5};
+                                for (int t = 0; t < 3; t++) {
+                                    d[mem[upper[t]]] = T / 3 + (t < T % 3 ? 1 : 0);
+                                    d[mem[lower[t]]] = 0;
+                                }
+                            }
                         }
                     }
 }
@@ -355,6 +387,7 @@ void orc_concentrate_D_to_C_range(orc_state *st, int i_lo, int i_hi)
         for (int j = 0; j < N; j++)
             for (int k = 0; k < N; k++) {
                 if (k == i) continue;
+                if (st->paired && k < i) continue;  /* R13: the complement holds the pair */
                 for (int n = 0; n < N; n++) {
                     if (n == j) continue;
                     int r = 0, s = 0;

@@ -259,3 +259,89 @@ def test_clustered_n20_first_passes(orc):
     rng = np.random.default_rng(3)
     perms = np.array([rng.permutation(20) for _ in range(200)])
     assert conservation_residual(F, D, st, perms) == 0
+
+
+# ---------------------------------------------------------------- paired form
+
+def _lower_tiles_zero(st):
+    """Paired form (reading R13): every submatrix D_ijkn with i > k stays 0."""
+    N = st.N
+    idx = np.arange(N)
+    i = idx[:, None, None, None]
+    k = idx[None, None, :, None]
+    low = np.broadcast_to(i > k, (N, N, N, N))
+    return not st.d[low].any()
+
+
+@pytest.mark.parametrize("N,seed", [(3, 0), (4, 1), (5, 2), (6, 3)])
+def test_paired_conservation_every_operation_all_perms(orc, N, seed):
+    """The complementary-submatrix form keeps every solution's cost after each
+    operation, keeps the reduced costs >= 0 and the other half of D at 0, and
+    bounds the optimum."""
+    F, D = I.uniform_symmetric(N, seed=seed)
+    perms = list(itertools.permutations(range(N)))
+    st = orc.State(F, D, paired=True)
+    lbs = []
+    for _ in range(6):
+        step_all(st, F, D, perms)
+        assert _lower_tiles_zero(st)
+        lbs.append(st.LB)
+    assert all(a <= b for a, b in zip(lbs, lbs[1:]))
+    assert lbs[-1] <= brute_force_qap(F, D)
+
+
+def test_paired_asymmetric_linear_term_and_half_the_laps(orc):
+    rng = np.random.default_rng(12)
+    N = 6
+    F = rng.integers(0, 8, size=(N, N)).astype(np.int32)
+    D = rng.integers(0, 8, size=(N, N)).astype(np.int32)
+    np.fill_diagonal(F, 0)
+    np.fill_diagonal(D, 0)
+    Bl = rng.integers(0, 30, size=(N, N))
+    perms = list(itertools.permutations(range(N)))
+    st = orc.State(F, D, B_lin=Bl, lb_const=9, paired=True)
+    full = orc.State(F, D, B_lin=Bl, lb_const=9)
+    for _ in range(3):
+        step_all(st, F, D, perms, Bl, 9)
+        full.iterate()
+    assert st.LB <= brute_force_qap(F, D, Bl, 9)
+    # per pass: N^2 (N-1)^2 / 2 D-LAPs + N^2 C-LAPs + 1, against N^2 (N-1)^2 + N^2 + 1
+    per_pass = N * N * (N - 1) ** 2
+    assert st.work()["laps"] == 3 * (per_pass // 2 + N * N + 1)
+    assert full.work()["laps"] == 3 * (per_pass + N * N + 1)
+
+
+def test_paired_three_way_split_by_hand(orc):
+    """One class of N = 3 (the only one: facilities 0 < 1 < 2, locations
+    0, 1, 2): after spreading c (from one unit of flow) and the 3-way split,
+    the three members with first facility below the second hold T split as
+    floor(T/3) + [t < T mod 3] in lexicographic order, the other three 0."""
+    F = np.zeros((3, 3), np.int32)
+    D = np.zeros((3, 3), np.int32)
+    F[0, 1] = 7          # c_{0j1n} = 7 * D[j,n]
+    D[0, 1] = D[1, 0] = 1
+    st = orc.State(F, D, paired=True)
+    st.spread_B_to_C()
+    st.spread_C_to_D()
+    d = st.d
+    # the pair (i,j,k,n) = (0,0,1,1) and (0,1,1,0) carry c = 7; one row p = 2
+    # with one column q = 2: d_{0,0,1,1,2,2} = 7 and d_{0,1,1,0,2,2} = 7
+    assert d[0, 0, 1, 1, 2, 2] == 7 and d[0, 1, 1, 0, 2, 2] == 7
+    st.complementary_D()
+    # class {(0,0),(1,1),(2,2)}: T = 7; members d_001122, d_002211, d_112200 get 3, 2, 2
+    assert (d[0, 0, 1, 1, 2, 2], d[0, 0, 2, 2, 1, 1], d[1, 1, 2, 2, 0, 0]) == (3, 2, 2)
+    assert (d[1, 1, 0, 0, 2, 2], d[2, 2, 0, 0, 1, 1], d[2, 2, 1, 1, 0, 0]) == (0, 0, 0)
+    # class {(0,1),(1,0),(2,2)}: T = 7 as well
+    assert (d[0, 1, 1, 0, 2, 2], d[0, 1, 2, 2, 1, 0], d[1, 0, 2, 2, 0, 1]) == (3, 2, 2)
+
+
+def test_paired_uniform_n8_below_optimum(orc):
+    F, D, iters = I.instance("uniform_n8")
+    opt = brute_force_qap(F, D)
+    st = orc.State(F, D, paired=True)
+    hist = st.run(iters)
+    assert (np.diff(hist) >= 0).all() and hist[-1] <= opt
+    assert nonneg(st) and _lower_tiles_zero(st)
+    rng = np.random.default_rng(1)
+    perms = np.array([rng.permutation(8) for _ in range(2000)])
+    assert conservation_residual(F, D, st, perms) == 0
