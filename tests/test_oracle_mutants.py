@@ -28,7 +28,8 @@ MUTANTS = {
     "column_potential_sign": ("v[j] -= delta;", "v[j] += delta;"),
     "share_remainder_to_last_rows": ("return x / m + (t < x % m ? 1 : 0);",
                                      "return x / m + (t >= m - x % m ? 1 : 0);"),
-    "spread_into_meaningless_column": ("if (q != j && q != n) st->d", "if (q != j) st->d"),
+    "spread_into_meaningless_column": ("if (q == j || q == n) continue;\n                            if (up)",
+                                       "if (q == j) continue;\n                            if (up)"),
     "complementary_D_rank_swap": ("ix6(N, k, n, i, j, p, q), ix6(N, k, n, p, q, i, j)",
                                   "ix6(N, k, n, p, q, i, j), ix6(N, k, n, i, j, p, q)"),
     "complementary_C_odd_unit_to_second": (
