@@ -73,8 +73,9 @@ typedef struct {
     double min_progress;  /* K of Algorithm 1: stop once LB'/UB < K; 0: never     */
     void *stream;         /* cudaStream_t to run on; NULL = a non-blocking stream
                              created for (and owned by) the context              */
-    int store;            /* how D is kept: RLT2_STORE_TILES (default) or
-                             RLT2_STORE_CLASSES; results are identical          */
+    int store;            /* how D is kept: RLT2_STORE_TILES (default),
+                             RLT2_STORE_CLASSES (identical results) or
+                             RLT2_STORE_PAIRS (the paired dual ascent)          */
     int lanes;            /* lanes per D->C LAP of instances with N <= 16: 32 (a
                              warp each) or 16 (two per warp); 0 (default) =
                              16 for a context or group, chosen by timing for
@@ -93,6 +94,19 @@ typedef struct {
  */
 #define RLT2_STORE_TILES   0
 #define RLT2_STORE_CLASSES 1
+/*
+ * RLT2_STORE_PAIRS: the complementary submatrices of Sec. 6.  Each
+ * coefficient (d_ijkn)_pq has the complementary coefficient (d_knij)_pq (the
+ * same variable), so the pair is kept as one sum in D_ijkn with i < k: half
+ * of D and half of the D->C LAPs per pass.  This is a different dual ascent:
+ * spreading C->D adds the shares of c_knij to D_ijkn, the transfer between
+ * complementary costs of D splits a class sum equally over its three members
+ * d_ijknpq, d_ijpqkn, d_knpqij (i < k < p), and D->C concentrates D_ijkn
+ * (i < k) into c_ijkn.  Its bounds differ from the other two stores' (same
+ * for both of those); the oracle has the same form.  Exported D (level 2):
+ * the pair sums in the tiles with i < k, the others 0.
+ */
+#define RLT2_STORE_PAIRS   2
 
 typedef struct rlt2_ctx rlt2_ctx;
 

@@ -94,12 +94,13 @@ struct NodeOffsets {
 
 constexpr size_t kNone = (size_t)-1;
 
-// D in the tile store (with_d, !sym) or in the class-sum store (with_d, sym).
-NodeOffsets plan_node(Arena &a, int N, bool with_d, bool sym, int hist_cap)
+// D (with_d) in the tile store, the class-sum store or the pair store (RLT2_STORE_*).
+NodeOffsets plan_node(Arena &a, int N, bool with_d, int store, int hist_cap)
 {
     const Geom g = make_geom(N);
+    const bool sym = store == RLT2_STORE_CLASSES;
     NodeOffsets o;
-    o.z = with_d && !sym ? a.take((size_t)g.tiles * g.TS * 4) : kNone;
+    o.z = with_d && !sym ? a.take((size_t)(store == RLT2_STORE_PAIRS ? g.htiles : g.tiles) * g.TS * 4) : kNone;
     o.T = with_d && sym ? a.take((size_t)g.classes_ints * 4) : kNone;
     o.du = with_d && sym ? a.take((size_t)g.tiles * g.DS * 4) : kNone;
     o.yS = a.take((size_t)g.tiles * 4);
@@ -257,7 +258,7 @@ void rlt2_destroy(rlt2_ctx *c) { free_ctx(c); }
 // initialisation of the costs): stream, one arena, the instance descriptor,
 // the group of one, the triple table, zeroed status and work counter.
 // *stage receives 3 N^2 ints of device staging memory.
-static int setup_ctx(rlt2_ctx *c, int N, bool with_d, bool sym, long long U, int32_t **stage)
+static int setup_ctx(rlt2_ctx *c, int N, bool with_d, int store, long long U, int32_t **stage)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RLT2_E_CUDA;
@@ -269,10 +270,11 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, bool sym, long long U, int
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return RLT2_E_CUDA;
         c->own_stream = true;
     }
-    const int JC = p1_chunk(N, with_d && sym);
+    const bool sym = with_d && store == RLT2_STORE_CLASSES, paired = with_d && store == RLT2_STORE_PAIRS;
+    const int JC = p1_chunk(N, sym, paired);
     const std::vector<int4> tri = triple_table(N);
     Arena a;
-    const NodeOffsets no = plan_node(a, N, with_d, sym, c->opts.max_iters);
+    const NodeOffsets no = plan_node(a, N, with_d, store, c->opts.max_iters);
     const size_t o_node = a.take(sizeof(NodeDesc));
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
     const size_t o_cnt = a.take(8);
@@ -286,10 +288,12 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, bool sym, long long U, int
     }
     char *base = c->mem;
     NodeDesc &nd = c->node;
+    nd.paired = paired;
     fill_node(nd, N, JC);
     nd.p = node_state(base, no, c->opts.max_iters, c->opts);
     encode_zmap(nd, JC);
     nd.tile_base = 0;
+    nd.dtile_base = 0;
     nd.cta_base = 0;
     nd.prob_base = 0;
 
@@ -304,9 +308,11 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, bool sym, long long U, int
     g.JC = JC;
     g.pack = 3 * U < (1LL << 25);
     g.rlt1_only = !with_d;
-    g.sym = with_d && sym;
+    g.sym = sym;
+    g.paired = paired;
+    g.dtiles = nd.dtiles;
     // instances with N <= 16: D->C LAPs on half-warps unless opts ask for whole warps
-    g.small_tiles = with_d && N <= kSmallN && c->opts.lanes != 32 ? (int)nd.tiles : 0;
+    g.small_tiles = with_d && !paired && N <= kSmallN && c->opts.lanes != 32 ? (int)nd.tiles : 0;
     g.smallTS = nd.TS;
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
@@ -343,7 +349,7 @@ static rlt2_ctx *new_ctx(const rlt2_opts *opts)
 // the class sums (C(N,3) N^3 int32) and the tile duals (tiles x DS int32).
 struct CkptHeader {
     char magic[8];
-    int32_t version, N, with_d, iter, stop, sym;
+    int32_t version, N, with_d, iter, stop, store;
     int64_t LB, U, tiles, z_ints;
 };
 static const char kCkptMagic[8] = {'R', 'L', 'T', '2', 'C', 'K', 'P', 'T'};
@@ -383,12 +389,13 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
     rlt2_ctx *c = new_ctx(opts);
     if (!c) return RLT2_E_OOM;
     int32_t *stage = nullptr;
-    if ((c->opts.store != RLT2_STORE_TILES && c->opts.store != RLT2_STORE_CLASSES) ||
+    if ((c->opts.store != RLT2_STORE_TILES && c->opts.store != RLT2_STORE_CLASSES &&
+         c->opts.store != RLT2_STORE_PAIRS) ||
         (c->opts.lanes != 0 && c->opts.lanes != 16 && c->opts.lanes != 32)) {
         free_ctx(c);
         return RLT2_E_INVAL;
     }
-    rc = setup_ctx(c, N, !c->opts.rlt1_only, c->opts.store == RLT2_STORE_CLASSES, U, &stage);
+    rc = setup_ctx(c, N, !c->opts.rlt1_only, c->opts.store, U, &stage);
     if (rc != RLT2_OK) {
         free_ctx(c);
         return rc;
@@ -416,13 +423,15 @@ int rlt2_save(rlt2_ctx *c, const char *path)
     h.version = 1;
     h.N = nd.N;
     h.with_d = nd.p.z != nullptr || nd.p.T != nullptr;
-    h.sym = nd.p.T != nullptr;
+    h.store = nd.p.T ? RLT2_STORE_CLASSES : nd.paired ? RLT2_STORE_PAIRS : RLT2_STORE_TILES;
     h.iter = it;
     CK(cudaMemcpy(&h.stop, nd.p.stop, 4, cudaMemcpyDeviceToHost));
     h.LB = lb;
     h.U = c->U;
     h.tiles = nd.tiles;
-    h.z_ints = !h.with_d ? 0 : h.sym ? make_geom(nd.N).classes_ints + nd.tiles * nd.DS : nd.tiles * nd.TS;
+    h.z_ints = !h.with_d                     ? 0
+               : h.store == RLT2_STORE_CLASSES ? make_geom(nd.N).classes_ints + nd.tiles * nd.DS
+                                               : nd.dtiles * nd.TS;
     FILE *f = std::fopen(path, "wb");
     if (!f) return RLT2_E_IO;
     const int nh = std::min(it, c->opts.max_iters);
@@ -430,11 +439,12 @@ int rlt2_save(rlt2_ctx *c, const char *path)
     if (rc == RLT2_OK) rc = file_device(f, (char *)nd.p.hist, (size_t)nh * 8, true, c->stream);
     if (rc == RLT2_OK) rc = file_device(f, (char *)nd.p.x, (size_t)nd.N * nd.N * 4, true, c->stream);
     if (rc == RLT2_OK) rc = file_device(f, (char *)nd.p.yC, (size_t)nd.tiles * 4, true, c->stream);
-    if (rc == RLT2_OK && h.with_d && !h.sym)
+    const bool hsym = h.store == RLT2_STORE_CLASSES;
+    if (rc == RLT2_OK && h.with_d && !hsym)
         rc = file_device(f, (char *)nd.p.z, (size_t)h.z_ints * 4, true, c->stream);
-    if (rc == RLT2_OK && h.sym)
+    if (rc == RLT2_OK && hsym)
         rc = file_device(f, (char *)nd.p.T, (size_t)make_geom(nd.N).classes_ints * 4, true, c->stream);
-    if (rc == RLT2_OK && h.sym) rc = file_device(f, (char *)nd.p.du, (size_t)nd.tiles * nd.DS * 4, true, c->stream);
+    if (rc == RLT2_OK && hsym) rc = file_device(f, (char *)nd.p.du, (size_t)nd.tiles * nd.DS * 4, true, c->stream);
     if (std::fclose(f) != 0 && rc == RLT2_OK) rc = RLT2_E_IO;
     return rc;
 }
@@ -451,10 +461,13 @@ int rlt2_load(const char *path, const rlt2_opts *opts, rlt2_ctx **out)
     do {
         if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1 ||
             h.N < RLT2_MIN_N || h.N > RLT2_MAX_N || h.iter < 0 || h.U < 0 || h.U > RLT2_LAP_MAX_ENTRY ||
-            h.tiles != make_geom(h.N).tiles || (h.sym != 0 && h.sym != 1) || (h.sym && !h.with_d) ||
+            h.tiles != make_geom(h.N).tiles || h.store < RLT2_STORE_TILES || h.store > RLT2_STORE_PAIRS ||
+            (h.store != RLT2_STORE_TILES && !h.with_d) ||
             h.z_ints != (!h.with_d ? 0
-                         : h.sym ? make_geom(h.N).classes_ints + h.tiles * (long long)make_geom(h.N).DS
-                                 : h.tiles * (long long)make_geom(h.N).TS)) {
+                         : h.store == RLT2_STORE_CLASSES
+                             ? make_geom(h.N).classes_ints + h.tiles * (long long)make_geom(h.N).DS
+                         : h.store == RLT2_STORE_PAIRS ? make_geom(h.N).htiles * (long long)make_geom(h.N).TS
+                                                       : h.tiles * (long long)make_geom(h.N).TS)) {
             rc = RLT2_E_IO;
             break;
         }
@@ -464,24 +477,25 @@ int rlt2_load(const char *path, const rlt2_opts *opts, rlt2_ctx **out)
             break;
         }
         c->opts.rlt1_only = !h.with_d;
-        c->opts.store = h.sym ? RLT2_STORE_CLASSES : RLT2_STORE_TILES;
+        c->opts.store = h.store;
         if (h.iter > c->opts.max_iters) {  // the history must fit
             rc = RLT2_E_INVAL;
             break;
         }
         int32_t *stage = nullptr;
-        if ((rc = setup_ctx(c, h.N, h.with_d != 0, h.sym != 0, h.U, &stage)) != RLT2_OK) break;
+        if ((rc = setup_ctx(c, h.N, h.with_d != 0, h.store, h.U, &stage)) != RLT2_OK) break;
+        const bool hsym = h.store == RLT2_STORE_CLASSES;
         const NodeDesc &nd = c->node;
         if ((rc = file_device(f, (char *)nd.p.hist, (size_t)h.iter * 8, false, c->stream)) != RLT2_OK) break;
         if ((rc = file_device(f, (char *)nd.p.x, (size_t)h.N * h.N * 4, false, c->stream)) != RLT2_OK) break;
         if ((rc = file_device(f, (char *)nd.p.yC, (size_t)h.tiles * 4, false, c->stream)) != RLT2_OK) break;
-        if (h.with_d && !h.sym &&
+        if (h.with_d && !hsym &&
             (rc = file_device(f, (char *)nd.p.z, (size_t)h.z_ints * 4, false, c->stream)) != RLT2_OK)
             break;
-        if (h.sym && (rc = file_device(f, (char *)nd.p.T, (size_t)make_geom(h.N).classes_ints * 4, false,
+        if (hsym && (rc = file_device(f, (char *)nd.p.T, (size_t)make_geom(h.N).classes_ints * 4, false,
                                        c->stream)) != RLT2_OK)
             break;
-        if (h.sym &&
+        if (hsym &&
             (rc = file_device(f, (char *)nd.p.du, (size_t)h.tiles * nd.DS * 4, false, c->stream)) != RLT2_OK)
             break;
         cudaError_t e = cudaMemcpyAsync(nd.p.LB, &h.LB, 8, cudaMemcpyHostToDevice, c->stream);
@@ -573,7 +587,7 @@ int rlt2_get_state(rlt2_ctx *c, int level, int32_t *host, size_t count)
         // class-sum store is first expanded to that layout on the device
         std::vector<int32_t> tmp;
         try {
-            tmp.resize((size_t)nd.tiles * nd.TS);
+            tmp.resize((size_t)nd.dtiles * nd.TS);
         } catch (...) {
             return RLT2_E_OOM;
         }
@@ -597,8 +611,15 @@ int rlt2_get_state(rlt2_ctx *c, int level, int32_t *host, size_t count)
         size_t o = 0;
         for (long long t = 0; t < nd.tiles; t++) {
             const int nn = (int)(t % m), j = (int)((t / ((long long)m * m)) % N);
+            const int ij = (int)(t / ((long long)m * m)), i = ij / N, kk = (int)((t / m) % m);
+            const int k = kk + (kk >= i);
             const int nl = nn + (nn >= j);
-            const int32_t *src = tmp.data() + (size_t)t * nd.TS;
+            if (nd.paired && k < i) {  // pair store: the complement holds the pair, this tile is 0
+                for (int e = 0; e < n * n; e++) host[o++] = 0;
+                continue;
+            }
+            const long long ts = nd.paired ? ((long long)pair_index(i, k) * N + j) * m + nn : t;
+            const int32_t *src = tmp.data() + (size_t)ts * nd.TS;
             for (int r = 0; r < n; r++)
                 for (int q = 0; q < N; q++)
                     if (q != j && q != nl) host[o++] = src[r * W + q];
@@ -666,7 +687,7 @@ size_t rlt2_state_bytes(int N, int rlt1_only, int max_iters, int store)
     if (N < RLT2_MIN_N || N > RLT2_MAX_N) return 0;
     if (max_iters <= 0) max_iters = 65536;
     Arena a;
-    plan_node(a, N, !rlt1_only, store == RLT2_STORE_CLASSES, max_iters);
+    plan_node(a, N, !rlt1_only, store, max_iters);
     a.take(sizeof(NodeDesc));
     a.take((size_t)n_triples(N) * sizeof(int4));
     a.take(4);
@@ -730,7 +751,8 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     if (!out || !ctxs || count < 1) return RLT2_E_INVAL;
     *out = nullptr;
     for (int b = 0; b < count; b++)
-        if (!ctxs[b] || ctxs[b]->g.rlt1_only != ctxs[0]->g.rlt1_only || ctxs[b]->g.sym != ctxs[0]->g.sym)
+        if (!ctxs[b] || ctxs[b]->g.rlt1_only != ctxs[0]->g.rlt1_only || ctxs[b]->g.sym != ctxs[0]->g.sym ||
+            ctxs[b]->g.paired != ctxs[0]->g.paired)
             return RLT2_E_INVAL;
     rlt2_group *gr = new (std::nothrow) rlt2_group();
     if (!gr) return RLT2_E_OOM;
@@ -756,7 +778,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
         maxN = std::max(maxN, c->node.N);
         pack = pack && c->g.pack;
     }
-    const int JC = p1_chunk(maxN, ctxs[0]->g.sym);
+    const int JC = p1_chunk(maxN, ctxs[0]->g.sym, ctxs[0]->g.paired);
     const std::vector<int4> tri = triple_table(maxN);
     Arena a;
     const size_t o_nodes = a.take((size_t)count * sizeof(NodeDesc));
@@ -770,7 +792,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
         return fail(cuda_code(e));
     }
     // instances with N <= 16 first: their tiles form the half-warp range of D->C
-    bool halves = !ctxs[0]->g.rlt1_only;
+    bool halves = !ctxs[0]->g.rlt1_only && !ctxs[0]->g.paired;
     for (rlt2_ctx *c : gr->ctxs) halves = halves && c->opts.lanes != 32;
     std::vector<int> order(count);
     for (int b = 0; b < count; b++) order[b] = b;
@@ -779,7 +801,7 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
             return (gr->ctxs[x]->node.N <= kSmallN) > (gr->ctxs[y]->node.N <= kSmallN);
         });
     std::vector<NodeDesc> hn(count);
-    long long tiles = 0, small_tiles = 0;
+    long long tiles = 0, small_tiles = 0, dtiles = 0;
     int ctas = 0, probs = 0, maxTS = 0, smallTS = 4;
     for (int b = 0; b < count; b++) {
         NodeDesc &nd = hn[b];
@@ -787,6 +809,8 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
         fill_node(nd, nd.N, JC);           // the group's location chunk
         encode_zmap(nd, JC);
         nd.tile_base = tiles;
+        nd.dtile_base = dtiles;
+        dtiles += nd.dtiles;
         nd.cta_base = ctas;
         nd.prob_base = probs;
         tiles += nd.tiles;
@@ -813,6 +837,8 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     g.pack = pack;
     g.rlt1_only = ctxs[0]->g.rlt1_only;
     g.sym = ctxs[0]->g.sym;
+    g.paired = ctxs[0]->g.paired;
+    g.dtiles = dtiles;
     g.counter = reinterpret_cast<unsigned *>(gr->mem + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(gr->mem + o_st);
     g.triples = reinterpret_cast<const int4 *>(gr->mem + o_tri);
@@ -942,16 +968,16 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
         pack = pack && 3 * U < (1LL << 25);
         maxN = std::max(maxN, I.Np);
     }
-    if (o.store != RLT2_STORE_TILES && o.store != RLT2_STORE_CLASSES) return RLT2_E_INVAL;
-    const int JC = p1_chunk(maxN, o.store == RLT2_STORE_CLASSES);
+    if (o.store != RLT2_STORE_TILES && o.store != RLT2_STORE_CLASSES && o.store != RLT2_STORE_PAIRS)
+        return RLT2_E_INVAL;
+    const int JC = p1_chunk(maxN, o.store == RLT2_STORE_CLASSES, o.store == RLT2_STORE_PAIRS);
     const int hist_cap = std::max(iters, 1);
 
     // one allocation for the whole group
     Arena a;
     std::vector<NodeOffsets> no(B);
-    if (o.store != RLT2_STORE_TILES && o.store != RLT2_STORE_CLASSES) return RLT2_E_INVAL;
-    const bool sym = o.store == RLT2_STORE_CLASSES;
-    for (int b = 0; b < B; b++) no[b] = plan_node(a, in[b].Np, true, sym, hist_cap);
+    const bool sym = o.store == RLT2_STORE_CLASSES, paired = o.store == RLT2_STORE_PAIRS;
+    for (int b = 0; b < B; b++) no[b] = plan_node(a, in[b].Np, true, o.store, hist_cap);
     const std::vector<int4> tri = triple_table(maxN);
     const size_t o_nodes = a.take((size_t)B * sizeof(NodeDesc));
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
@@ -988,18 +1014,21 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return (in[x].Np <= kSmallN) > (in[y].Np <= kSmallN); });
     int ctas = 0, probs = 0, maxTS = 0, smallTS = 4;
-    long long small_tiles = 0;
+    long long small_tiles = 0, dtiles = 0;
     for (int b = 0; b < B; b++) {
         NodeDesc &nd = hn[b];
         const int ob = order[b];
+        nd.paired = paired;
         fill_node(nd, in[ob].Np, JC);
         nd.p = node_state(base, no[ob], hist_cap, o);
         encode_zmap(nd, JC);
-        if (nd.N <= kSmallN) {
+        if (nd.N <= kSmallN && !paired) {
             small_tiles += nd.tiles;
             smallTS = std::max(smallTS, nd.TS);
         }
         nd.tile_base = tiles;
+        nd.dtile_base = dtiles;
+        dtiles += nd.dtiles;
         nd.cta_base = ctas;
         nd.prob_base = probs;
         tiles += nd.tiles;
@@ -1018,6 +1047,8 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     g.pack = pack;
     g.rlt1_only = false;
     g.sym = sym;
+    g.paired = paired;
+    g.dtiles = dtiles;
     g.small_tiles = 0;
     g.smallTS = smallTS;
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);

@@ -30,6 +30,7 @@ struct Geom {
     int DS;           // class-sum store: ints of duals per tile, U0 + W
     long long tiles;  // N^2 (N-1)^2
     long long classes_ints;  // class-sum store: C(N,3) N^3 ints
+    long long htiles;        // pair store: the tiles with i < k, N (N-1)/2 * N (N-1)
 };
 
 inline Geom make_geom(int N)
@@ -43,6 +44,7 @@ inline Geom make_geom(int N)
     g.DS = g.U0 + g.W;
     g.tiles = (long long)N * N * (N - 1) * (N - 1);
     g.classes_ints = (long long)N * (N - 1) * (N - 2) / 6 * N * N * N;
+    g.htiles = g.tiles / 2;
     return g;
 }
 
@@ -94,6 +96,18 @@ __host__ __device__ inline int sym_member(int T, int rank)
     return q + (rank < T - 6 * q ? 1 : 0);
 }
 
+// Pair store (the complementary submatrices of Sec. 6 kept as one): the tile
+// D_ijkn with i < k holds the sum of D_ijkn and D_knij; its index is
+// th = (pair(i,k) N + j)(N-1) + n' with n' = n - (n > j) and pair(i,k) = C(k,2) + i.
+__host__ __device__ inline int pair_index(int i, int k) { return k * (k - 1) / 2 + i; }
+
+__host__ __device__ inline void pair_of(int idx, int &i, int &k)
+{
+    k = 1;
+    while ((k + 1) * k / 2 <= idx) ++k;  // k <= 63: at most 63 steps
+    i = idx - k * (k - 1) / 2;
+}
+
 // Device state of one instance.
 struct PassState {
     int *z;            // tile store of D (null without D or with the class-sum store)
@@ -120,12 +134,15 @@ struct NodeDesc {
     // and skipped on store).
     CUtensorMap zmap;     // class-sum store: the same box over the v part of the tile duals
     int zmap_ok;
+    int paired;           // D in the pair store (z holds the tiles with i < k)
     PassState p;
     int N, W, TS;
     int U0, DS;           // class-sum store: dual offsets (Geom)
     int nchunks;          // location chunks of the fused pass over D
-    long long tiles;
+    long long tiles;      // tiles of C (all (i,j,k,n))
     long long tile_base;  // first group-wide tile index of this instance
+    long long dtiles;     // D->C work units: tiles, or the pair store's htiles
+    long long dtile_base; // first group-wide D->C unit of this instance
     int cta_base;         // first fused-pass CTA of this instance
     int prob_base;        // first C->B problem of this instance
     FastDiv fN, fm, fmm, fn, fW4;
@@ -140,6 +157,7 @@ inline void fill_node(NodeDesc &d, int N, int JC)
     d.U0 = g.U0;
     d.DS = g.DS;
     d.tiles = g.tiles;
+    d.dtiles = d.paired ? g.htiles : g.tiles;  // d.paired is set by the caller first
     d.nchunks = (N + JC - 1) / JC;
     d.fN = make_fastdiv(N);
     d.fm = make_fastdiv(N - 1);
@@ -160,6 +178,8 @@ struct Group {
     bool pack;              // every instance's keys fit the packed reduction
     bool rlt1_only;
     bool sym;               // D in the class-sum store (every instance of the group)
+    bool paired;            // D in the pair store (every instance of the group)
+    long long dtiles;       // total D->C work units
     int small_tiles;        // D->C: the first small_tiles tiles (instances with N <= 16, which
                             // come first in the group) are solved two per warp, 16 lanes each
     int smallTS;            // largest tile stride (ints) among those instances
@@ -169,11 +189,12 @@ struct Group {
     NodeDesc first;         // copy of nodes[0]: kernels of a group of one read it as a parameter
 };
 
-int p1_chunk(int N, bool sym);         // locations per CTA of the fused pass over D
+int p1_chunk(int N, bool sym, bool paired);  // locations per CTA of the fused pass over D
 // Encode nd.zmap for the fused pass with location chunk JC (sets zmap_ok;
-// false leaves the pieces to per-piece copies).  nd.p.z and the geometry must be set.
+// false leaves the pieces to per-piece copies).  nd.p.z (or du), nd.paired
+// and the geometry must be set.
 bool encode_zmap(NodeDesc &nd, int JC);
-size_t p1_smem_bytes(int N, int JC, bool sym);  // its dynamic shared memory
+size_t p1_smem_bytes(int N, int JC, bool sym, bool paired);  // its dynamic shared memory
 
 // Initialise instance `node` of the group (index b) from device copies of its
 // F, D and linear costs (Blin may be null).

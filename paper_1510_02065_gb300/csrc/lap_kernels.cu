@@ -28,7 +28,10 @@ constexpr int kBatchWarps = 4;
 // false if the copy did not complete within the spin limit (recorded in
 // status; the copy in flight has landed or been waited for, bounded).
 // SEG = 16: the calling half-warp solves the tile (N <= 16), lane = its lane in the half.
-template <int NS, bool PACK, int SEG = 32>
+// PAIR: t indexes the pair store (tiles with i < k holding the sum of the two
+// complementary submatrices); S goes to c_ijkn and c_knij, which receives no
+// concentration, is set to 0 (everything it had was spread to D).
+template <int NS, bool PACK, int SEG = 32, bool PAIR = false>
 __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *buf, uint64_t *bar,
                                           unsigned &parity, int lane, unsigned &steps, unsigned &relax,
                                           DevStatus *status)
@@ -48,10 +51,24 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
     parity ^= 1u;
 
     // the tile's own locations j and n are the columns without coefficient
-    const unsigned ij = fdiv(t, nd.fmm);
-    const unsigned rem = t - ij * (unsigned)(m * m);
-    const int nn = (int)(rem - fdiv(rem, nd.fm) * (unsigned)m);
-    const int j = (int)(ij - fdiv(ij, nd.fN) * (unsigned)N);
+    int j, nn;
+    unsigned tf = t, tlow = 0;  // tile of C receiving S; PAIR: the complement's
+    if constexpr (PAIR) {
+        const unsigned pj = fdiv(t, nd.fm);  // t = (pair * N + j) * m + n'
+        nn = (int)(t - pj * (unsigned)m);
+        const unsigned pr = fdiv(pj, nd.fN);
+        j = (int)(pj - pr * (unsigned)N);
+        int i, k;
+        pair_of((int)pr, i, k);
+        const int nl0 = nn + (nn >= j);
+        tf = (((unsigned)i * N + j) * m + (k - 1)) * m + nn;                          // (i,j,k,n), k' = k - 1
+        tlow = (((unsigned)k * N + nl0) * m + i) * m + (unsigned)(j - (j > nl0));       // (k,n,i,j), i' = i
+    } else {
+        const unsigned ij = fdiv(t, nd.fmm);
+        const unsigned rem = t - ij * (unsigned)(m * m);
+        nn = (int)(rem - fdiv(rem, nd.fm) * (unsigned)m);
+        j = (int)(ij - fdiv(ij, nd.fN) * (unsigned)N);
+    }
     const int nl = nn + (nn >= j);
     int rowOf[NS], uM[NS], v[NS];
     if (!warp_hungarian<NS, PACK, SEG>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
@@ -69,7 +86,10 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
         }
     }
     const long long S = lap_value<NS, SEG>(N, j, nl, uM, v);
-    if (lane == 0) nd.p.yS[t] = (int)S;
+    if (lane == 0) {
+        nd.p.yS[tf] = (int)S;
+        if constexpr (PAIR) nd.p.yS[tlow] = 0;
+    }
     // the generic writes of column j above precede the next tile's bulk copy
     // into this buffer (async proxy)
     fence_proxy_async_smem();
@@ -165,9 +185,11 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
 // instance): the instance is the kernel parameter g.first, read from
 // parameter space, and the stopping rule is checked once.  Every CTA size
 // caps registers at 32 per thread (64 warps per SM).
-template <int NS, bool PACK, bool ONE, bool SYM, int WARPS>
+// MODE: 0 tile store, 1 class-sum store, 2 pair store (work units: its tiles).
+template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 64 / WARPS) dlap_kernel(Group g)
 {
+    constexpr bool SYM = MODE == 1, PAIR = MODE == 2;
     if (ONE && *g.first.p.stop) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -183,10 +205,10 @@ __global__ void __launch_bounds__(WARPS * 32, 64 / WARPS) dlap_kernel(Group g)
 
     unsigned parity = 0;
     unsigned steps = 0, relax = 0, laps = 0;
-    const unsigned ntiles = (unsigned)g.tiles;  // < 2^31 for any group the host accepts
+    const unsigned ntiles = (unsigned)g.dtiles;  // < 2^31 for any group the host accepts
     int b = 0;
     for (;;) {
-        unsigned T = 0;  // tiles [0, small_tiles) are the half-warp kernel's
+        unsigned T = 0;  // units [0, small_tiles) are the half-warp kernel's
         if (lane == 0) T = atomicAdd(g.counter, 1u) + (unsigned)g.small_tiles;
         T = __shfl_sync(kFull, T, 0);
         if (T >= ntiles) break;
@@ -194,20 +216,20 @@ __global__ void __launch_bounds__(WARPS * 32, 64 / WARPS) dlap_kernel(Group g)
         if constexpr (SYM && ONE) {
             ok = dlap_tile_sym<NS, PACK>(g.first, T, buf, lane, steps, relax, g.status);
         } else if constexpr (SYM) {
-            if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
-                b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
+            if (T < (unsigned)g.nodes[b].dtile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].dtile_base))
+                b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.dtile_base; });
             const NodeDesc &nd = g.nodes[b];
             if (*nd.p.stop) continue;
-            ok = dlap_tile_sym<NS, PACK>(nd, T - (unsigned)nd.tile_base, buf, lane, steps, relax, g.status);
+            ok = dlap_tile_sym<NS, PACK>(nd, T - (unsigned)nd.dtile_base, buf, lane, steps, relax, g.status);
         } else if constexpr (ONE) {
-            ok = dlap_tile<NS, PACK>(g.first, T, buf, bar, parity, lane, steps, relax, g.status);
+            ok = dlap_tile<NS, PACK, 32, PAIR>(g.first, T, buf, bar, parity, lane, steps, relax, g.status);
         } else {
-            if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
-                b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
+            if (T < (unsigned)g.nodes[b].dtile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].dtile_base))
+                b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.dtile_base; });
             const NodeDesc &nd = g.nodes[b];
             if (*nd.p.stop) continue;
-            ok = dlap_tile<NS, PACK>(nd, T - (unsigned)nd.tile_base, buf, bar, parity, lane, steps, relax,
-                                     g.status);
+            ok = dlap_tile<NS, PACK, 32, PAIR>(nd, T - (unsigned)nd.dtile_base, buf, bar, parity, lane, steps,
+                                               relax, g.status);
         }
         if (!ok) return;
         ++laps;
@@ -259,11 +281,11 @@ __global__ void __launch_bounds__(kDlap16Warps * 32, 64 / kDlap16Warps) dlap16_k
                 else ok = dlap_tile<1, PACK, 16>(g.first, T, buf, bar, parity, hl, steps, relax, g.status);
                 laps += ok;
             } else {
-                if (T < (unsigned)g.nodes[b].tile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].tile_base))
-                    b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.tile_base; });
+                if (T < (unsigned)g.nodes[b].dtile_base || (b + 1 < g.B && T >= (unsigned)g.nodes[b + 1].dtile_base))
+                    b = find_node(g.nodes, g.B, T, [](const NodeDesc &d) { return d.dtile_base; });
                 const NodeDesc &nd = g.nodes[b];
                 if (!*nd.p.stop) {
-                    const unsigned t = T - (unsigned)nd.tile_base;
+                    const unsigned t = T - (unsigned)nd.dtile_base;
                     if constexpr (SYM) ok = dlap_tile_sym<1, PACK, 16>(nd, t, buf, hl, steps, relax, g.status);
                     else ok = dlap_tile<1, PACK, 16>(nd, t, buf, bar, parity, hl, steps, relax, g.status);
                     laps += ok;
@@ -451,11 +473,11 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
 // ---------------------------------------------------------------- launchers
 
 // Resident warps per SM of the D->C kernel with CTAs of WARPS warps.
-template <int NS, bool PACK, bool ONE, bool SYM, int WARPS>
+template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
 static cudaError_t dlap_fit(const Group &g, int &warps_per_sm)
 {
     const size_t smem = (size_t)WARPS * ((size_t)g.maxTS * 4 + 8);
-    auto k = dlap_kernel<NS, PACK, ONE, SYM, WARPS>;
+    auto k = dlap_kernel<NS, PACK, ONE, MODE, WARPS>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -464,45 +486,45 @@ static cudaError_t dlap_fit(const Group &g, int &warps_per_sm)
     return e;
 }
 
-template <int NS, bool PACK, bool ONE, bool SYM, int WARPS>
+template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
 static cudaError_t dlap_run(const Group &g, int sm_count, cudaStream_t s)
 {
     const size_t smem = (size_t)WARPS * ((size_t)g.maxTS * 4 + 8);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dlap_kernel<NS, PACK, ONE, SYM, WARPS>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dlap_kernel<NS, PACK, ONE, MODE, WARPS>,
                                                                   WARPS * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)per_sm * sm_count;
-    const long long need = (g.tiles + WARPS - 1) / WARPS;
+    const long long need = (g.dtiles + WARPS - 1) / WARPS;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    dlap_kernel<NS, PACK, ONE, SYM, WARPS><<<(unsigned)grid, WARPS * 32, smem, s>>>(g);
+    dlap_kernel<NS, PACK, ONE, MODE, WARPS><<<(unsigned)grid, WARPS * 32, smem, s>>>(g);
     return cudaGetLastError();
 }
 
 // CTA size: the one of 4, 16 or 32 warps that keeps the most warps resident
 // (shared memory decides: at N = 30 two CTAs of 32 warps fit where fourteen
 // of 4 do), the smaller on a tie.
-template <int NS, bool PACK, bool ONE, bool SYM>
+template <int NS, bool PACK, bool ONE, int MODE>
 static cudaError_t dlap_go(const Group &g, int sm_count, cudaStream_t s)
 {
     int w4 = 0, w16 = 0, w32 = 0;
     cudaError_t e;
-    if ((e = dlap_fit<NS, PACK, ONE, SYM, 4>(g, w4)) != cudaSuccess) return e;
-    if ((e = dlap_fit<NS, PACK, ONE, SYM, 16>(g, w16)) != cudaSuccess) return e;
-    if ((e = dlap_fit<NS, PACK, ONE, SYM, 32>(g, w32)) != cudaSuccess) return e;
-    if (w32 > w4 && w32 > w16) return dlap_run<NS, PACK, ONE, SYM, 32>(g, sm_count, s);
-    if (w16 > w4) return dlap_run<NS, PACK, ONE, SYM, 16>(g, sm_count, s);
-    return dlap_run<NS, PACK, ONE, SYM, 4>(g, sm_count, s);
+    if ((e = dlap_fit<NS, PACK, ONE, MODE, 4>(g, w4)) != cudaSuccess) return e;
+    if ((e = dlap_fit<NS, PACK, ONE, MODE, 16>(g, w16)) != cudaSuccess) return e;
+    if ((e = dlap_fit<NS, PACK, ONE, MODE, 32>(g, w32)) != cudaSuccess) return e;
+    if (w32 > w4 && w32 > w16) return dlap_run<NS, PACK, ONE, MODE, 32>(g, sm_count, s);
+    if (w16 > w4) return dlap_run<NS, PACK, ONE, MODE, 16>(g, sm_count, s);
+    return dlap_run<NS, PACK, ONE, MODE, 4>(g, sm_count, s);
 }
 
-template <bool ONE, bool SYM>
+template <bool ONE, int MODE>
 static cudaError_t dlap_pick(const Group &g, int sm_count, cudaStream_t s)
 {
     if (g.maxN <= 32)
-        return g.pack ? dlap_go<1, true, ONE, SYM>(g, sm_count, s) : dlap_go<1, false, ONE, SYM>(g, sm_count, s);
-    return g.pack ? dlap_go<2, true, ONE, SYM>(g, sm_count, s) : dlap_go<2, false, ONE, SYM>(g, sm_count, s);
+        return g.pack ? dlap_go<1, true, ONE, MODE>(g, sm_count, s) : dlap_go<1, false, ONE, MODE>(g, sm_count, s);
+    return g.pack ? dlap_go<2, true, ONE, MODE>(g, sm_count, s) : dlap_go<2, false, ONE, MODE>(g, sm_count, s);
 }
 
 template <bool PACK, bool ONE, bool SYM>
@@ -537,14 +559,15 @@ static cudaError_t dlap16_any(const Group &g, int sm_count, cudaStream_t s)
 
 static cudaError_t dlap_any(const Group &g, int sm_count, cudaStream_t s)
 {
-    if (g.sym) return g.B == 1 ? dlap_pick<true, true>(g, sm_count, s) : dlap_pick<false, true>(g, sm_count, s);
-    return g.B == 1 ? dlap_pick<true, false>(g, sm_count, s) : dlap_pick<false, false>(g, sm_count, s);
+    if (g.sym) return g.B == 1 ? dlap_pick<true, 1>(g, sm_count, s) : dlap_pick<false, 1>(g, sm_count, s);
+    if (g.paired) return g.B == 1 ? dlap_pick<true, 2>(g, sm_count, s) : dlap_pick<false, 2>(g, sm_count, s);
+    return g.B == 1 ? dlap_pick<true, 0>(g, sm_count, s) : dlap_pick<false, 0>(g, sm_count, s);
 }
 
 cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s, const SideStream *side)
 {
     if (g.small_tiles <= 0) return dlap_any(g, sm_count, s);
-    if (g.small_tiles >= g.tiles) return dlap16_any(g, sm_count, s);
+    if (g.small_tiles >= g.dtiles) return dlap16_any(g, sm_count, s);
     cudaError_t e;
     if (!side) {
         if ((e = dlap16_any(g, sm_count, s)) != cudaSuccess) return e;

@@ -64,7 +64,8 @@ struct P1Layout {
 
 __host__ __device__ inline int up4(int x) { return (x + 3) & ~3; }
 
-__host__ __device__ inline P1Layout p1_layout(int N, int W, int JC, bool sym)
+// paired: the pair store's pass moves only kinds 1, 2 and 4 (A3, A5, A6 empty).
+__host__ __device__ inline P1Layout p1_layout(int N, int W, int JC, bool sym, bool paired = false)
 {
     P1Layout L;
     L.S13 = W;
@@ -73,12 +74,12 @@ __host__ __device__ inline P1Layout p1_layout(int N, int W, int JC, bool sym)
     L.H6p = N | 1;
     int o = 0;
     L.A1 = o; o += JC * N * L.S13;
-    L.A3 = o; o += JC * N * L.S13;
+    L.A3 = o; o += paired ? 0 : JC * N * L.S13;
     L.A2 = o; o += JC * N * L.S25;
-    L.A5 = o; o += JC * N * L.S25;
+    L.A5 = o; o += paired ? 0 : JC * N * L.S25;
     o = (o + 31) & ~31;  // tensor-copy destinations on 128-byte boundaries
     L.A4 = o; o += (N * L.P46 + 31) & ~31;
-    L.A6 = o; o += up4(N * L.P46);
+    L.A6 = o; o += paired ? 0 : up4(N * L.P46);
     L.H1 = o; o += up4(JC * N);
     L.H3 = o; o += up4(JC * N);
     L.H2 = o; o += up4(JC * N);
@@ -91,7 +92,10 @@ __host__ __device__ inline P1Layout p1_layout(int N, int W, int JC, bool sym)
     return L;
 }
 
-size_t p1_smem_bytes(int N, int JC, bool sym) { return (size_t)p1_layout(N, up4(N), JC, sym).total * 4; }
+size_t p1_smem_bytes(int N, int JC, bool sym, bool paired)
+{
+    return (size_t)p1_layout(N, up4(N), JC, sym, paired).total * 4;
+}
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
@@ -126,9 +130,19 @@ bool encode_zmap(NodeDesc &nd, int JC)
     // every tile as (column, -, n', k', i*N + j) with the tile's dual stride
     const cuuint64_t R = nd.p.z ? W : (cuuint64_t)nd.DS;  // ints per row step
     const cuuint64_t rows = nd.p.z ? n : 1;
-    const cuuint64_t dim[5] = {W, rows, m, m, N * N};
-    const cuuint64_t stride[4] = {R * 4, R * rows * 4, R * rows * m * 4, R * rows * m * m * 4};
-    const cuuint32_t box[5] = {4, 1, (cuuint32_t)(m | 1), 1, (cuuint32_t)N};
+    cuuint64_t dim[5] = {W, rows, m, m, N * N};
+    cuuint64_t stride[4] = {R * 4, R * rows * 4, R * rows * m * 4, R * rows * m * m * 4};
+    cuuint32_t box[5] = {4, 1, (cuuint32_t)(m | 1), 1, (cuuint32_t)N};
+    if (nd.paired) {
+        // pair store: (column, row, n', j, pair(i,k)); the box takes every
+        // location a of the first facility: (4, 1, m|1, N, 1)
+        dim[3] = N;
+        dim[4] = N * (N - 1) / 2;
+        stride[2] = W * n * m * 4;
+        stride[3] = W * n * m * N * 4;
+        box[3] = (cuuint32_t)N;
+        box[4] = 1;
+    }
     const cuuint32_t estride[5] = {1, 1, 1, 1, 1};
     void *base = nd.p.z ? (void *)nd.p.z : (void *)(nd.p.du + nd.U0);
     if (fn(&nd.zmap, CU_TENSOR_MAP_DATA_TYPE_INT32, 5, base, dim, stride, box, estride,
@@ -139,12 +153,12 @@ bool encode_zmap(NodeDesc &nd, int JC)
     return true;
 }
 
-int p1_chunk(int N, bool sym)
+int p1_chunk(int N, bool sym, bool paired)
 {
 #ifdef RLT2_P1_JC
-    if (p1_smem_bytes(N, RLT2_P1_JC, sym) <= 200 * 1024) return RLT2_P1_JC;  // build-time override
+    if (p1_smem_bytes(N, RLT2_P1_JC, sym, paired) <= 200 * 1024) return RLT2_P1_JC;  // build-time override
 #endif
-    for (int jc : {4, 2}) if (p1_smem_bytes(N, jc, sym) <= 112 * 1024) return jc;
+    for (int jc : {4, 2}) if (p1_smem_bytes(N, jc, sym, paired) <= 112 * 1024) return jc;
     return 1;
 }
 
@@ -397,6 +411,133 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
     bulk_wait_read_all();  // shared memory stays valid until the bulk stores have read it
 }
 
+// Tile of the pair store holding D_abcd (a < c): ((pair(a,c) N + b)(N-1) + d').
+__device__ __forceinline__ int tidx_h(int N, int a, int b, int c, int d)
+{
+    return ((pair_index(a, c) * N + b) * (N - 1)) + (d - (d > b));
+}
+
+// The same pass for the pair store (reading of Sec. 6's complementary
+// submatrices): of each class only the members of tiles whose first facility
+// is below the second exist -- kind 1 (tile (i,j,k,n), row p), kind 2 (tile
+// (i,j,p,q), row k) and kind 4 (tile (k,n,p,q), row i) -- each holding the sum
+// with its complement (kinds 3, 5 and 6), whose c' shares it also receives;
+// the class sum is split equally over the three, in lexicographic order.
+template <int JC, bool ONE>
+__global__ void __launch_bounds__(kP1Threads, 2) p1_pair_kernel(const __grid_constant__ Group g)
+{
+    if (blockIdx.x == 0 && threadIdx.x < 2) g.counter[threadIdx.x] = 0;  // work counters of the D -> C sweep
+    const NodeDesc &nd =
+        ONE ? g.first
+            : g.nodes[find_node(g.nodes, g.B, blockIdx.x, [](const NodeDesc &d) { return (long long)d.cta_base; })];
+    const PassState p = nd.p;
+    if (*p.stop) return;
+    const int N = nd.N, W = nd.W, nchunks = nd.nchunks;
+    const FastDiv fN = nd.fN, fn = nd.fn;
+    const int bid = blockIdx.x - nd.cta_base;
+    extern __shared__ __align__(128) int sm[];
+    const P1Layout L = p1_layout(N, W, JC, false, true);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t TS = (size_t)(N - 2) * W;
+    const int4 tr = g.triples[bid / nchunks];
+    const int i = tr.x, k = tr.y, pp = tr.z;
+    const int j0 = (bid % nchunks) * JC;
+    const int jc = min(JC, N - j0);
+    int *__restrict__ z = p.z;
+    const int NN = N * N;
+
+    __shared__ __align__(8) uint64_t bar;
+    const bool tma = JC == 4 && nd.zmap_ok;
+    const void *zmap = &nd.zmap;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (!ONE && tma) tensormap_acquire(zmap);
+    }
+    __syncthreads();
+    const unsigned rowBytes = (unsigned)W * 4u;
+    if (threadIdx.x == 0) {
+        const unsigned pieceBytes = tma ? (unsigned)(N * L.P46) * 4u : 0u;
+        mbar_arrive_expect_tx(&bar, (unsigned)(2 * jc * (N - 1)) * rowBytes + pieceBytes);
+        if (tma) tensor_load5(sm + L.A4, zmap, j0, i, 0, 0, pair_index(k, pp), &bar);  // kind 4: tiles (k,a,p,l), row i
+    }
+    for (int e = threadIdx.x; e < 2 * JC * N; e += kP1Threads) {
+        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
+        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
+        if (jj >= jc || x == j) continue;
+        // kind 1: tile (i,j,k,x) row p; kind 2: tile (i,j,p,x) row k
+        const int t = q == 0 ? tidx_h(N, i, j, k, x) : tidx_h(N, i, j, pp, x);
+        const int row = q == 0 ? pp - 2 : k - 1;
+        int *dst = q == 0 ? sm + L.A1 + (jj * N + x) * L.S13 : sm + L.A2 + (jj * N + x) * L.S25;
+        bulk_load_tx(dst, z + t * TS + (size_t)row * W, rowBytes, &bar);
+    }
+    for (int e = tma ? NN : threadIdx.x; e < NN; e += kP1Threads) {
+        const int a = (int)fdiv((unsigned)e, fN), l = e - a * N;
+        if (l == a) continue;
+        cp_async_piece<JC>(sm + L.A4 + a * L.P46 + (l - (l > a)) * JC,
+                           z + (size_t)tidx_h(N, k, a, pp, l) * TS + (size_t)i * W + j0);
+    }
+    // c' of all six member tiles (the complements' shares join their pairs)
+    p1_gather_c<JC, false>(L, N, i, k, pp, j0, jc, fN, p.yS, nullptr, 0, sm);
+
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (__syncthreads_or(!mbar_wait(&bar, 0))) {
+        if (threadIdx.x == 0) atomicOr(&g.status->err, kDevTimeout);
+        mbar_wait(&bar, 0);
+        __syncthreads();
+        return;
+    }
+    p1_shares<false>(L, N, i, k, pp, fn, sm);
+    __syncthreads();
+
+    for (int nn = warp; nn < N; nn += kP1Warps) {
+        const int *h4 = sm + L.H4 + nn * N, *h6 = sm + L.H6 + nn;
+        for (int qq = lane; qq < N; qq += 32) {
+            if (qq == nn) continue;
+            int *a4 = sm + L.A4 + nn * L.P46 + (qq - (qq > nn)) * JC;   // piece (nn, qq)
+            int p4[JC];
+            load_piece<JC>(p4, a4);
+            const int h46 = h4[qq] + h6[qq * L.H6p];
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj) {
+                const int j = j0 + jj;
+                if (jj >= jc || j == nn || j == qq) continue;
+                const int rn = jj * N + nn, rq = jj * N + qq;
+                int *a1 = sm + L.A1 + rn * L.S13 + qq;
+                int *a2 = sm + L.A2 + rq * L.S25 + nn;
+                const int T = *a1 + sm[L.H1 + rn] + sm[L.H3 + rn] + *a2 + sm[L.H2 + rq] + sm[L.H5 + rq] +
+                              p4[jj] + h46;
+                const int q3 = T / 3, rm = T - 3 * q3;
+                *a1 = q3 + (0 < rm);      // d_ijknpq, d_ijpqkn, d_knpqij in lexicographic order
+                *a2 = q3 + (1 < rm);
+                p4[jj] = q3 + (2 < rm);
+            }
+            store_piece<JC>(a4, p4);
+        }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+
+    for (int e = threadIdx.x; e < 2 * JC * N; e += kP1Threads) {
+        const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
+        const int q = qj / JC, jj = qj % JC, j = j0 + jj;
+        if (jj >= jc || x == j) continue;
+        const int t = q == 0 ? tidx_h(N, i, j, k, x) : tidx_h(N, i, j, pp, x);
+        const int row = q == 0 ? pp - 2 : k - 1;
+        const int *src = q == 0 ? sm + L.A1 + (jj * N + x) * L.S13 : sm + L.A2 + (jj * N + x) * L.S25;
+        bulk_store(z + t * TS + (size_t)row * W, src, rowBytes);
+    }
+    if (tma && threadIdx.x == 0) tensor_store5(zmap, j0, i, 0, 0, pair_index(k, pp), sm + L.A4);
+    bulk_commit();
+    for (int e = tma ? NN : threadIdx.x; e < NN; e += kP1Threads) {
+        const int a = (int)fdiv((unsigned)e, fN), l = e - a * N;
+        if (l == a) continue;
+        copy_piece<JC>(z + (size_t)tidx_h(N, k, a, pp, l) * TS + (size_t)i * W + j0,
+                       sm + L.A4 + a * L.P46 + (l - (l > a)) * JC);
+    }
+    bulk_wait_read_all();  // shared memory stays valid until the bulk stores have read it
+}
+
 // The same pass for an instance in the class-sum store.  The reduced cost of a
 // member is (its value from the class sum) - u_row - v_col of its tile's last
 // LAP, and the six values of a class sum back to T (the split is lossless), so
@@ -600,7 +741,7 @@ cudaError_t launch_init(const NodeDesc &nd, const int32_t *F, const int32_t *D,
 {
     const PassState &p = nd.p;
     cudaError_t e = cudaSuccess;
-    if (p.z) e = cudaMemsetAsync(p.z, 0, (size_t)nd.tiles * nd.TS * 4, s);
+    if (p.z) e = cudaMemsetAsync(p.z, 0, (size_t)nd.dtiles * nd.TS * 4, s);
     if (e == cudaSuccess && p.T) e = cudaMemsetAsync(p.T, 0, (size_t)make_geom(nd.N).classes_ints * 4, s);
     if (e == cudaSuccess && p.du) e = cudaMemsetAsync(p.du, 0, (size_t)nd.tiles * nd.DS * 4, s);
     if (e != cudaSuccess) return e;
@@ -618,9 +759,10 @@ cudaError_t launch_init(const NodeDesc &nd, const int32_t *F, const int32_t *D,
 template <int JC>
 static cudaError_t p1_go(const Group &g, cudaStream_t s)
 {
-    const size_t smem = p1_smem_bytes(g.maxN, JC, g.sym);
-    auto k = g.sym ? (g.B == 1 ? p1_sym_kernel<JC, true> : p1_sym_kernel<JC, false>)
-                   : (g.B == 1 ? p1_kernel<JC, true> : p1_kernel<JC, false>);
+    const size_t smem = p1_smem_bytes(g.maxN, JC, g.sym, g.paired);
+    auto k = g.sym      ? (g.B == 1 ? p1_sym_kernel<JC, true> : p1_sym_kernel<JC, false>)
+             : g.paired ? (g.B == 1 ? p1_pair_kernel<JC, true> : p1_pair_kernel<JC, false>)
+                        : (g.B == 1 ? p1_kernel<JC, true> : p1_kernel<JC, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<g.ctas, kP1Threads, smem, s>>>(g);

@@ -30,6 +30,7 @@ RLT2_E_INTERNAL = -7
 RLT2_E_IO = -8
 RLT2_STORE_TILES = 0
 RLT2_STORE_CLASSES = 1
+RLT2_STORE_PAIRS = 2
 RLT2_MIN_N = 3
 RLT2_MAX_N = 64
 RLT2_LAP_MAX_ENTRY = 536870911

@@ -54,7 +54,7 @@ def gpu():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("store", [rlt2.RLT2_STORE_TILES, rlt2.RLT2_STORE_CLASSES])
+@pytest.mark.parametrize("store", [rlt2.RLT2_STORE_TILES, rlt2.RLT2_STORE_CLASSES, rlt2.RLT2_STORE_PAIRS])
 def test_batch_equals_single_contexts_and_oracle(gpu, orc, store):
     F, D = I.clustered_euclid(12, seed=3)
     nodes = []
@@ -67,10 +67,10 @@ def test_batch_equals_single_contexts_and_oracle(gpu, orc, store):
     assert ms > 0
     for b, (fac, loc) in enumerate(nodes):
         Fp, Dp, Bl, cst = rlt2.rlt2_subproblem(F, D, fac, loc)
-        with rlt2.Context(Fp, Dp, B_lin=Bl, lb_const=cst) as ctx:
+        with rlt2.Context(Fp, Dp, B_lin=Bl, lb_const=cst, store=store) as ctx:
             ctx.iterate(iters)
             assert ctx.bound()[1] == lbs[b], b
-        st = orc.State(Fp, Dp, B_lin=Bl, lb_const=cst)
+        st = orc.State(Fp, Dp, B_lin=Bl, lb_const=cst, paired=store == rlt2.RLT2_STORE_PAIRS)
         assert st.run(iters)[-1] == lbs[b], b
 
 

@@ -29,12 +29,13 @@ def gpu():
 @pytest.mark.gpu
 @pytest.mark.parametrize("name,rlt1_only,store", [("grid_n12", False, rlt2.RLT2_STORE_TILES),
                                                   ("grid_n12", False, rlt2.RLT2_STORE_CLASSES),
+                                                  ("grid_n12", False, rlt2.RLT2_STORE_PAIRS),
                                                   ("uniform_n8", True, rlt2.RLT2_STORE_TILES)])
 def test_resume_continues_exactly(gpu, orc, tmp_path, name, rlt1_only, store):
     F, D, _ = I.instance(name)
     N = F.shape[0]
     path = str(tmp_path / "ck.rlt2")
-    st = orc.State(F, D, rlt1_only=rlt1_only)
+    st = orc.State(F, D, rlt1_only=rlt1_only, paired=store == rlt2.RLT2_STORE_PAIRS)
     for _ in range(7):
         st.iterate()
     with rlt2.Context(F, D, rlt1_only=rlt1_only, max_iters=20, store=store) as ctx:

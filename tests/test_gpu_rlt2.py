@@ -202,13 +202,14 @@ def _conservation_sample(F, D, N, LB, x, y, z, perms):
 
 
 def _first_pass_then_properties(orc, F, D, N, seed, store=rlt2.RLT2_STORE_TILES):
+    paired = store == rlt2.RLT2_STORE_PAIRS
     """First pass against the oracle (LB, all of B and C, 200,000 sampled D
     entries), then three passes checked through properties that hold at any
     size: non-negative reduced costs, monotone LB, conservation on 100
     sampled permutations."""
     rng = np.random.default_rng(seed)
     perms = [rng.permutation(N) for _ in range(100)]
-    st = orc.State(F, D)
+    st = orc.State(F, D, paired=paired)
     with rlt2.Context(F, D, store=store) as ctx:
         ctx.iterate(1)
         st.iterate()
@@ -317,7 +318,7 @@ def test_stores_agree_and_sizes(gpu, orc):
 def test_unknown_store_rejected(gpu):
     F, D = I.uniform_symmetric(6, seed=1)
     with pytest.raises(rlt2.Rlt2Error) as e:
-        rlt2.Context(F, D, store=2)
+        rlt2.Context(F, D, store=3)
     assert e.value.code == rlt2.RLT2_E_INVAL
 
 
@@ -346,3 +347,100 @@ def test_unknown_lanes_rejected(gpu):
     with pytest.raises(rlt2.Rlt2Error) as e:
         rlt2.Context(F, D, lanes=8)
     assert e.value.code == rlt2.RLT2_E_INVAL
+
+
+
+# ------------------------------------------------------------ pair store
+
+PAIRS = rlt2.RLT2_STORE_PAIRS
+
+
+@pytest.mark.parametrize("name", ["uniform_n8", "grid_n12"])
+def test_pairs_full_state_every_pass(gpu, orc, name):
+    """The pair store (complementary submatrices of Sec. 6) against the
+    oracle's paired form: B, C, D (pair sums in the tiles with i < k, zeros in
+    the others) and LB after every pass, and the D->C work (half the LAPs)."""
+    F, D, iters = I.instance(name)
+    st = orc.State(F, D, paired=True)
+    with rlt2.Context(F, D, store=PAIRS) as ctx:
+        for t in range(min(iters, 20)):
+            ctx.iterate(1)
+            st.iterate()
+            assert_same_state(ctx, st, "after pass %d" % (t + 1))
+        w, ow = ctx.work(), st.work()
+        assert (w["laps"], w["steps"], w["relaxations"]) == (ow["laps"], ow["steps"], ow["relaxations"])
+
+
+@pytest.mark.parametrize("N,seed", [(3, 0), (4, 1), (5, 2), (6, 3), (7, 4)])
+def test_pairs_small_ragged_with_linear_term(gpu, orc, N, seed):
+    rng = np.random.default_rng(seed + 50)
+    F = rng.integers(0, 12, size=(N, N)).astype(np.int32)
+    D = rng.integers(0, 12, size=(N, N)).astype(np.int32)
+    Bl = rng.integers(0, 40, size=(N, N)).astype(np.int32)
+    st = orc.State(F, D, B_lin=Bl, lb_const=5, paired=True)
+    with rlt2.Context(F, D, B_lin=Bl, lb_const=5, store=PAIRS, use_graph=(seed % 2 == 1)) as ctx:
+        for t in range(6):
+            ctx.iterate(1)
+            st.iterate()
+            assert_same_state(ctx, st, "after pass %d" % (t + 1))
+
+
+def test_pairs_clustered_n20(gpu, orc):
+    F, D, _ = I.instance("clustered_n20")
+    st = orc.State(F, D, paired=True)
+    with rlt2.Context(F, D, store=PAIRS) as ctx:
+        for t in range(3):
+            ctx.iterate(1)
+            st.iterate()
+            assert_same_state(ctx, st, "after pass %d" % (t + 1))
+
+
+@pytest.mark.slow
+def test_pairs_headline_n30(gpu, orc):
+    F, D, _ = I.instance("clustered_n30")
+    _first_pass_then_properties(orc, F, D, 30, 31, PAIRS)
+
+
+@pytest.mark.slow
+def test_pairs_n34_two_location_chunks(gpu, orc):
+    """N = 34 in the pair store: two column slots per lane in the LAPs and the
+    fused pass in chunks of two locations with per-piece copies; the oracle's
+    D->C on three facility slices, 10^6 sampled D entries, then properties."""
+    N = 34
+    F, D = I.clustered_euclid(N, seed=N + 1)
+    rng = np.random.default_rng(N)
+    perms = [rng.permutation(N) for _ in range(100)]
+    st = orc.State(F, D, paired=True)
+    st.spread_B_to_C()
+    st.spread_C_to_D()
+    st.complementary_D()
+    slices = (0, N // 2, N - 2)
+    for a in slices:
+        st.concentrate_D_to_C_range(a, a + 1)
+    with rlt2.Context(F, D, store=PAIRS) as ctx:
+        ctx.iterate(1)
+        z = ctx.state(2)
+        i, j, k, n = [a.astype(np.int64) for a in tile_indices(N)]
+        per = N * (N - 1) ** 2
+        for a in slices:
+            sel = a * per + rng.integers(0, per, size=1000000)
+            rr = rng.integers(0, N - 2, size=sel.size)
+            ss = rng.integers(0, N - 2, size=sel.size)
+            lo, hi = np.minimum(i[sel], k[sel]), np.maximum(i[sel], k[sel])
+            p = rr + (rr >= lo)
+            p = p + (p >= hi)
+            lo, hi = np.minimum(j[sel], n[sel]), np.maximum(j[sel], n[sel])
+            q = ss + (ss >= lo)
+            q = q + (q >= hi)
+            ref = st.d[i[sel], j[sel], k[sel], n[sel], p, q]
+            got = z[(sel * (N - 2) + rr) * (N - 2) + ss]
+            assert (got == ref).all(), "D differs in slice i = %d" % a
+        st.close()
+        hist = [ctx.bound()[1]]
+        for t in range(3):
+            ctx.iterate(1)
+            hist.append(ctx.bound()[1])
+        x, y, z = ctx.state(0), ctx.state(1), ctx.state(2)
+        assert x.min() >= 0 and y.min() >= 0 and z.min() >= 0
+        assert all(a <= b for a, b in zip(hist, hist[1:]))
+        assert _conservation_sample(F, D, N, hist[-1], x, y, z, perms) == 0
