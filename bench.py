@@ -107,9 +107,10 @@ def serve_measure(instances, torch, count, passes=50, rate=50.0):
     return out
 
 
-def n35_measure(rlt2, instances, torch, steps, store, warmup=3):
-    """Root bound of the 35-facility clustered instance."""
-    F, D, _ = instances.instance("clustered_n35")
+def n35_measure(rlt2, instances, torch, steps, store, warmup=3, workload="clustered_n35"):
+    """Root bound of one clustered instance (the 35-facility one by default)."""
+    F, D, _ = instances.instance(workload)
+    N = F.shape[0]
     s = torch.cuda.Stream()
     with rlt2.Context(F, D, profile=True, max_iters=steps + warmup + 1, stream=s.cuda_stream,
                       store=store) as c:
@@ -125,14 +126,14 @@ def n35_measure(rlt2, instances, torch, steps, store, warmup=3):
         ms, n = c.stage_times()
         lb = c.bound()[1]
     t = e0.elapsed_time(e1)
-    return {"metric": "RLT2 dual-ascent iters/sec at N=35", "unit": "iters/s",
+    return {"metric": "RLT2 dual-ascent iters/sec at N=%d" % N, "unit": "iters/s",
             "value": steps / (t / 1000.0), "steps": steps, "LB": lb,
             "stages_ms": {"spread_complementary_D": ms[0] / n, "concentrate_D_to_C": ms[1] / n,
                           "complementary_C_concentrate_C_to_B": ms[2] / n,
                           "concentrate_B_to_LB": ms[3] / n},
             "store": "%s (%.2f GB on the device)" % (
-                "class sums" if store == rlt2.RLT2_STORE_CLASSES else "tiles",
-                rlt2.rlt2_state_bytes(35, store=store) / 1e9)}
+                {rlt2.RLT2_STORE_CLASSES: "class sums", rlt2.RLT2_STORE_PAIRS: "pairs (Sec. 6)"}.get(store, "tiles"),
+                rlt2.rlt2_state_bytes(N, store=store) / 1e9)}
 
 
 def bnb_measure(instances, torch):
@@ -478,6 +479,11 @@ def main():
     if args.n35_steps > 0:
         line["n35"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_CLASSES)
         line["n35_tiles"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_TILES)
+        # the paired dual ascent of Sec. 6's complementary submatrices (another
+        # arithmetic: half the D->C LAPs, its own bound), beside the metric
+        line["pairs_n30"] = n35_measure(rlt2, instances, torch, 100, rlt2.RLT2_STORE_PAIRS,
+                                        workload="clustered_n30")
+        line["pairs_n35"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_PAIRS)
     if args.serve_requests > 0:
         line["serve"] = serve_measure(instances, torch, args.serve_requests)
     if args.batch_nodes > 0:
