@@ -402,9 +402,9 @@ def test_pairs_headline_n30(gpu, orc):
 
 
 @pytest.mark.slow
-def test_pairs_n34_two_location_chunks(gpu, orc):
-    """N = 34 in the pair store: two column slots per lane in the LAPs and the
-    fused pass in chunks of two locations with per-piece copies; the oracle's
+def test_pairs_n34_two_column_slots(gpu, orc):
+    """N = 34 in the pair store: two column slots per lane in the LAPs (the
+    pair store's fused pass still fits chunks of four locations); the oracle's
     D->C on three facility slices, 10^6 sampled D entries, then properties."""
     N = 34
     F, D = I.clustered_euclid(N, seed=N + 1)
