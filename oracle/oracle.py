@@ -29,6 +29,8 @@ def lib():
         L.orc_create.argtypes = [C.c_int, _i32p, _i32p, _i64p, C.c_int64, C.c_int]
         L.orc_set_paired.restype = None
         L.orc_set_paired.argtypes = [C.c_void_p, C.c_int]
+        L.orc_child.restype = C.c_void_p
+        L.orc_child.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.orc_destroy.argtypes = [C.c_void_p]
         for name in ("orc_spread_B_to_C", "orc_spread_C_to_D", "orc_complementary_D",
                      "orc_concentrate_D_to_C", "orc_complementary_C", "orc_concentrate_C_to_B"):
@@ -127,6 +129,18 @@ class State:
         self.paired = paired
         if paired:
             lib().orc_set_paired(self._h, 1)
+
+    def child(self, f, l):
+        """Warm-started state of the node fixing facility f to location l."""
+        h = lib().orc_child(self._h, int(f), int(l))
+        if not h:
+            raise ValueError("no child state (N too small or bad indices)")
+        st = State.__new__(State)
+        st._h = h
+        st.N = self.N - 1
+        st.rlt1_only = self.rlt1_only
+        st.paired = self.paired
+        return st
 
     def close(self):
         if self._h:

@@ -547,5 +547,72 @@ int orc_subproblem(int N, const int32_t *F, const int32_t *Dist, int kfix,
     return Np;
 }
 
+/*
+ * Warm start of a branch-and-bound child (the node of the parent fixing
+ * facility f to location l).  The conservation identity of the parent,
+ *   Q(pi) = LB + sum_i b_{i pi_i} + sum_{i!=k} c_{i pi_i k pi_k}
+ *              + sum_{distinct i,k,p} d_{i pi_i k pi_k p pi_p},
+ * restricted to the permutations with pi(f) = l splits into the child's terms
+ * over the other facilities and locations (renumbered in ascending order):
+ *   LB'      = LB + b_fl
+ *   b'_kn    = b_kn + c_flkn + c_knfl
+ *   c'_knpq  = c_knpq + d_flknpq + d_knflpq + d_knpqfl
+ *   d'       = d over the free indices,
+ * all sums of reduced costs, so >= 0, and the child's dual ascent starts from
+ * LB' >= LB instead of from 0.  (The paper is silent on how a node's bound is
+ * started; this is the warm-started variant of reading R10.)  The child keeps
+ * the parent's paired flag (the pair sums stay in the tiles with i < k).
+ * Returns NULL for N < 4 or on allocation failure.
+ */
+orc_state *orc_child(const orc_state *par, int f, int l)
+{
+    const int N = par->N, M = N - 1;
+    if (M < 3 || f < 0 || f >= N || l < 0 || l >= N) return NULL;
+    orc_state *st = calloc(1, sizeof(orc_state));
+    if (!st) return NULL;
+    st->N = M;
+    st->rlt1_only = par->rlt1_only;
+    st->paired = par->paired;
+    size_t m2 = (size_t)M * M, m4 = m2 * m2;
+    st->b = calloc(m2, sizeof(int64_t));
+    st->c = calloc(m4, sizeof(int64_t));
+    if (!par->rlt1_only) st->d = calloc(m4 * m2, sizeof(int64_t));
+    if (!st->b || !st->c || (!par->rlt1_only && !st->d)) {
+        free(st->b); free(st->c); free(st->d); free(st);
+        return NULL;
+    }
+    int fa[64], lo[64];  /* child index -> parent index */
+    for (int x = 0, a = 0; a < N; a++) if (a != f) fa[x++] = a;
+    for (int x = 0, a = 0; a < N; a++) if (a != l) lo[x++] = a;
+    st->LB = par->LB + par->b[ix2(N, f, l)];
+    for (int x = 0; x < M; x++)
+        for (int y = 0; y < M; y++) {
+            const int k = fa[x], n = lo[y];
+            st->b[ix2(M, x, y)] = par->b[ix2(N, k, n)] + par->c[ix4(N, f, l, k, n)] + par->c[ix4(N, k, n, f, l)];
+        }
+    for (int x = 0; x < M; x++)
+        for (int y = 0; y < M; y++)
+            for (int u = 0; u < M; u++)
+                for (int w = 0; w < M; w++) {
+                    if (u == x || w == y) continue;
+                    const int k = fa[x], n = lo[y], p = fa[u], q = lo[w];
+                    int64_t v = par->c[ix4(N, k, n, p, q)];
+                    if (par->d)
+                        v += par->d[ix6(N, f, l, k, n, p, q)] + par->d[ix6(N, k, n, f, l, p, q)] +
+                             par->d[ix6(N, k, n, p, q, f, l)];
+                    st->c[ix4(M, x, y, u, w)] = v;
+                }
+    if (st->d)
+        for (int x = 0; x < M; x++)
+            for (int y = 0; y < M; y++)
+                for (int u = 0; u < M; u++)
+                    for (int w = 0; w < M; w++)
+                        for (int r = 0; r < M; r++)
+                            for (int z = 0; z < M; z++)
+                                st->d[ix6(M, x, y, u, w, r, z)] =
+                                    par->d[ix6(N, fa[x], lo[y], fa[u], lo[w], fa[r], lo[z])];
+    return st;
+}
+
 /* LB <- LB + x (the last line of the loop of Algorithm 1, for step-wise use). */
 void orc_add_LB(orc_state *st, int64_t x) { st->LB += x; }

@@ -345,3 +345,60 @@ def test_paired_uniform_n8_below_optimum(orc):
     rng = np.random.default_rng(1)
     perms = np.array([rng.permutation(8) for _ in range(2000)])
     assert conservation_residual(F, D, st, perms) == 0
+
+
+# ------------------------------------------------------------- warm start
+
+@pytest.mark.parametrize("paired", [False, True])
+@pytest.mark.parametrize("N,seed,f,l", [(5, 0, 1, 3), (6, 1, 0, 5), (6, 2, 4, 2)])
+def test_child_conserves_every_completion(orc, N, seed, f, l, paired):
+    """The warm-started child of a node fixing f -> l: for every permutation
+    with pi(f) = l, Q(pi) equals the child's LB plus its reduced costs along
+    the restricted permutation (child indices renumbered in ascending order);
+    the child's reduced costs are >= 0, its bound starts at or above the
+    parent's and stays below the optimum of the node after further passes."""
+    F, D = I.uniform_symmetric(N, seed=seed)
+    par = orc.State(F, D, paired=paired)
+    par.run(3)
+    ch = par.child(f, l)
+    assert ch.N == N - 1 and ch.LB >= par.LB
+    fa = [a for a in range(N) if a != f]
+    lo = [a for a in range(N) if a != l]
+    perms = []
+    for rest in itertools.permutations(lo):
+        perms.append(list(rest))
+    # the child's permutation pi' maps child facility x to child location index of pi(fa[x])
+    child_perms = [[lo.index(v) for v in p] for p in perms]
+    full = []
+    for p in perms:
+        q = np.empty(N, np.int64)
+        q[f] = l
+        q[fa] = p
+        full.append(q)
+    Q = np.array([qap_cost(F, D, q) for q in full])
+    for _ in range(3):
+        st_pass = np.array(child_perms)
+        # residual of the child's identity: its own conservation against the full Q
+        resid = conservation_residual_vs(ch, st_pass, Q)
+        assert resid == 0
+        assert nonneg(ch)
+        ch.iterate()
+    node_opt = int(Q.min())
+    assert ch.LB <= node_opt
+
+
+def conservation_residual_vs(st, P, Q):
+    """max |Q - (LB + reduced costs along the permutations P)| for a state."""
+    N = st.N
+    idx = np.arange(N)
+    tot = np.full(len(P), st.LB, np.int64) + st.b[idx[None, :], P].sum(1)
+    I_, K_ = np.meshgrid(idx, idx, indexing="ij")
+    off = I_ != K_
+    Ii, Kk = I_[off], K_[off]
+    tot += st.c[Ii[None, :], P[:, Ii], Kk[None, :], P[:, Kk]].sum(1)
+    if st.d is not None:
+        I3, K3, P3 = np.meshgrid(idx, idx, idx, indexing="ij")
+        ok = (I3 != K3) & (I3 != P3) & (K3 != P3)
+        I3, K3, P3 = I3[ok], K3[ok], P3[ok]
+        tot += st.d[I3[None, :], P[:, I3], K3[None, :], P[:, K3], P3[None, :], P[:, P3]].sum(1)
+    return int(np.abs(np.asarray(Q, np.int64) - tot).max())
