@@ -203,6 +203,26 @@ void *rlt2_device_state(rlt2_ctx *ctx, int which);
 int rlt2_row_stride(int N);
 
 /*
+ * Warm-started child of a branch-and-bound node (the paper does not say how a
+ * node's bound starts; this is the warm form of the cold start rlt2_subproblem
+ * gives).  The child fixes the parent's facility f to its location l (parent
+ * indices); its facilities and locations are the parent's others, renumbered
+ * in ascending order, and its state is the parent's dual state restricted to
+ * the permutations with pi(f) = l:
+ *   LB' = LB + b_fl,  b'_kn = b_kn + c_flkn + c_knfl,
+ *   c'_knpq = c_knpq + d_flknpq + d_knflpq + d_knpqfl,  d' = d restricted,
+ * all reduced costs >= 0 and LB' >= LB; further passes continue from there.
+ * The child is a new context (N - 1) with the parent's store (tiles or pairs;
+ * the class-sum store is refused) and RLT1 mode, opts for the rest; it is
+ * derived on the device after every pass enqueued on the parent (its stream
+ * waits for the parent's), and the call synchronises the child.
+ * Errors: RLT2_E_INVAL (N - 1 < RLT2_MIN_N, f or l out of range, class-sum
+ * store, bad opts), RLT2_E_OOM, RLT2_E_CUDA, RLT2_E_TIMEOUT / RLT2_E_INTERNAL
+ * (a pending error of the parent's passes; no child).
+ */
+int rlt2_child(rlt2_ctx *parent, int f, int l, const rlt2_opts *opts, rlt2_ctx **out);
+
+/*
  * Checkpoint and resume of a dual ascent (no counterpart in the paper, whose
  * runs are not interrupted; it serves long branch-and-bound runs).
  *

@@ -17,7 +17,11 @@ facilities to locations.  This driver does the same on one GPU:
 * nodes with at most `enum_size` free facilities are completed by exhaustive
   enumeration on the host;
 * the initial UB comes from pairwise-exchange local search from a few seeded
-  random permutations (the paper's UB heuristic is not specified).
+  random permutations (the paper's UB heuristic is not specified);
+* warm=True: a node keeps its context, and its children start from its dual
+  state (rlt2_child: the state restricted to the child's fixed pair) instead
+  of cold residual instances; the children of a node are advanced together
+  as one group (rlt2_group_*), each stopping once its bound reaches the UB.
 
 Children are visited in increasing order of their bound.  With integer costs
 a node whose bound reaches the incumbent cannot contain a better solution.
@@ -70,7 +74,7 @@ class BranchAndBound:
 
     def __init__(self, F, D, iters: int = 12, root_iters: int = 30, strong_depth: int = 1,
                  strong_iters: int = 3, enum_size: int = 3, ub: Optional[int] = None,
-                 node_limit: int = 1_000_000, store: int = rlt2.RLT2_STORE_TILES):
+                 node_limit: int = 1_000_000, store: int = rlt2.RLT2_STORE_TILES, warm: bool = False):
         self.F = np.ascontiguousarray(F, np.int32)
         self.D = np.ascontiguousarray(D, np.int32)
         self.N = self.F.shape[0]
@@ -81,6 +85,7 @@ class BranchAndBound:
         self.enum_size = max(1, enum_size)
         self.node_limit = node_limit
         self.store = store
+        self.warm = warm
         self.ub0 = ub
         self.stats = dict(nodes_bounded=0, nodes_pruned=0, leaves_enumerated=0, batches=0,
                           strong_evaluations=0)
@@ -92,6 +97,21 @@ class BranchAndBound:
         self.stats["batches"] += 1
         self.stats["nodes_bounded"] += len(nodes)
         return [int(x) for x in lbs]
+
+    def _children_warm(self, ctx, free_facs, free_locs, f) -> List[Tuple[int, object]]:
+        """Children of the node held by ctx, warm-started from its dual state and
+        advanced `iters` passes together; returns (bound, context) per location."""
+        fl = free_facs.index(f)
+        kids = [ctx.child(fl, x, ub=float(self.ub), max_iters=self.iters + 1) for x in range(len(free_locs))]
+        grp = rlt2.rlt2_group_create([k.ctx for k in kids])
+        try:
+            rlt2.rlt2_group_iterate(grp, self.iters)
+            rlt2.rlt2_group_sync(grp)
+        finally:
+            rlt2.rlt2_group_destroy(grp)
+        self.stats["batches"] += 1
+        self.stats["nodes_bounded"] += len(kids)
+        return [(k.bound()[1], k) for k in kids]
 
     def _rlt1_child_min(self, fac, loc, f, free_locs) -> int:
         best = None
@@ -126,6 +146,39 @@ class BranchAndBound:
                 self.ub, self.best = c, perm.copy()
 
     # -- search -----------------------------------------------------------
+    def _expand(self, lb, fac, loc, ctx, stack) -> int:
+        """Process one node; push its surviving children.  Returns 1 if the node
+        counted as visited (its bound was still below the incumbent)."""
+        if lb >= self.ub:          # the incumbent improved since the node was queued
+            self.stats["nodes_pruned"] += 1
+            return 0
+        free_facs = [f for f in range(self.N) if f not in fac]
+        free_locs = [l for l in range(self.N) if l not in loc]
+        if len(free_facs) <= self.enum_size:
+            self._enumerate(fac, loc, free_facs, free_locs)
+            return 1
+        f = self._branch_facility(fac, loc, free_facs, free_locs)
+        if len(free_facs) - 1 < rlt2.RLT2_MIN_N:
+            # children too small for the bound: enumerate them
+            for l in free_locs:
+                ff = [x for x in free_facs if x != f]
+                ll = [x for x in free_locs if x != l]
+                self._enumerate(fac + [f], loc + [l], ff, ll)
+            return 1
+        if self.warm and ctx is not None:
+            kids = [(b, l, k) for (b, k), l in zip(self._children_warm(ctx, free_facs, free_locs, f), free_locs)]
+        else:
+            kids = [(b, l, None) for b, l in zip(self._children_bounds(fac, loc, f, free_locs), free_locs)]
+        kids.sort(key=lambda x: -x[0])   # popped in increasing bound order
+        for b, l, k in kids:
+            if b >= self.ub:
+                self.stats["nodes_pruned"] += 1
+                if k is not None:
+                    k.close()
+                continue
+            stack.append((b, fac + [f], loc + [l], k))
+        return 1
+
     def solve(self) -> dict:
         t0 = time.perf_counter()
         if self.ub0 is not None:
@@ -133,38 +186,28 @@ class BranchAndBound:
         else:
             self.ub, self.best = local_search_ub(self.F, self.D)
         ub_initial = self.ub
-        with rlt2.Context(self.F, self.D, ub=float(self.ub), max_iters=self.root_iters + 1,
-                          store=self.store) as c:
-            c.iterate(self.root_iters)
-            root_lb = c.bound()[1]
-        stack = [(root_lb, [], [])] if root_lb < self.ub else []
+        root = rlt2.Context(self.F, self.D, ub=float(self.ub), max_iters=self.root_iters + 1, store=self.store)
+        root.iterate(self.root_iters)
+        root_lb = root.bound()[1]
+        if not self.warm:
+            root.close()
+            root = None
+        stack = [(root_lb, [], [], root)] if root_lb < self.ub else []
+        if not stack and root is not None:
+            root.close()
         visited = 0
-        while stack and visited < self.node_limit:
-            lb, fac, loc = stack.pop()
-            if lb >= self.ub:          # the incumbent improved since the node was queued
-                self.stats["nodes_pruned"] += 1
-                continue
-            visited += 1
-            free_facs = [f for f in range(self.N) if f not in fac]
-            free_locs = [l for l in range(self.N) if l not in loc]
-            if len(free_facs) <= self.enum_size:
-                self._enumerate(fac, loc, free_facs, free_locs)
-                continue
-            f = self._branch_facility(fac, loc, free_facs, free_locs)
-            if len(free_facs) - 1 < rlt2.RLT2_MIN_N:
-                # children too small for the bound: enumerate them
-                for l in free_locs:
-                    ff = [x for x in free_facs if x != f]
-                    ll = [x for x in free_locs if x != l]
-                    self._enumerate(fac + [f], loc + [l], ff, ll)
-                continue
-            lbs = self._children_bounds(fac, loc, f, free_locs)
-            kids = sorted(zip(lbs, free_locs), reverse=True)   # popped in increasing bound order
-            for lb, l in kids:
-                if lb >= self.ub:
-                    self.stats["nodes_pruned"] += 1
-                    continue
-                stack.append((lb, fac + [f], loc + [l]))
-        return dict(optimum=self.ub, perm=self.best, proven=not stack, root_lb=root_lb,
+        try:
+            while stack and visited < self.node_limit:
+                lb, fac, loc, ctx = stack.pop()
+                try:
+                    visited += self._expand(lb, fac, loc, ctx, stack)
+                finally:
+                    if ctx is not None:
+                        ctx.close()
+        finally:
+            for entry in stack:
+                if entry[3] is not None:
+                    entry[3].close()
+        return dict(optimum=self.ub, perm=self.best, proven=not stack, root_lb=root_lb, warm=self.warm,
                     ub_initial=ub_initial, nodes_visited=visited, seconds=time.perf_counter() - t0,
                     **self.stats)

@@ -410,6 +410,44 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
     return RLT2_OK;
 }
 
+int rlt2_child(rlt2_ctx *par, int f, int l, const rlt2_opts *opts, rlt2_ctx **out)
+{
+    if (!par || !out) return RLT2_E_INVAL;
+    *out = nullptr;
+    const NodeDesc &pn = par->node;
+    const int N = pn.N;
+    if (N - 1 < RLT2_MIN_N || f < 0 || f >= N || l < 0 || l >= N || pn.p.T) return RLT2_E_INVAL;
+    rlt2_ctx *c = new_ctx(opts);
+    if (!c) return RLT2_E_OOM;
+    c->opts.rlt1_only = pn.p.z == nullptr;
+    c->opts.store = pn.paired ? RLT2_STORE_PAIRS : RLT2_STORE_TILES;
+    if (c->opts.lanes != 0 && c->opts.lanes != 16 && c->opts.lanes != 32) {
+        free_ctx(c);
+        return RLT2_E_INVAL;
+    }
+    int32_t *stage = nullptr;
+    int rc = setup_ctx(c, N - 1, pn.p.z != nullptr, c->opts.store, par->U, &stage);
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (rc == RLT2_OK) {
+        // after every pass enqueued on the parent
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, par->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, ev, 0);
+        if (e == cudaSuccess) e = launch_child(pn, c->node, f, l, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (ev) cudaEventDestroy(ev);
+        if (e != cudaSuccess) rc = cuda_code(e);
+    }
+    if (rc == RLT2_OK) rc = group_status(par->g, par->stream);  // the parent's passes were sound
+    if (rc != RLT2_OK) {
+        free_ctx(c);
+        return rc;
+    }
+    *out = c;
+    return RLT2_OK;
+}
+
 int rlt2_save(rlt2_ctx *c, const char *path)
 {
     if (!c || !path) return RLT2_E_INVAL;

@@ -201,6 +201,9 @@ size_t p1_smem_bytes(int N, int JC, bool sym, bool paired);  // its dynamic shar
 cudaError_t launch_init(const NodeDesc &node, const int32_t *F, const int32_t *D,
                         const int32_t *Blin, long long lb_const, cudaStream_t s);
 cudaError_t launch_spread_x(const Group &g, cudaStream_t s);
+// State of the warm-started child ch (N - 1) of instance par fixing facility f
+// to location l (tile or pair store): B, C, D and LB derived on the device.
+cudaError_t launch_child(const NodeDesc &par, const NodeDesc &ch, int f, int l, cudaStream_t s);
 // Reduced costs of D of a class-sum-store instance in the tile-store layout
 // (tiles x (N-2) x W ints at out; columns without coefficient 0).
 cudaError_t launch_materialize(const NodeDesc &nd, int *out, cudaStream_t s);

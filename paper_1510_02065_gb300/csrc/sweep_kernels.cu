@@ -685,6 +685,123 @@ cudaError_t launch_materialize(const NodeDesc &nd, int *out, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ------------------------------------------------ warm-started children
+//
+// The child of a node fixing facility f to location l inherits the node's
+// dual state restricted to the permutations with pi(f) = l (indices of the
+// child: the other facilities and locations, ascending):
+//   LB' = LB + b_fl,  b'_kn = b_kn + c_flkn + c_knfl,
+//   c'_knpq = c_knpq + d_flknpq + d_knflpq + d_knpqfl,  d' = d restricted.
+
+// c_ijkn of an instance (i != k, j != n) from its reduced C.
+__device__ __forceinline__ int c_at(const NodeDesc &nd, int i, int j, int k, int n)
+{
+    const int N = nd.N, m = N - 1;
+    return nd.p.yC[(((size_t)i * N + j) * m + (k - (k > i))) * m + (n - (n > j))];
+}
+
+// d_ijknpq of an instance in the tile or pair store (distinct i, k, p;
+// distinct j, n, q); the pair store's tiles with i > k hold 0.
+__device__ __forceinline__ int d_at(const NodeDesc &nd, int i, int j, int k, int n, int p, int q)
+{
+    const int N = nd.N, m = N - 1;
+    size_t t;
+    if (nd.paired) {
+        if (i > k) return 0;
+        t = ((size_t)pair_index(i, k) * N + j) * m + (n - (n > j));
+    } else {
+        t = (((size_t)i * N + j) * m + (k - (k > i))) * m + (n - (n > j));
+    }
+    const int lo = min(i, k), hi = max(i, k);
+    const int r = p - (p > lo) - (p > hi);
+    return nd.p.z[t * nd.TS + (size_t)r * nd.W + q];
+}
+
+__global__ void child_bc_kernel(const NodeDesc par, const NodeDesc ch, int f, int l)
+{
+    const int M = ch.N, N = par.N, m = M - 1;
+    const long long nb = (long long)M * M, nc = (long long)M * M * m * m;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nb + nc;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (e < nb) {
+            const int x = (int)(e / M), y = (int)(e % M);
+            const int k = x + (x >= f), n = y + (y >= l);
+            ch.p.x[e] = par.p.x[k * N + n] + c_at(par, f, l, k, n) + c_at(par, k, n, f, l);
+        } else {
+            const long long t = e - nb;
+            const int w1 = (int)(t % m), u1 = (int)((t / m) % m);
+            const int xy = (int)(t / ((long long)m * m)), x = xy / M, y = xy % M;
+            const int u = u1 + (u1 >= x), w = w1 + (w1 >= y);
+            const int k = x + (x >= f), n = y + (y >= l), p = u + (u >= f), q = w + (w >= l);
+            int v = c_at(par, k, n, p, q);
+            if (par.p.z)
+                v += d_at(par, f, l, k, n, p, q) + d_at(par, k, n, f, l, p, q) + d_at(par, k, n, p, q, f, l);
+            ch.p.yC[t] = v;
+        }
+    }
+}
+
+// One thread per (child tile, row); the row is written whole (columns without
+// coefficient 0).
+__global__ void child_d_kernel(const NodeDesc par, const NodeDesc ch, int f, int l)
+{
+    const int M = ch.N, m = M - 1, n2 = M - 2, W = ch.W;
+    const long long total = ch.dtiles * n2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long th = e / n2;
+        const int r = (int)(e - th * n2);
+        int x, y, u, w;
+        const int w1 = (int)(th % m);
+        if (ch.paired) {
+            const long long pj = th / m;
+            y = (int)(pj % M);
+            pair_of((int)(pj / M), x, u);
+            w = w1 + (w1 >= y);
+        } else {
+            const int u1 = (int)((th / m) % m), xy = (int)(th / ((long long)m * m));
+            x = xy / M;
+            y = xy % M;
+            u = u1 + (u1 >= x);
+            w = w1 + (w1 >= y);
+        }
+        const int lo = min(x, u), hi = max(x, u);
+        int rr = r + (r >= lo);
+        rr += (rr >= hi);                       // the row's child facility
+        // parent indices of the tile's facilities and locations and of the row's facility
+        const int k = x + (x >= f), n = y + (y >= l), p = u + (u >= f), q = w + (w >= l);
+        const int pr = rr + (rr >= f);
+        int *out = ch.p.z + th * ch.TS + (size_t)r * W;
+        for (int z = 0; z < W; ++z)
+            out[z] = (z < M && z != y && z != w) ? d_at(par, k, n, p, q, pr, z + (z >= l)) : 0;
+    }
+}
+
+__global__ void child_scalars_kernel(const NodeDesc par, const NodeDesc ch, int f, int l)
+{
+    *ch.p.LB = *par.p.LB + par.p.x[f * par.N + l];
+    *ch.p.iter = 0;
+    *ch.p.stop = 0;
+}
+
+cudaError_t launch_child(const NodeDesc &par, const NodeDesc &ch, int f, int l, cudaStream_t s)
+{
+    const long long nbc = (long long)ch.N * ch.N * (1 + (long long)(ch.N - 1) * (ch.N - 1));
+    long long blocks = (nbc + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    child_bc_kernel<<<(unsigned)blocks, 256, 0, s>>>(par, ch, f, l);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ch.p.z) {
+        blocks = (ch.dtiles * (ch.N - 2) + 255) / 256;
+        if (blocks > 8192) blocks = 8192;
+        child_d_kernel<<<(unsigned)blocks, 256, 0, s>>>(par, ch, f, l);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    child_scalars_kernel<<<1, 1, 0, s>>>(par, ch, f, l);
+    return cudaGetLastError();
+}
+
 // Costs spreading from B to C (Sec. 4.2): c'_ijkn = c_ijkn + the share of b_ij
 // of row k (k' = rank of k among the facilities != i), written to yS.  One
 // thread per tile of the group.

@@ -88,6 +88,7 @@ def lib():
         "rlt2_lap_batch_static": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "rlt2_state_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int]),
         "rlt2_save": (C.c_int, [_vp, C.c_char_p]),
+        "rlt2_child": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(rlt2_opts), C.POINTER(_vp)]),
         "rlt2_load": (C.c_int, [C.c_char_p, C.POINTER(rlt2_opts), C.POINTER(_vp)]),
         "rlt2_group_create": (C.c_int, [C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)]),
         "rlt2_group_iterate": (C.c_int, [_vp, C.c_int]),
@@ -156,6 +157,13 @@ def rlt2_create(F, D, N=None, B_lin=None, lb_const=0, opts=None):
 
 def rlt2_destroy(ctx):
     lib().rlt2_destroy(_vp(ctx))
+
+
+def rlt2_child(ctx, f, l, opts=None):
+    out = _vp()
+    _chk(lib().rlt2_child(_vp(ctx), int(f), int(l), C.byref(opts) if opts is not None else None, C.byref(out)),
+         "rlt2_child")
+    return out.value
 
 
 def rlt2_save(ctx, path):
@@ -343,6 +351,13 @@ class Context:
 
     def save(self, path):
         rlt2_save(self.ctx, path)
+
+    def child(self, f, l, **kw):
+        """Warm-started child fixing facility f to location l (indices of this context)."""
+        ch = Context.__new__(Context)
+        ch.ctx = rlt2_child(self.ctx, f, l, self._opts(**kw))
+        ch.N = self.N - 1
+        return ch
 
     def iterate(self, k=1):
         rlt2_iterate(self.ctx, k)

@@ -62,3 +62,16 @@ def test_without_strong_branching_and_with_a_poor_incumbent(gpu):
     assert res["proven"] and res["optimum"] == opt
     assert bnb.qap_cost(F, D, res["perm"]) == opt
     assert res["nodes_bounded"] > 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,make", CASES)
+def test_warm_started_search_proves_the_same_optimum(gpu, name, make):
+    """Children started from their parent's dual state (rlt2_child, advanced
+    as one group per node) lead to the same proven optimum."""
+    F, D = make()
+    opt = brute_force_qap(F, D)
+    res = bnb.BranchAndBound(F, D, iters=6, root_iters=20, strong_depth=1, warm=True).solve()
+    assert res["proven"] and res["optimum"] == opt and res["warm"], (name, res)
+    if res["perm"] is not None:
+        assert bnb.qap_cost(F, D, res["perm"]) == opt
