@@ -149,6 +149,42 @@ def bnb_measure(instances, torch):
     return r
 
 
+def lap_methods_measure(rlt2, instances, torch, count=100000):
+    """LAPs/s of the Hungarian kernel (the dual ascent's) and of the auction
+    method (the paper's GPU LAP) on the same real D tiles: `count` random
+    tiles of the 30-facility clustered instance after one pass, 28 x 28 (the
+    tile's own two locations dropped), exported through the C ABI."""
+    F, D, _ = instances.instance("clustered_n30")
+    N, n, m = 30, 28, 29
+    with rlt2.Context(F, D) as c:
+        c.iterate(1)
+        z = c.state(2).reshape(-1, n, n)             # compact tiles on the host
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(z.shape[0], size=count, replace=False))
+    M = torch.from_numpy(np.ascontiguousarray(z[pick])).cuda()
+    del z
+    s = torch.cuda.Stream()
+    S1 = torch.empty(count, dtype=torch.int64, device="cuda")
+    S2 = torch.empty(count, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    out = {}
+    for name, call in (("hungarian", lambda: rlt2.rlt2_lap_batch(M.data_ptr(), n, count, S1.data_ptr(),
+                                                                 stream=s.cuda_stream)),
+                       ("auction", lambda: rlt2.rlt2_lap_batch_auction(M.data_ptr(), n, count, S2.data_ptr(),
+                                                                       stream=s.cuda_stream))):
+        call()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        rc = call()
+        e1.record(s)
+        torch.cuda.synchronize()
+        out[name] = {"laps_per_s": count / (e0.elapsed_time(e1) / 1000.0), "rc": rc}
+    out["identical_optima"] = bool(torch.equal(S1, S2))
+    out["problems"] = "%d D tiles (28 x 28) of clustered N=30 after one pass" % count
+    return out
+
+
 def batch_measure(rlt2, instances, torch, nodes_count, iters):
     """Batched B&B bounding against the plain one-node-at-a-time path.
 
@@ -488,6 +524,7 @@ def main():
         line["serve"] = serve_measure(instances, torch, args.serve_requests)
     if args.batch_nodes > 0:
         line["bnb"] = bnb_measure(instances, torch)
+        line["lap_methods"] = lap_methods_measure(rlt2, instances, torch)
 
     if rank == 0 and world == 1 and args.cpu_budget > 0:
         t_pass, nslices, rest = oracle_sample(F, D, args.cpu_budget)

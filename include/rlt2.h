@@ -340,6 +340,22 @@ int rlt2_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assi
                    int32_t *u, int32_t *v, int64_t *work, void *stream);
 
 /*
+ * The same problems solved by the auction method, the LAP method the paper
+ * uses on its GPU (Sec. 6; Bertsekas' auction), for comparison with the
+ * Hungarian kernel.  One warp per problem, Gauss-Seidel bidding with
+ * eps-scaling on costs scaled by n + 1 down to eps = 1, which makes the final
+ * assignment optimal: S equals rlt2_lap_batch's S (the assignment may differ
+ * where optima tie).  No potentials are returned (the auction's prices are not
+ * the Hungarian method's duals).
+ *   M, n, count, S, assign, stream: as rlt2_lap_batch
+ *   work    device, count int64: bids placed (may be NULL)
+ * Synchronises the stream.  Errors: as rlt2_lap_batch; RLT2_E_INTERNAL if a
+ * problem needed more than 64 n^2 + 64 bids in one eps phase (S = -1 there).
+ */
+int rlt2_lap_batch_auction(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
+                           int64_t *work, void *stream);
+
+/*
  * rlt2_lap_batch_static -- rlt2_lap_batch for callers that must not let a
  * library allocate device memory (the paper has no counterpart to this call).
  * Such callers hand all device memory to one owning allocator, run under a

@@ -1184,6 +1184,25 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
 
 // ------------------------------------------------------------------ LAP batch
 
+int rlt2_lap_batch_auction(const int32_t *M, int n, int count, int64_t *S, int32_t *assign, int64_t *work,
+                           void *stream)
+{
+    if (n < 1 || n > 64 || count < 0 || (count > 0 && (!M || !S))) return RLT2_E_INVAL;
+    if (count == 0) return RLT2_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevStatus *st = nullptr;
+    CK(cudaMallocAsync((void **)&st, sizeof(DevStatus), s));
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if (e == cudaSuccess) e = launch_auction_batch(M, n, count, S, assign, work, st, s);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &st->err, 4, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(st, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_code(e);
+    if (err & kDevInternal) return RLT2_E_INTERNAL;
+    return (err & kDevRange) ? RLT2_E_INVAL : RLT2_OK;
+}
+
 int rlt2_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign, int32_t *u,
                    int32_t *v, int64_t *work, void *stream)
 {

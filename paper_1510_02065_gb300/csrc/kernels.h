@@ -222,6 +222,10 @@ cudaError_t launch_lap_batch(const int32_t *M, int n, int count, int64_t *S, int
                              int32_t *u, int32_t *v, int64_t *work, DevStatus *status,
                              cudaStream_t s);
 
+// The auction method on caller matrices (comparison with the Hungarian method).
+cudaError_t launch_auction_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
+                                 int64_t *work, DevStatus *status, cudaStream_t s);
+
 // Index of the instance owning group-wide item x; base(node) is its first item.
 template <typename F>
 __device__ __forceinline__ int find_node(const NodeDesc *nodes, int B, long long x, F base)

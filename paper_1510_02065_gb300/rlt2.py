@@ -86,6 +86,7 @@ def lib():
         "rlt2_row_stride": (C.c_int, [C.c_int]),
         "rlt2_lap_batch": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "rlt2_lap_batch_static": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "rlt2_lap_batch_auction": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
         "rlt2_state_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int]),
         "rlt2_save": (C.c_int, [_vp, C.c_char_p]),
         "rlt2_child": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(rlt2_opts), C.POINTER(_vp)]),
@@ -228,6 +229,12 @@ def rlt2_device_state(ctx, which: int) -> int:
 
 def rlt2_row_stride(N: int) -> int:
     return lib().rlt2_row_stride(int(N))
+
+
+def rlt2_lap_batch_auction(M_ptr, n, count, S_ptr, assign_ptr=0, work_ptr=0, stream=0):
+    """Device addresses in, device addresses out (see rlt2.h).  Returns the C code."""
+    return lib().rlt2_lap_batch_auction(_vp(M_ptr or None), int(n), int(count), _vp(S_ptr or None),
+                                        _vp(assign_ptr or None), _vp(work_ptr or None), _vp(stream or None))
 
 
 def rlt2_lap_batch(M_ptr, n, count, S_ptr, assign_ptr=0, u_ptr=0, v_ptr=0, work_ptr=0, stream=0):
