@@ -145,7 +145,7 @@ struct NodeDesc {
     long long dtile_base; // first group-wide D->C unit of this instance
     int cta_base;         // first fused-pass CTA of this instance
     int prob_base;        // first C->B problem of this instance
-    FastDiv fN, fm, fmm, fn, fW4;
+    FastDiv fN, fm, fmm, fn;
 };
 
 inline void fill_node(NodeDesc &d, int N, int JC)
@@ -163,7 +163,6 @@ inline void fill_node(NodeDesc &d, int N, int JC)
     d.fm = make_fastdiv(N - 1);
     d.fmm = make_fastdiv((N - 1) * (N - 1));
     d.fn = make_fastdiv(N - 2);
-    d.fW4 = make_fastdiv(g.W / 4);
 }
 
 // A group of instances advanced together.
