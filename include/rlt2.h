@@ -340,6 +340,16 @@ int rlt2_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assi
                    int32_t *u, int32_t *v, int64_t *work, void *stream);
 
 /*
+ * Failure-detection self-test (no counterpart in the paper): one warp waits on
+ * an mbarrier that nothing completes, through the same bounded wait every
+ * device-side wait of the library uses, giving up after `polls` polls.
+ * Nothing is in flight and nothing faults; the device stays usable.
+ * Returns RLT2_E_TIMEOUT (the expected outcome), RLT2_E_INVAL (polls = 0) or
+ * RLT2_E_CUDA.  Synchronises the stream.
+ */
+int rlt2_selftest_timeout(unsigned polls, void *stream);
+
+/*
  * The same problems solved by the auction method, the LAP method the paper
  * uses on its GPU (Sec. 6; Bertsekas' auction), for comparison with the
  * Hungarian kernel.  One warp per problem, Gauss-Seidel bidding with

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI declared in include/rlt2.h.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -148,6 +149,13 @@ cudaError_t init_node(const NodeDesc &nd, const int32_t *F, const int32_t *D, co
 }
 
 // One pass of Algorithm 1 for the whole group.  ev: 5 events around the stages.
+// NVTX range around the host-side enqueue of one stage (visible in timeline
+// profilers; no cost without a tool attached).
+struct StageRange {
+    explicit StageRange(const char *name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+};
+
 cudaError_t enqueue_pass(const Group &g, int sm_count, cudaStream_t s, cudaEvent_t *ev,
                          const SideStream *side = nullptr)
 {
@@ -155,16 +163,26 @@ cudaError_t enqueue_pass(const Group &g, int sm_count, cudaStream_t s, cudaEvent
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
     if (!g.rlt1_only) {
-        if ((e = launch_p1(g, s)) != cudaSuccess) return e;
+        {
+            StageRange r("rlt2: spread B->C, C->D + complementary D");
+            if ((e = launch_p1(g, s)) != cudaSuccess) return e;
+        }
         if ((e = mark(1)) != cudaSuccess) return e;
+        StageRange r("rlt2: concentration D->C");
         if ((e = launch_dlap(g, sm_count, s, side)) != cudaSuccess) return e;
     } else if ((e = mark(1)) != cudaSuccess) {
         return e;
     }
     if ((e = mark(2)) != cudaSuccess) return e;
-    if ((e = launch_clap(g, s)) != cudaSuccess) return e;
+    {
+        StageRange r("rlt2: complementary C + concentration C->B");
+        if ((e = launch_clap(g, s)) != cudaSuccess) return e;
+    }
     if ((e = mark(3)) != cudaSuccess) return e;
-    if ((e = launch_xlap(g, s)) != cudaSuccess) return e;
+    {
+        StageRange r("rlt2: concentration B->LB");
+        if ((e = launch_xlap(g, s)) != cudaSuccess) return e;
+    }
     return mark(4);
 }
 
@@ -1183,6 +1201,22 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
 }
 
 // ------------------------------------------------------------------ LAP batch
+
+int rlt2_selftest_timeout(unsigned polls, void *stream)
+{
+    if (polls == 0) return RLT2_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevStatus *st = nullptr;
+    CK(cudaMallocAsync((void **)&st, sizeof(DevStatus), s));
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if (e == cudaSuccess) e = launch_wait_selftest(st, polls, s);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &st->err, 4, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(st, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_code(e);
+    return (err & kDevTimeout) ? RLT2_E_TIMEOUT : RLT2_OK;
+}
 
 int rlt2_lap_batch_auction(const int32_t *M, int n, int count, int64_t *S, int32_t *assign, int64_t *work,
                            void *stream)

@@ -173,10 +173,10 @@ __device__ __forceinline__ unsigned fdiv(unsigned x, const FastDiv &f)
 
 // Wait for the phase of parity `parity` of bar to complete; false after
 // kSpinLimit unsuccessful polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit = kSpinLimit)
 {
     const uint32_t a = smem_addr(bar);
-    for (unsigned it = 0; it < kSpinLimit; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

@@ -221,6 +221,9 @@ cudaError_t launch_lap_batch(const int32_t *M, int n, int count, int64_t *S, int
                              int32_t *u, int32_t *v, int64_t *work, DevStatus *status,
                              cudaStream_t s);
 
+// Failure-detection self-test: a bounded wait on an mbarrier nothing completes.
+cudaError_t launch_wait_selftest(DevStatus *status, unsigned limit, cudaStream_t s);
+
 // The auction method on caller matrices (comparison with the Hungarian method).
 cudaError_t launch_auction_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
                                  int64_t *work, DevStatus *status, cudaStream_t s);

@@ -470,6 +470,29 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
     }
 }
 
+// ------------------------------------------------------ failure detection
+
+// A warp waits on an mbarrier that is never completed (its one arrival is
+// expected with bytes no copy will deliver; no copy is issued): the bounded
+// wait gives up after `limit` polls and records kDevTimeout, the same path
+// every wait of the library takes.  Nothing is in flight, nothing faults.
+__global__ void wait_selftest_kernel(DevStatus *status, unsigned limit)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (!__all_sync(kFull, mbar_wait(&bar, 0, limit)) && threadIdx.x == 0) atomicOr(&status->err, kDevTimeout);
+}
+
+cudaError_t launch_wait_selftest(DevStatus *status, unsigned limit, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 32, 0, s>>>(status, limit);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- launchers
 
 // Resident warps per SM of the D->C kernel with CTAs of WARPS warps.

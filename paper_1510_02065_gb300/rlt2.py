@@ -87,6 +87,7 @@ def lib():
         "rlt2_lap_batch": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "rlt2_lap_batch_static": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
         "rlt2_lap_batch_auction": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
+        "rlt2_selftest_timeout": (C.c_int, [C.c_uint, _vp]),
         "rlt2_state_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int]),
         "rlt2_save": (C.c_int, [_vp, C.c_char_p]),
         "rlt2_child": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(rlt2_opts), C.POINTER(_vp)]),
@@ -229,6 +230,11 @@ def rlt2_device_state(ctx, which: int) -> int:
 
 def rlt2_row_stride(N: int) -> int:
     return lib().rlt2_row_stride(int(N))
+
+
+def rlt2_selftest_timeout(polls, stream=0) -> int:
+    """Returns the C code (RLT2_E_TIMEOUT expected)."""
+    return lib().rlt2_selftest_timeout(int(polls), _vp(stream or None))
 
 
 def rlt2_lap_batch_auction(M_ptr, n, count, S_ptr, assign_ptr=0, work_ptr=0, stream=0):

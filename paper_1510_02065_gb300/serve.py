@@ -9,7 +9,9 @@ requests of different sizes shares the same kernel launches.  Between rounds
 finished requests leave (their bound is read and their memory released) and
 waiting ones join: the group is rebuilt whenever its membership changes.
 Each result equals that of the request bounded alone (same passes, same
-arithmetic).
+arithmetic).  A request can be cancelled (cancel(rid), from any thread, or
+cancel_after passes for a client that gives up mid-run): it leaves at the
+next round boundary with its memory released and error "cancelled".
 
 All device work runs through the C ABI (librlt2.so); this module only
 schedules.
@@ -18,6 +20,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import threading
 import time
 from typing import List, Optional
 
@@ -35,6 +38,7 @@ class Request:
     arrival: float = 0.0            # seconds after the start of serve()
     B_lin: Optional[np.ndarray] = None
     lb_const: int = 0
+    cancel_after: Optional[int] = None   # cancel once this many passes are done
     # filled in by the server
     lb: Optional[int] = None
     admitted: Optional[float] = None
@@ -63,6 +67,19 @@ class BoundServer:
         self.peak_bytes = 0
         self.rounds = 0
         self.slot_rounds = 0
+        self._cancelled = set()
+        self._lock = threading.Lock()
+
+    def cancel(self, rid: int) -> None:
+        """Cancel request rid (queued or running); effective at the next round boundary."""
+        with self._lock:
+            self._cancelled.add(rid)
+
+    def _is_cancelled(self, req: Request, done: int = 0) -> bool:
+        with self._lock:
+            if req.rid in self._cancelled:
+                return True
+        return req.cancel_after is not None and done >= req.cancel_after
 
     def _bytes(self, req: Request) -> int:
         return rlt2.rlt2_state_bytes(req.N, False, req.iters + 1, self.store)
@@ -87,6 +104,10 @@ class BoundServer:
             t = now()
             while future and (future[0].arrival <= t or (not realtime and not active and not pending)):
                 pending.append(future.popleft())
+            for req in [r for r in pending if self._is_cancelled(r)]:
+                pending.remove(req)
+                req.error = "cancelled"
+                finished.append(req)
             while pending and len(active) < self.max_slots:
                 req = pending[0]
                 need = self._bytes(req)
@@ -120,6 +141,9 @@ class BoundServer:
                 group = rlt2.rlt2_group_create([a[1].ctx for a in active], self.stream)
                 changed = False
             k = min(self.passes_per_round, min(a[0].iters - a[2] for a in active))
+            for a in active:               # stop at a client's cancellation point
+                if a[0].cancel_after is not None and a[2] < a[0].cancel_after:
+                    k = min(k, a[0].cancel_after - a[2])
             if k > 0:
                 rlt2.rlt2_group_iterate(group, k)
                 rlt2.rlt2_group_sync(group)
@@ -128,7 +152,7 @@ class BoundServer:
             leaving = []
             for a in active:
                 a[2] += k
-                if a[2] >= a[0].iters:
+                if a[2] >= a[0].iters or self._is_cancelled(a[0], a[2]):
                     leaving.append(a)
             if leaving:
                 rlt2.rlt2_group_destroy(group)
@@ -136,7 +160,11 @@ class BoundServer:
                 changed = True
                 for a in leaving:
                     req, ctx = a[0], a[1]
-                    req.lb = ctx.bound()[1]
+                    if a[2] >= req.iters:
+                        req.lb = ctx.bound()[1]
+                    else:
+                        ctx.bound()          # surfaces a device error, if any
+                        req.error = "cancelled"
                     req.done = now()
                     ctx.close()
                     used -= self._bytes(req)

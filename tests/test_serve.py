@@ -83,3 +83,24 @@ def test_group_rejects_mixed_stores(gpu):
     finally:
         a.close()
         b.close()
+
+
+def test_cancelled_request_leaves_and_others_are_unaffected(gpu):
+    """A request cancelled mid-run (its client gives up after 2 of 8 passes)
+    and one cancelled while queued leave without a bound; every other result
+    equals the request bounded alone."""
+    reqs = _requests(3, 8)
+    for r in reqs:
+        r.iters = 8
+    reqs[2].cancel_after = 2
+    srv = BoundServer(mem_budget=1 << 40, max_slots=3, passes_per_round=1)
+    srv.cancel(reqs[6].rid)
+    stats = srv.serve(reqs, realtime=False)
+    assert reqs[2].error == "cancelled" and reqs[2].lb is None
+    assert reqs[6].error == "cancelled" and reqs[6].lb is None
+    assert stats["completed"] == len(reqs) - 2
+    for r in reqs:
+        if r.error is None:
+            with rlt2.Context(r.F, r.D) as ctx:
+                ctx.iterate(r.iters)
+                assert ctx.bound()[1] == r.lb, r.rid
