@@ -29,17 +29,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RLT2 dual-ascent iters/sec at N=30"
 OPS_PER_RELAXATION = 9   # textbook int ops of one relaxation
-# DRAM bytes per launch of the D->C kernel on the 30-facility workload, from one
-# ncu capture (profiles/dram_dlap_p1_clustered_n30.md); reported only while the
-# kernel's sources hash to the captured version.
-# DRAM bytes per launch from one ncu capture of the headline workload (tile
-# store), valid while the kernel's sources hash to the captured version
-DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2714420480 + 2651898624,
+# DRAM bytes per launch of the D->C and fused-pass kernels on the 30-facility
+# workload (tile store), from one ncu capture (profiles/dram_dlap_p1_clustered_n30.md);
+# reported only while the kernel's sources hash to the captured version.
+DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2714472704 + 2651894528,
                 "files": ("lap_kernels.cu", "device.cuh", "kernels.h"),
-                "sources_sha1": "9c540a01643cd88ebd7d51cd1d615c54fa4f2649"}
-P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2741275648 + 2655557376,
+                "sources_sha1": "8f72c099ba58a2d2388ce333a90eb70659637f27"}
+P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2740685568 + 2655290368,
               "files": ("sweep_kernels.cu", "device.cuh", "kernels.h"),
-              "sources_sha1": "41184b3d8ba7e186eb461cde31bdb07a2430a53d"}
+              "sources_sha1": "0eafd798ec382b4ec2a33a9443f411e39707fa44"}
 
 
 def captured_traffic(rec, workload, store):
