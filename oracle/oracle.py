@@ -57,6 +57,35 @@ def lib():
         L.orc_subproblem.restype = C.c_int
         L.orc_subproblem.argtypes = [C.c_int, _i32p, _i32p, C.c_int, _i32p, _i32p,
                                      _i32p, _i32p, _i64p, _i64p]
+        # FP64 form (reading R14)
+        _f64p = C.POINTER(C.c_double)
+        L.orf_lap.restype = C.c_double
+        L.orf_lap.argtypes = [C.c_int, _f64p, _f64p, _f64p, _i32p, _i64p, C.c_void_p]
+        L.orf_lap_batch.restype = None
+        L.orf_lap_batch.argtypes = [C.c_int, C.c_int, _f64p, _f64p, _f64p, _f64p, _i32p, _i64p]
+        L.orf_create.restype = C.c_void_p
+        L.orf_create.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, C.c_int]
+        L.orf_destroy.argtypes = [C.c_void_p]
+        for name in ("orf_spread_B_to_C", "orf_spread_C_to_D", "orf_complementary_D",
+                     "orf_concentrate_D_to_C", "orf_complementary_C", "orf_concentrate_C_to_B"):
+            getattr(L, name).argtypes = [C.c_void_p]
+            getattr(L, name).restype = None
+        for name in ("orf_spread_C_to_D_range", "orf_complementary_D_range",
+                     "orf_concentrate_D_to_C_range"):
+            getattr(L, name).argtypes = [C.c_void_p, C.c_int, C.c_int]
+            getattr(L, name).restype = None
+        L.orf_concentrate_B_to_LB.restype = C.c_double
+        L.orf_concentrate_B_to_LB.argtypes = [C.c_void_p]
+        L.orf_iterate.restype = C.c_double
+        L.orf_iterate.argtypes = [C.c_void_p]
+        L.orf_run.argtypes = [C.c_void_p, C.c_int, _f64p]
+        L.orf_LB.restype = C.c_double
+        L.orf_LB.argtypes = [C.c_void_p]
+        L.orf_add_LB.argtypes = [C.c_void_p, C.c_double]
+        for name in ("orf_b", "orf_c", "orf_d"):
+            getattr(L, name).restype = _f64p
+            getattr(L, name).argtypes = [C.c_void_p]
+        L.orf_work.argtypes = [C.c_void_p, _i64p]
         _lib = L
     return _lib
 
@@ -67,6 +96,10 @@ def _p64(a):
 
 def _p32(a):
     return a.ctypes.data_as(_i32p)
+
+
+def _pf(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
 def lap(M):
@@ -202,3 +235,107 @@ class State:
         w = np.zeros(4, np.int64)
         lib().orc_work(self._h, _p64(w))
         return dict(laps=int(w[0]), steps=int(w[1]), relaxations=int(w[2]), max_abs=int(w[3]))
+
+
+# ------------------------------------------------------------ FP64 form (R14)
+
+def lap_f64(M):
+    """FP64 Hungarian method on one n x n matrix -> (S, col_of_row, u, v, (steps, relaxations))."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    n = M.shape[0]
+    u = np.zeros(n)
+    v = np.zeros(n)
+    sig = np.zeros(n, np.int32)
+    work = np.zeros(3, np.int64)
+    S = lib().orf_lap(n, _pf(M), _pf(u), _pf(v), _p32(sig), _p64(work), None)
+    return float(S), sig, u, v, (int(work[0]), int(work[1]))
+
+
+def lap_batch_f64(M):
+    """Batch of count x n x n double matrices -> (S[count], col_of_row, u, v, work[count,3])."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    count, n, _ = M.shape
+    S = np.zeros(count)
+    u = np.zeros((count, n))
+    v = np.zeros((count, n))
+    sig = np.zeros((count, n), np.int32)
+    work = np.zeros((count, 3), np.int64)
+    lib().orf_lap_batch(n, count, _pf(M), _pf(S), _pf(u), _pf(v), _p32(sig), _p64(work))
+    return S, sig, u, v, work
+
+
+class StateF64:
+    """RLT2 dual-ascent state of the oracle in the FP64 form (reading R14)."""
+
+    def __init__(self, F, D, B_lin=None, lb_const=0.0, rlt1_only=False):
+        F = np.ascontiguousarray(F, np.int32)
+        D = np.ascontiguousarray(D, np.int32)
+        self.N = N = F.shape[0]
+        bl = None
+        if B_lin is not None:
+            self._bl = np.ascontiguousarray(B_lin, np.float64)
+            bl = _pf(self._bl)
+        self._h = lib().orf_create(N, _p32(F), _p32(D), bl, float(lb_const), int(rlt1_only))
+        if not self._h:
+            raise MemoryError("oracle state allocation failed (N=%d)" % N)
+        self.rlt1_only = rlt1_only
+
+    def close(self):
+        if self._h:
+            lib().orf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spread_B_to_C(self): lib().orf_spread_B_to_C(self._h)
+    def spread_C_to_D(self): lib().orf_spread_C_to_D(self._h)
+    def complementary_D(self): lib().orf_complementary_D(self._h)
+    def concentrate_D_to_C(self): lib().orf_concentrate_D_to_C(self._h)
+    def complementary_C(self): lib().orf_complementary_C(self._h)
+    def concentrate_C_to_B(self): lib().orf_concentrate_C_to_B(self._h)
+    def concentrate_B_to_LB(self): return float(lib().orf_concentrate_B_to_LB(self._h))
+
+    def spread_C_to_D_range(self, lo, hi): lib().orf_spread_C_to_D_range(self._h, lo, hi)
+    def complementary_D_range(self, lo, hi): lib().orf_complementary_D_range(self._h, lo, hi)
+    def concentrate_D_to_C_range(self, lo, hi): lib().orf_concentrate_D_to_C_range(self._h, lo, hi)
+
+    def iterate(self):
+        return float(lib().orf_iterate(self._h))
+
+    def run(self, k):
+        hist = np.zeros(k)
+        lib().orf_run(self._h, k, _pf(hist))
+        return hist
+
+    @property
+    def LB(self):
+        return float(lib().orf_LB(self._h))
+
+    def add_LB(self, x):
+        lib().orf_add_LB(self._h, float(x))
+
+    @property
+    def b(self):
+        N = self.N
+        return np.ctypeslib.as_array(lib().orf_b(self._h), shape=(N, N))
+
+    @property
+    def c(self):
+        N = self.N
+        return np.ctypeslib.as_array(lib().orf_c(self._h), shape=(N, N, N, N))
+
+    @property
+    def d(self):
+        N = self.N
+        if self.rlt1_only:
+            return None
+        return np.ctypeslib.as_array(lib().orf_d(self._h), shape=(N,) * 6)
+
+    def work(self):
+        w = np.zeros(3, np.int64)
+        lib().orf_work(self._h, _p64(w))
+        return dict(laps=int(w[0]), steps=int(w[1]), relaxations=int(w[2]))

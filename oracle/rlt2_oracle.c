@@ -49,6 +49,13 @@
  *       with i < k, adding S to c_ijkn.  Half of D and half of the D -> C LAPs
  *       remain; the bound differs from the full form (a LAP of a sum is at
  *       least the sum of the LAPs).
+ *   R14 (FP64 form, the orf_* functions) the paper's real division: a cost x
+ *       spread over m rows adds x/m (one IEEE double division, the same
+ *       quotient for every row) to each coefficient of the submatrix; a class
+ *       of s complementary costs is summed in lexicographic rank order and
+ *       every member becomes T/s; costs, potentials and LB are doubles, and
+ *       every sum is formed in the order written below (rows and columns
+ *       ascending, left to right), so that the result is one defined double.
  *
  * Parity pins for every function live in tests/ (N!-enumeration and scipy for
  * the LAP, brute-force QAP optima, the conservation identity
@@ -58,6 +65,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <math.h>
 
 #define ORC_INF INT64_MAX
 
@@ -616,3 +624,325 @@ orc_state *orc_child(const orc_state *par, int f, int l)
 
 /* LB <- LB + x (the last line of the loop of Algorithm 1, for step-wise use). */
 void orc_add_LB(orc_state *st, int64_t x) { st->LB += x; }
+
+/* ====================================================== FP64 form (R14) */
+
+/*
+ * The same dual ascent with double costs and the paper's real division
+ * (Sec. 4.2 divides a cost by N-1 or N-2; Sec. 4.3 re-splits a class sum).
+ * Storage as in the int64 form: b[i][j], c[i][j][k][n], d[i][j][k][n][p][q].
+ */
+typedef struct {
+    int N;
+    int rlt1_only;
+    double LB;
+    int64_t iters;
+    double *b, *c, *d;
+    int64_t laps, steps, relaxations;
+} orf_state;
+
+/*
+ * Hungarian method in doubles: the steps of orc_lap (reading R6), every
+ * reduced distance formed as (M[i0][j] - u[i0]) - v[j], the potentials moved
+ * by delta after every step.  Returns S = sum over columns j = 0..n-1 (in that
+ * order, from 0) of M[row of j][j].
+ */
+double orf_lap(int n, const double *M, double *u_out, double *v_out,
+               int32_t *col_of_row, int64_t *work, orf_state *st)
+{
+    double *u = calloc((size_t)n + 1, sizeof(double));
+    double *v = calloc((size_t)n + 1, sizeof(double));
+    double *dist = malloc(((size_t)n + 1) * sizeof(double));
+    int *row_at = malloc(((size_t)n + 1) * sizeof(int));
+    int *pred = malloc(((size_t)n + 1) * sizeof(int));
+    char *labelled = malloc((size_t)n + 1);
+    int64_t steps = 0, relax = 0;
+
+    for (int j = 0; j <= n; j++) row_at[j] = -1;
+
+    for (int r = 0; r < n; r++) {
+        const int root = n;
+        row_at[root] = r;
+        for (int j = 0; j <= n; j++) { dist[j] = INFINITY; labelled[j] = 0; }
+        int col = root;
+        for (;;) {
+            labelled[col] = 1;
+            const int i0 = row_at[col];
+            double delta = INFINITY;
+            int next = -1;
+            steps++;
+            for (int j = 0; j < n; j++) {
+                if (labelled[j]) continue;
+                relax++;
+                double red = M[(size_t)i0 * n + j] - u[i0] - v[j];
+                if (red < dist[j]) { dist[j] = red; pred[j] = col; }
+                if (dist[j] < delta) { delta = dist[j]; next = j; }
+            }
+            for (int j = 0; j <= n; j++) {
+                if (labelled[j]) {
+                    u[row_at[j]] += delta;
+                    v[j] -= delta;
+                } else {
+                    dist[j] -= delta;
+                }
+            }
+            col = next;
+            if (row_at[col] < 0) break;
+        }
+        while (col != root) {
+            int p = pred[col];
+            row_at[col] = row_at[p];
+            col = p;
+        }
+    }
+
+    double S = 0.0;
+    for (int j = 0; j < n; j++) {
+        int r = row_at[j];
+        S += M[(size_t)r * n + j];
+        if (col_of_row) col_of_row[r] = j;
+    }
+    if (u_out) for (int r = 0; r < n; r++) u_out[r] = u[r];
+    if (v_out) for (int j = 0; j < n; j++) v_out[j] = v[j];
+    if (work) { work[0] += steps; work[1] += relax; work[2] += 1; }
+    if (st) { st->steps += steps; st->relaxations += relax; st->laps += 1; }
+    free(u); free(v); free(dist); free(row_at); free(pred); free(labelled);
+    return S;
+}
+
+void orf_lap_batch(int n, int count, const double *M, double *S,
+                   double *u, double *v, int32_t *col_of_row, int64_t *work)
+{
+    for (int t = 0; t < count; t++)
+        S[t] = orf_lap(n, M + (size_t)t * n * n, u ? u + (size_t)t * n : NULL,
+                       v ? v + (size_t)t * n : NULL,
+                       col_of_row ? col_of_row + (size_t)t * n : NULL,
+                       work ? work + (size_t)t * 3 : NULL, NULL);
+}
+
+/* Initialisation of Algorithm 1 in doubles (c_ijkn = f_ik d_jn exactly). */
+orf_state *orf_create(int N, const int32_t *F, const int32_t *Dist,
+                      const double *B_lin, double lb_const, int rlt1_only)
+{
+    if (N < 3) return NULL;
+    orf_state *st = calloc(1, sizeof(orf_state));
+    st->N = N;
+    st->rlt1_only = rlt1_only;
+    st->LB = lb_const;
+    size_t n2 = (size_t)N * N, n4 = n2 * n2;
+    st->b = calloc(n2, sizeof(double));
+    st->c = calloc(n4, sizeof(double));
+    if (!rlt1_only) st->d = calloc(n4 * n2, sizeof(double));
+    if (!st->b || !st->c || (!rlt1_only && !st->d)) {
+        free(st->b); free(st->c); free(st->d); free(st);
+        return NULL;
+    }
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+            st->b[ix2(N, i, j)] = B_lin ? B_lin[ix2(N, i, j)] : 0.0;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+            for (int k = 0; k < N; k++)
+                for (int n = 0; n < N; n++)
+                    if (k != i && n != j)
+                        st->c[ix4(N, i, j, k, n)] =
+                            (double)((int64_t)F[ix2(N, i, k)] * (int64_t)Dist[ix2(N, j, n)]);
+    return st;
+}
+
+void orf_destroy(orf_state *st)
+{
+    if (!st) return;
+    free(st->b); free(st->c); free(st->d); free(st);
+}
+
+/* Spreading B -> C (Sec. 4.2): every c_ijkn (k != i, n != j) += b_ij / (N-1). */
+void orf_spread_B_to_C(orf_state *st)
+{
+    const int N = st->N;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            const double sh = st->b[ix2(N, i, j)] / (double)(N - 1);
+            for (int k = 0; k < N; k++) {
+                if (k == i) continue;
+                for (int n = 0; n < N; n++)
+                    if (n != j) st->c[ix4(N, i, j, k, n)] += sh;
+            }
+            st->b[ix2(N, i, j)] = 0.0;
+        }
+}
+
+/* Spreading C -> D (Sec. 4.2): every d_ijknpq (p not in {i,k}, q not in {j,n})
+ * += c_ijkn / (N-2).  First indices i in [i_lo, i_hi) only. */
+void orf_spread_C_to_D_range(orf_state *st, int i_lo, int i_hi)
+{
+    const int N = st->N;
+    for (int i = i_lo; i < i_hi; i++)
+        for (int j = 0; j < N; j++)
+            for (int k = 0; k < N; k++) {
+                if (k == i) continue;
+                for (int n = 0; n < N; n++) {
+                    if (n == j) continue;
+                    const double sh = st->c[ix4(N, i, j, k, n)] / (double)(N - 2);
+                    for (int p = 0; p < N; p++) {
+                        if (p == i || p == k) continue;
+                        for (int q = 0; q < N; q++)
+                            if (q != j && q != n) st->d[ix6(N, i, j, k, n, p, q)] += sh;
+                    }
+                    st->c[ix4(N, i, j, k, n)] = 0.0;
+                }
+            }
+}
+
+void orf_spread_C_to_D(orf_state *st) { orf_spread_C_to_D_range(st, 0, st->N); }
+
+/* Complementary costs of D (Sec. 4.3): the six members of a class, in the
+ * lexicographic order of orc_complementary_D, are summed in that order and
+ * each becomes T / 6.  Smallest facilities i in [i_lo, i_hi) only. */
+void orf_complementary_D_range(orf_state *st, int i_lo, int i_hi)
+{
+    const int N = st->N;
+    double *d = st->d;
+    for (int i = i_lo; i < i_hi; i++)
+        for (int k = i + 1; k < N; k++)
+            for (int p = k + 1; p < N; p++)
+                for (int j = 0; j < N; j++)
+                    for (int n = 0; n < N; n++) {
+                        if (n == j) continue;
+                        for (int q = 0; q < N; q++) {
+                            if (q == j || q == n) continue;
+                            size_t mem[6] = {
+                                ix6(N, i, j, k, n, p, q), ix6(N, i, j, p, q, k, n),
+                                ix6(N, k, n, i, j, p, q), ix6(N, k, n, p, q, i, j),
+                                ix6(N, p, q, i, j, k, n), ix6(N, p, q, k, n, i, j)};
+                            double T = 0.0;
+                            for (int t = 0; t < 6; t++) T += d[mem[t]];
+                            for (int t = 0; t < 6; t++) d[mem[t]] = T / 6.0;
+                        }
+                    }
+}
+
+void orf_complementary_D(orf_state *st) { orf_complementary_D_range(st, 0, st->N); }
+
+/* Complementary costs of C (Sec. 4.3): T = c_ijkn + c_knij (i < k); both = T / 2. */
+void orf_complementary_C(orf_state *st)
+{
+    const int N = st->N;
+    for (int i = 0; i < N; i++)
+        for (int k = i + 1; k < N; k++)
+            for (int j = 0; j < N; j++)
+                for (int n = 0; n < N; n++) {
+                    if (n == j) continue;
+                    const double T = st->c[ix4(N, i, j, k, n)] + st->c[ix4(N, k, n, i, j)];
+                    st->c[ix4(N, i, j, k, n)] = T / 2.0;
+                    st->c[ix4(N, k, n, i, j)] = T / 2.0;
+                }
+}
+
+/* Concentration D -> C (Sec. 4.1): c_ijkn += LAP(D_ijkn); D_ijkn becomes
+ * (M - u) - v.  First indices i in [i_lo, i_hi) only. */
+void orf_concentrate_D_to_C_range(orf_state *st, int i_lo, int i_hi)
+{
+    const int N = st->N, m = N - 2;
+    double *M = malloc((size_t)m * m * sizeof(double));
+    double *u = malloc((size_t)m * sizeof(double));
+    double *v = malloc((size_t)m * sizeof(double));
+    int rows[64], cols[64];
+    for (int i = i_lo; i < i_hi; i++)
+        for (int j = 0; j < N; j++)
+            for (int k = 0; k < N; k++) {
+                if (k == i) continue;
+                for (int n = 0; n < N; n++) {
+                    if (n == j) continue;
+                    int r = 0, s = 0;
+                    for (int p = 0; p < N; p++) if (p != i && p != k) rows[r++] = p;
+                    for (int q = 0; q < N; q++) if (q != j && q != n) cols[s++] = q;
+                    for (r = 0; r < m; r++)
+                        for (s = 0; s < m; s++)
+                            M[r * m + s] = st->d[ix6(N, i, j, k, n, rows[r], cols[s])];
+                    const double S = orf_lap(m, M, u, v, NULL, NULL, st);
+                    st->c[ix4(N, i, j, k, n)] += S;
+                    for (r = 0; r < m; r++)
+                        for (s = 0; s < m; s++)
+                            st->d[ix6(N, i, j, k, n, rows[r], cols[s])] = M[r * m + s] - u[r] - v[s];
+                }
+            }
+    free(M); free(u); free(v);
+}
+
+void orf_concentrate_D_to_C(orf_state *st) { orf_concentrate_D_to_C_range(st, 0, st->N); }
+
+/* Concentration C -> B (Sec. 4.1): b_ij += LAP(C_ij); C_ij becomes (M - u) - v. */
+void orf_concentrate_C_to_B(orf_state *st)
+{
+    const int N = st->N, m = N - 1;
+    double *M = malloc((size_t)m * m * sizeof(double));
+    double *u = malloc((size_t)m * sizeof(double));
+    double *v = malloc((size_t)m * sizeof(double));
+    int rows[64], cols[64];
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            int r = 0, s = 0;
+            for (int k = 0; k < N; k++) if (k != i) rows[r++] = k;
+            for (int n = 0; n < N; n++) if (n != j) cols[s++] = n;
+            for (r = 0; r < m; r++)
+                for (s = 0; s < m; s++)
+                    M[r * m + s] = st->c[ix4(N, i, j, rows[r], cols[s])];
+            const double S = orf_lap(m, M, u, v, NULL, NULL, st);
+            st->b[ix2(N, i, j)] += S;
+            for (r = 0; r < m; r++)
+                for (s = 0; s < m; s++)
+                    st->c[ix4(N, i, j, rows[r], cols[s])] = M[r * m + s] - u[r] - v[s];
+        }
+    free(M); free(u); free(v);
+}
+
+/* Concentration B -> LB (Sec. 4.1): returns LAP(B); B becomes (M - u) - v. */
+double orf_concentrate_B_to_LB(orf_state *st)
+{
+    const int N = st->N;
+    double *u = malloc((size_t)N * sizeof(double));
+    double *v = malloc((size_t)N * sizeof(double));
+    double *M = malloc((size_t)N * N * sizeof(double));
+    memcpy(M, st->b, (size_t)N * N * sizeof(double));
+    const double S = orf_lap(N, M, u, v, NULL, NULL, st);
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+            st->b[ix2(N, i, j)] = M[i * N + j] - u[i] - v[j];
+    free(u); free(v); free(M);
+    return S;
+}
+
+/* One pass of Algorithm 1 in the FP64 form (order of reading R2). */
+double orf_iterate(orf_state *st)
+{
+    orf_spread_B_to_C(st);
+    if (!st->rlt1_only) {
+        orf_spread_C_to_D(st);
+        orf_complementary_D(st);
+        orf_concentrate_D_to_C(st);
+    }
+    orf_complementary_C(st);
+    orf_concentrate_C_to_B(st);
+    st->LB += orf_concentrate_B_to_LB(st);
+    st->iters++;
+    return st->LB;
+}
+
+void orf_run(orf_state *st, int k, double *hist)
+{
+    for (int t = 0; t < k; t++) {
+        double lb = orf_iterate(st);
+        if (hist) hist[t] = lb;
+    }
+}
+
+double orf_LB(const orf_state *st) { return st->LB; }
+void orf_add_LB(orf_state *st, double x) { st->LB += x; }
+double *orf_b(orf_state *st) { return st->b; }
+double *orf_c(orf_state *st) { return st->c; }
+double *orf_d(orf_state *st) { return st->d; }
+void orf_work(const orf_state *st, int64_t *out3)
+{
+    out3[0] = st->laps; out3[1] = st->steps; out3[2] = st->relaxations;
+}
