@@ -20,7 +20,9 @@
  *    may run on distinct streams concurrently.
  *  - Arithmetic is exact: reduced costs, potentials and LAP values are
  *    integers (int32 on the device, guarded against overflow at creation);
- *    the bound LB is carried in int64 and also reported as a double.
+ *    the bound LB is carried in int64 and also reported as a double.  The
+ *    rlt2_f64_* calls at the end are the FP64 form (the paper's real
+ *    division), in doubles.
  *
  * Notation (Sec. 3, Eq. (5)): x_ij / b_ij is the assignment variable and its
  * reduced cost (matrix B, N x N); x'_ijkn / c_ijkn the pair variable and its
@@ -389,6 +391,75 @@ int rlt2_lap_batch_auction(const int32_t *M, int n, int count, int64_t *S, int32
 #define RLT2_LAP_STATIC_MAX_N 64
 int rlt2_lap_batch_static(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,
                           int32_t *u, int32_t *v, int64_t *work, void *stream);
+
+/* ------------------------------------------------------------------------
+ * FP64 form (the paper's real division).
+ *
+ * The same seven operations of Algorithm 1 with double costs, potentials and
+ * bound: a cost x spread over m rows (Sec. 4.2) adds x/m (one IEEE division)
+ * to every coefficient of the submatrix; a class of s complementary costs
+ * (Sec. 4.3) is summed (from 0, in lexicographic rank order of its members)
+ * and each member becomes T/s; the Hungarian method is that of the integer
+ * form with every reduced distance formed as (M - u) - v and the potentials
+ * moved after every step; S sums the LAP's columns in ascending order.  Every
+ * double operation is defined in this order, so results are reproducible bit
+ * for bit.  D is kept as tiles of N-2 rows by N location columns (8 B
+ * N^3 (N-1)^2 (N-2); 5.1 GB at N = 30); no class or pair store, no groups,
+ * batches, checkpoints or stopping rule.
+ * ------------------------------------------------------------------------ */
+typedef struct rlt2_f64_ctx rlt2_f64_ctx;
+
+/*
+ * Create an FP64 context, initialised as rlt2_create's (c_ijkn = F_ik * D_jn,
+ * converted to double once).
+ *   F, D, N   as rlt2_create (host int32, entries >= 0, N in 3..64)
+ *   B_lin     host, N x N doubles >= 0 (finite), or NULL for 0
+ *   lb_const  constant part of the objective (finite)
+ *   opts      NULL or options: rlt1_only, profile, max_iters and stream are
+ *             used; the rest are ignored
+ * Errors: RLT2_E_INVAL, RLT2_E_OOM, RLT2_E_CUDA.
+ */
+int rlt2_f64_create(const int32_t *F, const int32_t *D, int N, const double *B_lin, double lb_const,
+                    const rlt2_opts *opts, rlt2_f64_ctx **out);
+void rlt2_f64_destroy(rlt2_f64_ctx *ctx);
+
+/* Enqueue k passes (stream-ordered, no wait).  Errors: RLT2_E_INVAL (k < 0),
+ * RLT2_E_STATE (more passes than opts.max_iters), RLT2_E_CUDA. */
+int rlt2_f64_iterate(rlt2_f64_ctx *ctx, int k);
+
+/* LB and the number of completed passes (synchronises).  Errors: RLT2_E_INTERNAL
+ * if a Hungarian invariant failed (not for finite inputs), RLT2_E_CUDA. */
+int rlt2_f64_bound(rlt2_f64_ctx *ctx, double *lb, int *iters);
+
+/* LB after each completed pass, oldest first, up to cap into host out. */
+int rlt2_f64_bound_history(rlt2_f64_ctx *ctx, double *out, int cap, int *count);
+
+/* Reduced costs into host doubles, in the compact layouts of the integer form
+ * (level 0 x: N*N, 1 y: N^2 (N-1)^2, 2 z: N^2 (N-1)^2 (N-2)^2).  Synchronises.
+ * Errors: RLT2_E_INVAL on a wrong count (or level 2 in RLT1 mode). */
+int rlt2_f64_get_state(rlt2_f64_ctx *ctx, int level, double *host_buf, size_t count);
+
+/* Device pointer of x (which 0), y (1) or z (2: tile t at t * (N-2) * N doubles,
+ * row r = rank of p among the facilities not in {i,k}, column = location q;
+ * columns j and n hold 0), or NULL. */
+void *rlt2_f64_device_state(rlt2_f64_ctx *ctx, int which);
+
+/* Hungarian work as rlt2_work; stage times (opts.profile) as rlt2_stage_times. */
+int rlt2_f64_work(rlt2_f64_ctx *ctx, int64_t out[6]);
+int rlt2_f64_stage_times(rlt2_f64_ctx *ctx, double out[4], int *passes);
+
+/*
+ * The FP64 Hungarian method on count n x n problems, one warp each:
+ *   M       device, count * n * n doubles, finite, row-major (left unchanged)
+ *   S       device, count doubles: the assignment cost (columns summed in order)
+ *   assign  device, count * n int32: column of each row (may be NULL)
+ *   u, v    device, count * n doubles: row and column potentials (may be NULL)
+ *   work    device, count * 2 int64: steps, relaxations (may be NULL)
+ * n in 1..64.  Synchronises the stream.  Errors: RLT2_E_INVAL, RLT2_E_INTERNAL
+ * (an invariant failed: a non-finite entry), RLT2_E_CUDA.
+ */
+int rlt2_f64_lap_batch(double *M, int n, int count, double *S, int32_t *assign, double *u, double *v,
+                       int64_t *work, void *stream);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librlt2.so")
-SOURCES = ["api.cu", "lap_kernels.cu", "sweep_kernels.cu", "lap_static.cu", "auction.cu"]
+SOURCES = ["api.cu", "lap_kernels.cu", "sweep_kernels.cu", "lap_static.cu", "auction.cu", "f64.cu"]
 HEADERS = ["device.cuh", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]

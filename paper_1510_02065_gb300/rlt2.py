@@ -100,6 +100,17 @@ def lib():
                                       _i32p, _i64p]),
         "rlt2_batch_bound": (C.c_int, [_i32p, _i32p, C.c_int, C.POINTER(rlt2_node), C.c_int, C.c_int,
                                        C.POINTER(rlt2_opts), _i64p, _dblp, _intp]),
+        "rlt2_f64_create": (C.c_int, [_i32p, _i32p, C.c_int, _dblp, C.c_double, C.POINTER(rlt2_opts),
+                                      C.POINTER(_vp)]),
+        "rlt2_f64_destroy": (None, [_vp]),
+        "rlt2_f64_iterate": (C.c_int, [_vp, C.c_int]),
+        "rlt2_f64_bound": (C.c_int, [_vp, _dblp, _intp]),
+        "rlt2_f64_bound_history": (C.c_int, [_vp, _dblp, C.c_int, _intp]),
+        "rlt2_f64_get_state": (C.c_int, [_vp, C.c_int, _dblp, C.c_size_t]),
+        "rlt2_f64_device_state": (_vp, [_vp, C.c_int]),
+        "rlt2_f64_work": (C.c_int, [_vp, _i64p]),
+        "rlt2_f64_stage_times": (C.c_int, [_vp, _dblp, _intp]),
+        "rlt2_f64_lap_batch": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -393,6 +404,125 @@ class Context:
     def close(self):
         if getattr(self, "ctx", None):
             rlt2_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------ FP64 form (rlt2_f64_*)
+
+def _pd(a):
+    return a.ctypes.data_as(_dblp)
+
+
+def rlt2_f64_create(F, D, N=None, B_lin=None, lb_const=0.0, opts=None):
+    F = np.ascontiguousarray(F, np.int32)
+    D = np.ascontiguousarray(D, np.int32)
+    N = int(F.shape[0]) if N is None else int(N)
+    bl = None
+    if B_lin is not None:
+        B_lin = np.ascontiguousarray(B_lin, np.float64)
+        bl = _pd(B_lin)
+    out = _vp()
+    _chk(lib().rlt2_f64_create(_p32(F), _p32(D), N, bl, float(lb_const),
+                               C.byref(opts) if opts is not None else None, C.byref(out)),
+         "rlt2_f64_create")
+    return out
+
+
+def rlt2_f64_destroy(ctx):
+    lib().rlt2_f64_destroy(ctx)
+
+
+def rlt2_f64_iterate(ctx, k: int):
+    _chk(lib().rlt2_f64_iterate(ctx, int(k)), "rlt2_f64_iterate")
+
+
+def rlt2_f64_bound(ctx):
+    lb = C.c_double()
+    it = C.c_int()
+    _chk(lib().rlt2_f64_bound(ctx, C.byref(lb), C.byref(it)), "rlt2_f64_bound")
+    return lb.value, it.value
+
+
+def rlt2_f64_bound_history(ctx, cap: int):
+    out = np.zeros(max(cap, 1))
+    cnt = C.c_int()
+    _chk(lib().rlt2_f64_bound_history(ctx, _pd(out), int(cap), C.byref(cnt)), "rlt2_f64_bound_history")
+    return out[: cnt.value]
+
+
+def rlt2_f64_get_state(ctx, level: int, N: int):
+    m = N - 1
+    count = {0: N * N, 1: N * N * m * m, 2: N * N * m * m * (N - 2) ** 2}[level]
+    out = np.zeros(count)
+    _chk(lib().rlt2_f64_get_state(ctx, int(level), _pd(out), count), "rlt2_f64_get_state")
+    return out
+
+
+def rlt2_f64_device_state(ctx, which: int) -> int:
+    return lib().rlt2_f64_device_state(ctx, int(which)) or 0
+
+
+def rlt2_f64_work(ctx):
+    out = np.zeros(6, np.int64)
+    _chk(lib().rlt2_f64_work(ctx, _p64(out)), "rlt2_f64_work")
+    return out
+
+
+def rlt2_f64_stage_times(ctx):
+    out = np.zeros(4)
+    n = C.c_int()
+    _chk(lib().rlt2_f64_stage_times(ctx, _pd(out), C.byref(n)), "rlt2_f64_stage_times")
+    return out, n.value
+
+
+def rlt2_f64_lap_batch(M_ptr, n, count, S_ptr, assign_ptr=0, u_ptr=0, v_ptr=0, work_ptr=0, stream=0):
+    """Device pointers (integers); returns the status code (0 = ok)."""
+    return lib().rlt2_f64_lap_batch(M_ptr or None, int(n), int(count), S_ptr or None, assign_ptr or None,
+                                    u_ptr or None, v_ptr or None, work_ptr or None, stream or None)
+
+
+class ContextF64:
+    """Owning wrapper of an rlt2_f64_ctx (the FP64 form)."""
+
+    def __init__(self, F, D, B_lin=None, lb_const=0.0, rlt1_only=False, profile=False, max_iters=65536,
+                 stream=0):
+        o = Context._opts(rlt1_only=rlt1_only, profile=profile, max_iters=max_iters, stream=stream)
+        self.N = int(np.asarray(F).shape[0])
+        self.ctx = rlt2_f64_create(F, D, self.N, B_lin, lb_const, o)
+
+    def iterate(self, k=1):
+        rlt2_f64_iterate(self.ctx, k)
+
+    def bound(self):
+        return rlt2_f64_bound(self.ctx)
+
+    def history(self, cap=None):
+        return rlt2_f64_bound_history(self.ctx, cap if cap is not None else 65536)
+
+    def state(self, level):
+        return rlt2_f64_get_state(self.ctx, level, self.N)
+
+    def work(self):
+        return rlt2_f64_work(self.ctx)
+
+    def stage_times(self):
+        return rlt2_f64_stage_times(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            rlt2_f64_destroy(self.ctx)
             self.ctx = None
 
     def __enter__(self):

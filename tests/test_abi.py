@@ -89,3 +89,38 @@ def test_binding_fails_loudly_without_library(tmp_path):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True)
     assert r.returncode == 0 and "raised" in r.stdout, r.stdout + r.stderr
+
+
+def _f64_create_rc(L, F, D, N, Bl=None, const=0.0):
+    F = np.ascontiguousarray(F, np.int32)
+    D = np.ascontiguousarray(D, np.int32)
+    ctx = C.c_void_p()
+    bl = None if Bl is None else np.ascontiguousarray(Bl, np.float64).ctypes.data_as(C.POINTER(C.c_double))
+    return L.rlt2_f64_create(F.ctypes.data_as(C.POINTER(C.c_int32)), D.ctypes.data_as(C.POINTER(C.c_int32)),
+                             N, bl, const, None, C.byref(ctx))
+
+
+def test_f64_create_rejects_bad_input_before_cuda(L):
+    Z = np.zeros((4, 4), np.int32)
+    assert _f64_create_rc(L, Z[:2, :2], Z[:2, :2], 2) == rlt2.RLT2_E_INVAL
+    assert _f64_create_rc(L, np.zeros((65, 65), np.int32), np.zeros((65, 65), np.int32), 65) == rlt2.RLT2_E_INVAL
+    F = Z.copy()
+    F[1, 0] = -2
+    assert _f64_create_rc(L, F, Z, 4) == rlt2.RLT2_E_INVAL
+    Bl = np.zeros((4, 4))
+    Bl[3, 1] = -0.5
+    assert _f64_create_rc(L, Z, Z, 4, Bl) == rlt2.RLT2_E_INVAL
+    Bl[3, 1] = np.nan
+    assert _f64_create_rc(L, Z, Z, 4, Bl) == rlt2.RLT2_E_INVAL
+    Bl[3, 1] = np.inf
+    assert _f64_create_rc(L, Z, Z, 4, Bl) == rlt2.RLT2_E_INVAL
+    assert _f64_create_rc(L, Z, Z, 4, None, float("nan")) == rlt2.RLT2_E_INVAL
+    assert L.rlt2_f64_create(None, None, 5, None, 0.0, None, C.byref(C.c_void_p())) == rlt2.RLT2_E_INVAL
+
+
+def test_f64_lap_batch_rejects_bad_arguments(L):
+    assert rlt2.rlt2_f64_lap_batch(0, 0, 1, 0) == rlt2.RLT2_E_INVAL
+    assert rlt2.rlt2_f64_lap_batch(0, 65, 1, 0) == rlt2.RLT2_E_INVAL
+    assert rlt2.rlt2_f64_lap_batch(0, 5, -1, 0) == rlt2.RLT2_E_INVAL
+    assert rlt2.rlt2_f64_lap_batch(0, 5, 3, 0) == rlt2.RLT2_E_INVAL
+    assert rlt2.rlt2_f64_lap_batch(0, 5, 0, 0) == rlt2.RLT2_OK
