@@ -69,6 +69,8 @@ def parse():
                     help="requests of the serving measurement (0: skip)")
     ap.add_argument("--store", default="tiles", choices=["tiles", "classes"],
                     help="store of D for the headline run (results are identical)")
+    ap.add_argument("--fp64-steps", type=int, default=10,
+                    help="passes of the FP64 form timed on the workload (0: skip)")
     ap.add_argument("--n35-steps", type=int, default=30,
                     help="timed passes of the 35-facility root bound (0: skip)")
     return ap.parse_args()
@@ -132,6 +134,49 @@ def n35_measure(rlt2, instances, torch, steps, store, warmup=3, workload="cluste
             "store": "%s (%.2f GB on the device)" % (
                 {rlt2.RLT2_STORE_CLASSES: "class sums", rlt2.RLT2_STORE_PAIRS: "pairs (Sec. 6)"}.get(store, "tiles"),
                 rlt2.rlt2_state_bytes(N, store=store) / 1e9)}
+
+
+def fp64_measure(rlt2, instances, torch, steps, workload="clustered_n30", warmup=3):
+    """The FP64 form (the paper's real division) on the headline workload, with
+    the roofline of its D->C kernel on the FP64 pipe: the additions the method
+    needs per Hungarian step (2 per reduced distance, 1 per label or potential
+    moved) over GB300's nominal FP64 rate (1.25 TFLOP/s = 625 G additions/s)."""
+    F, D, _ = instances.instance(workload)
+    N = F.shape[0]
+    n = N - 2
+    s = torch.cuda.Stream()
+    with rlt2.ContextF64(F, D, profile=True, max_iters=warmup + 2, stream=s.cuda_stream) as c:
+        c.iterate(warmup)
+        w0 = c.work()
+        st0, n0 = c.stage_times()
+        c.iterate(2)
+        st1, n1 = c.stage_times()
+        w1 = c.work()
+    ms = (st1 - st0) / (n1 - n0)
+    dsteps = (w1[4] - w0[4]) / 2.0
+    drelax = (w1[5] - w0[5]) / 2.0
+    adds = drelax + (2 * n + 1) * dsteps
+    with rlt2.ContextF64(F, D, max_iters=warmup + steps, stream=s.cuda_stream) as c:
+        c.iterate(warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        c.iterate(steps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        lb = c.bound()[0]
+    t = e0.elapsed_time(e1)
+    achieved = adds / (ms[1] / 1e3) / 1e9
+    return {"metric": "RLT2 dual-ascent iters/sec at N=%d, FP64 form" % N, "unit": "iters/s",
+            "value": steps / (t / 1000.0), "steps": steps, "LB": lb, "dtype": "f64",
+            "stages_ms": {"spread_complementary_D": ms[0], "concentrate_D_to_C": ms[1],
+                          "complementary_C_concentrate_C_to_B": ms[2], "concentrate_B_to_LB": ms[3]},
+            "roofline": {"bound": "fp64", "kernel": "f64_dlap_kernel (concentration D->C)",
+                         "achieved": achieved, "peak": 625.0, "unit": "Gadd/s", "frac": achieved / 625.0,
+                         "traffic": None,
+                         "peak_kind": "nominal FP64 1.25 TFLOP/s (an FMA = 2 flops; one addition per FMA slot)",
+                         "work": {"steps": dsteps, "relaxations": drelax, "fp64_adds": adds}}}
 
 
 def bnb_measure(instances, torch):
@@ -518,6 +563,8 @@ def main():
         line["pairs_n30"] = n35_measure(rlt2, instances, torch, 100, rlt2.RLT2_STORE_PAIRS,
                                         workload="clustered_n30")
         line["pairs_n35"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_PAIRS)
+    if args.fp64_steps > 0:
+        line["fp64"] = fp64_measure(rlt2, instances, torch, args.fp64_steps, workload=args.workload)
     if args.serve_requests > 0:
         line["serve"] = serve_measure(instances, torch, args.serve_requests)
     if args.batch_nodes > 0:

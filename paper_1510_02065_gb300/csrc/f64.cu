@@ -74,9 +74,13 @@ __device__ __forceinline__ int warp_argmin(long long key, int col)
 // improvement; the potentials move by delta after every step).  Column c of
 // the matrix lives in lane c % 32, slot c / 32: its potential v, distance
 // label, predecessor, labelled flag, the row matched to it and that row's
-// potential uM.  The row being inserted carries its potential ur in a
-// register.  M row r at M + r * ld; the LAP's n columns are the indices
-// c < width other than dead0 and dead1, in ascending order.
+// potential uM.  The row being inserted keeps its potential in the uM slot of
+// column dead0 when there is one (a column without coefficient, which is
+// never matched), so that one addition moves it with the rows of the labelled
+// columns; else in a register.  The labelled columns' v and the unlabelled
+// columns' distance labels move by the same -delta in one addition.  M row r
+// at M + r * ld; the LAP's n columns are the indices c < width other than
+// dead0 and dead1, in ascending order.
 // Out: rowOf, uM, v per column slot; S = the sum over the columns in ascending
 // order of M[row][column], from 0; steps, relax += the work (as the int form
 // counts it).  Returns false if an invariant fails (not for finite entries).
@@ -87,11 +91,14 @@ __device__ bool hungarian_f64(const double *M, int ld, int n, int width, int dea
 {
     const int lane = threadIdx.x & 31;
     const double kInfD = __longlong_as_double(0x7ff0000000000000LL);
-    bool valid[NS];
+    const bool rootInLane = dead0 >= 0;
+    const int rl = dead0 & 31, rs = dead0 >> 5;
+    bool valid[NS], root[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int c = lane + 32 * s;
         valid[s] = c < width && c != dead0 && c != dead1;
+        root[s] = c == dead0;
         rowOf[s] = -1;
         uM[s] = 0.0;
         v[s] = 0.0;
@@ -105,6 +112,7 @@ __device__ bool hungarian_f64(const double *M, int ld, int n, int width, int dea
             dist[s] = kInfD;
             way[s] = -1;
             lab[s] = false;
+            if (root[s]) uM[s] = 0.0;  // u of row r before its insertion
         }
         double ur = 0.0, ui0 = 0.0;
         int col = -1, i0 = r, next = -1, K = 0;
@@ -137,15 +145,13 @@ __device__ bool hungarian_f64(const double *M, int ld, int n, int width, int dea
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 if (valid[s]) {
-                    if (lab[s]) {
-                        uM[s] += delta;
-                        v[s] -= delta;
-                    } else {
-                        dist[s] -= delta;
-                    }
+                    const double moved = (lab[s] ? v[s] : dist[s]) - delta;
+                    if (lab[s]) v[s] = moved;
+                    else dist[s] = moved;
                 }
+                if (lab[s] || root[s]) uM[s] += delta;
             }
-            ur += delta;
+            if (!rootInLane) ur += delta;
             const int rj = __shfl_sync(kFull, pick<NS>(rowOf, sl), src);
             const double uj = __shfl_sync(kFull, pick<NS>(uM, sl), src);
             if (rj < 0) break;  // free column: augmenting path found
@@ -156,6 +162,7 @@ __device__ bool hungarian_f64(const double *M, int ld, int n, int width, int dea
         }
         steps += (unsigned)K;
         relax += (unsigned)(n * K - K * (K - 1) / 2);
+        if (rootInLane) ur = __shfl_sync(kFull, pick<NS>(uM, rs), rl);
         // augment: each column on the path takes the row (and its potential)
         // of its predecessor; the first takes row r
         int c = next;
