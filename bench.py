@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RLT2 dual-ascent iters/sec at N=30"
 OPS_PER_RELAXATION = 9   # textbook int ops of one relaxation
+ALU_LANES_PER_SM = 64    # integer ALU pipe: 16 lanes per scheduler, 4 schedulers
 # DRAM bytes per launch of the D->C and fused-pass kernels on the 30-facility
 # workload (tile store), from one ncu capture (profiles/dram_dlap_p1_clustered_n30.md);
 # reported only while the kernel's sources hash to the captured version.
@@ -478,9 +479,13 @@ def main():
     t_clap = stage_ms[2] / passes
     t_xlap = stage_ms[3] / passes
 
-    # roofline of the dominant kernel (D -> C concentration): integer ALU bound
+    # roofline of the dominant kernel (D -> C concentration): integer ALU bound.
+    # The ALU pipe (integer compare, select, add, logic, shift) takes one warp
+    # instruction every two cycles per scheduler: 64 lanes per SM per clock
+    # (ncu on this kernel: issue slots 85.8% busy, ALU pipe 85.7% of its peak,
+    # FMA and MIO pipes about 22% each -- only a half-rate ALU pipe fits).
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12   # Tops/s int32
+    alu_peak = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12   # Tops/s
     achieved = OPS_PER_RELAXATION * d_relax / (t_dlap / 1e3) / 1e12
     n_tiles = N * N * (N - 1) ** 2
     m = N - 2
@@ -515,8 +520,8 @@ def main():
         "roofline": {"bound": "alu", "kernel": "dlap_kernel (concentration D->C)",
                      "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
-                     "peak_kind": "%d SMs x 128 int32 lanes x %.0f MHz (%s sm_max)" % (
-                         props.multi_processor_count, sm_max, peaks_kind),
+                     "peak_kind": "%d SMs x %d ALU-pipe lanes x %.0f MHz (%s sm_max)" % (
+                         props.multi_processor_count, ALU_LANES_PER_SM, sm_max, peaks_kind),
                      "work": {"laps": d_laps, "steps": d_steps, "relaxations": d_relax,
                               "ops_per_relaxation": OPS_PER_RELAXATION},
                      "hbm_gbs": dlap_hbm_gbs},
