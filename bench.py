@@ -137,6 +137,29 @@ def n35_measure(rlt2, instances, torch, steps, store, warmup=3, workload="cluste
                 rlt2.rlt2_state_bytes(N, store=store) / 1e9)}
 
 
+# DRAM bytes of one f64_dlap_kernel launch at N=20 (profiles/f64_launches_dram_clustered_n20.md)
+# per tile coefficient read (n x N per tile) and written (n x n), valid while
+# the FP64 sources hash to the captured version; other sizes scale by those units
+F64_DLAP_TRAFFIC = {"N": 20, "read": 417196544, "write": 355250688, "files": ("f64.cu", "device.cuh"),
+                    "sources_sha1": "f5aa7005c8fb1d0b9466a9a6bb85d7eb947e496e"}
+
+
+def f64_traffic(N):
+    import hashlib
+    rec = F64_DLAP_TRAFFIC
+    h = hashlib.sha1()
+    for f in rec["files"]:
+        with open(os.path.join(ROOT, "paper_1510_02065_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec["sources_sha1"]:
+        return None
+    M = rec["N"]
+    tiles = lambda K: K * K * (K - 1) ** 2
+    rd = rec["read"] / (tiles(M) * (M - 2) * M) * tiles(N) * (N - 2) * N
+    wr = rec["write"] / (tiles(M) * (M - 2) ** 2) * tiles(N) * (N - 2) ** 2
+    return int(rd + wr)
+
+
 def fp64_measure(rlt2, instances, torch, steps, workload="clustered_n30", warmup=3):
     """The FP64 form (the paper's real division) on the headline workload, with
     the roofline of its D->C kernel on the FP64 pipe: the additions the method
@@ -175,7 +198,8 @@ def fp64_measure(rlt2, instances, torch, steps, workload="clustered_n30", warmup
                           "complementary_C_concentrate_C_to_B": ms[2], "concentrate_B_to_LB": ms[3]},
             "roofline": {"bound": "fp64", "kernel": "f64_dlap_kernel (concentration D->C)",
                          "achieved": achieved, "peak": 625.0, "unit": "Gadd/s", "frac": achieved / 625.0,
-                         "traffic": None,
+                         "traffic": f64_traffic(N),
+                         "traffic_kind": "ncu DRAM bytes of the N=20 launch, scaled per tile coefficient",
                          "peak_kind": "nominal FP64 1.25 TFLOP/s (an FMA = 2 flops; one addition per FMA slot)",
                          "work": {"steps": dsteps, "relaxations": drelax, "fp64_adds": adds}}}
 

@@ -6,12 +6,14 @@
 // Every floating-point operation is the one the FP64 form defines, in its
 // order, so that device and definition agree bit for bit:
 //   spread B->C   c_ijkn = c_ijkn + b_ij / (N-1)
-//   spread C->D   d_ijknpq = d_ijknpq + c_ijkn / (N-2)
+//   spread C->D   d_ijknpq = d_ijknpq + c_ijkn / (N-2), c_ijkn = 0
 //   complementary D  T = 0 + six members in lexicographic rank order; each = T/6
-//   D->C          c_ijkn = c_ijkn + S; D_ijkn = (M - u) - v      (Hungarian below)
+//                 (spread C->D and this transfer run as one kernel)
+//   D->C          c_ijkn = 0 + S; D_ijkn = (M - u) - v      (Hungarian below)
 //   complementary C  T = c_ijkn + c_knij (i < k); both = T/2
 //   C->B, B->LB   b_ij = b_ij + S, LB = LB + S; residuals (M - u) - v
-// One kernel per operation; the LAP kernels run one warp per problem.
+// One kernel per operation (the two spreads into D fused); the LAP kernels run
+// one warp per problem.
 //
 // Layouts: x = b[i][j] (N*N); y = c in tile order t = ((i*N + j)(N-1) + k')(N-1)
 // + n' (C_ij is a contiguous (N-1)^2 block); z = tile t holds N-2 rows (p not
@@ -235,53 +237,99 @@ __global__ void f64_spread_x_kernel(F64Dev d)
         d.y[t] += d.x[t / mm] / (double)(d.N - 1);
 }
 
-// spread C -> D, one warp per tile: every d of the tile += c / (N-2); c = 0
-__global__ void f64_spread_y_kernel(F64Dev d)
+// Spread C -> D fused with the transfer between complementary costs of D: one
+// CTA per facility triple a < b < c and location la, i.e. the classes
+// {(a,la),(b,lb),(c,lc)} for every lb != la and lc not in {la, lb}.  Their
+// members, in lexicographic rank order, are
+//   m0 = d(a la, b lb, c lc)  row c of tile (a,la,b,lb), column lc
+//   m1 = d(a la, c lc, b lb)  row b of tile (a,la,c,lc), column lb
+//   m2 = d(b lb, a la, c lc)  row c of tile (b,lb,a,la), column lc
+//   m3 = d(b lb, c lc, a la)  row a of tile (b,lb,c,lc), column la
+//   m4 = d(c lc, a la, b lb)  row b of tile (c,lc,a,la), column lb
+//   m5 = d(c lc, b lb, a la)  row a of tile (c,lc,b,lb), column la
+// Kinds 0, 1, 2, 4 fill whole tile rows (every coefficient of such a row
+// belongs to one of the CTA's classes), so they move as contiguous rows
+// through shared memory; kinds 3 and 5 are single coefficients.  Each
+// coefficient first takes its tile's share (z + c/(N-2): spread C -> D), then
+// T = 0 + m0 + ... + m5 and every member becomes T/6.  On entry y holds the
+// shares (f64_share_kernel); it is not cleared here (other CTAs read it):
+// D -> C writes c = 0 + S.
+__global__ void __launch_bounds__(kF64Threads) f64_p1_kernel(F64Dev d)
 {
-    const int lane = threadIdx.x & 31;
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long t = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); t < d.tiles; t += nw) {
-        int i, j, k, n;
-        decode_tile(d, t, i, j, k, n);
-        const double sh = d.y[t] / (double)(d.N - 2);
-        double *zt = d.z + (size_t)t * d.TS;
-        for (int r = 0; r < d.n; ++r)
-            for (int q = lane; q < d.N; q += 32)
-                if (q != j && q != n) zt[r * d.N + q] += sh;
-        __syncwarp();
-        if (lane == 0) d.y[t] = 0.0;
+    extern __shared__ double f64_smem[];
+    const int N = d.N, m = d.m, TS = d.TS, NN = N * N;
+    const int4 tr = d.triples[blockIdx.x / N];
+    const int la = (int)(blockIdx.x % N);
+    const int a = tr.x, b = tr.y, c = tr.z;
+    double *A[4] = {f64_smem, f64_smem + NN, f64_smem + 2 * NN, f64_smem + 3 * NN};
+    auto tile = [&](int i, int j, int k, int n) -> long long {
+        return ((long long)(i * N + j) * m + (k - (k > i))) * m + (n - (n > j));
+    };
+    // row source of kind slot s (0: m0, 1: m1, 2: m2, 3: m4) for the row's own location x
+    auto row_tile = [&](int s, int x) -> long long {
+        return s == 0 ? tile(a, la, b, x) : s == 1 ? tile(a, la, c, x) : s == 2 ? tile(b, x, a, la) : tile(c, x, a, la);
+    };
+    auto row_of = [&](int s) -> int { return (s == 0 || s == 2) ? c - 2 : b - 1; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int sr = warp; sr < 4 * N; sr += nw) {
+        const int s = sr / N, x = sr - s * N;
+        if (x == la) continue;
+        const long long t = row_tile(s, x);
+        const double sh = d.y[t];  // the tile's share c/(N-2)
+        const double *src = d.z + (size_t)t * TS + (size_t)row_of(s) * N;
+        double *dst = A[s] + x * N;
+        for (int q = lane; q < N; q += 32) {
+            double v = src[q];
+            if (q != la && q != x) v = v + sh;
+            dst[q] = v;
+        }
     }
-}
-
-// transfer between complementary costs of D, one thread per class
-// {(a,la),(b,lb),(c,lc)}, a < b < c: members in lexicographic rank order
-__global__ void f64_complementary_D_kernel(F64Dev d)
-{
-    const int N = d.N;
-    const long long L3 = (long long)N * (N - 1) * (N - 2);
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < d.classes;
-         g += (long long)gridDim.x * blockDim.x) {
-        const int4 tr = d.triples[g / L3];
-        long long rem = g % L3;
-        const int lcp = (int)(rem % (N - 2));
-        rem /= (N - 2);
-        const int lbp = (int)(rem % (N - 1));
-        const int la = (int)(rem / (N - 1));
+    __syncthreads();
+    const int cls = (N - 1) * (N - 2);
+    for (int e = threadIdx.x; e < cls; e += blockDim.x) {
+        const int lbp = e / (N - 2), lcp = e - lbp * (N - 2);
         const int lb = lbp + (lbp >= la);
         const int lo = la < lb ? la : lb, hi = la < lb ? lb : la;
         int lc = lcp + (lcp >= lo);
         lc += (lc >= hi);
-        const int a = tr.x, b = tr.y, c = tr.z;
-        const size_t mem[6] = {zaddr(d, a, la, b, lb, c, lc), zaddr(d, a, la, c, lc, b, lb),
-                               zaddr(d, b, lb, a, la, c, lc), zaddr(d, b, lb, c, lc, a, la),
-                               zaddr(d, c, lc, a, la, b, lb), zaddr(d, c, lc, b, lb, a, la)};
+        const long long t3 = tile(b, lb, c, lc), t5 = tile(c, lc, b, lb);
+        double *p3 = d.z + (size_t)t3 * TS + (size_t)a * N + la;
+        double *p5 = d.z + (size_t)t5 * TS + (size_t)a * N + la;
+        const double m3 = *p3 + d.y[t3];
+        const double m5 = *p5 + d.y[t5];
         double T = 0.0;
-#pragma unroll
-        for (int e = 0; e < 6; ++e) T += d.z[mem[e]];
+        T += A[0][lb * N + lc];
+        T += A[1][lc * N + lb];
+        T += A[2][lb * N + lc];
+        T += m3;
+        T += A[3][lc * N + lb];
+        T += m5;
         const double each = T / 6.0;
-#pragma unroll
-        for (int e = 0; e < 6; ++e) d.z[mem[e]] = each;
+        A[0][lb * N + lc] = each;
+        A[1][lc * N + lb] = each;
+        A[2][lb * N + lc] = each;
+        A[3][lc * N + lb] = each;
+        *p3 = each;
+        *p5 = each;
     }
+    __syncthreads();
+    for (int sr = warp; sr < 4 * N; sr += nw) {
+        const int s = sr / N, x = sr - s * N;
+        if (x == la) continue;
+        double *dst = d.z + (size_t)row_tile(s, x) * TS + (size_t)row_of(s) * N;
+        const double *src = A[s] + x * N;
+        for (int q = lane; q < N; q += 32)
+            if (q != la && q != x) dst[q] = src[q];
+    }
+}
+
+// c_ijkn <- c_ijkn / (N-2): the share of every coefficient of tile D_ijkn in
+// spread C -> D, formed once per tile (f64_p1_kernel adds it)
+__global__ void f64_share_kernel(F64Dev d)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < d.tiles;
+         t += (long long)gridDim.x * blockDim.x)
+        d.y[t] = d.y[t] / (double)(d.N - 2);
 }
 
 // concentration D -> C, one warp per tile (tile and u of its rows in shared memory)
@@ -319,7 +367,7 @@ __global__ void __launch_bounds__(kF64Warps * 32) f64_dlap_kernel(F64Dev d)
                 if (c < N && c != j && c != nl) zt[r * N + c] = (buf[r * N + c] - ur) - v[s];
             }
         }
-        if (lane == 0) d.y[t] = d.y[t] + S;
+        if (lane == 0) d.y[t] = 0.0 + S;  // c was spread to D (cleared), then += S
         ++laps;
         __syncwarp();
     }
@@ -537,9 +585,11 @@ static int f64_pass(rlt2_f64_ctx *c)
     CKF(cudaGetLastError());
     CKF(cudaMemsetAsync(d.x, 0, (size_t)d.N * d.N * sizeof(double), s));
     if (!c->rlt1_only) {
-        f64_spread_y_kernel<<<grid_for(d.tiles, kF64Threads / 32), kF64Threads, 0, s>>>(d);
+        const size_t sm = 4 * (size_t)d.N * d.N * sizeof(double);
+        CKF(cudaFuncSetAttribute(f64_p1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        f64_share_kernel<<<ew, kF64Threads, 0, s>>>(d);
         CKF(cudaGetLastError());
-        f64_complementary_D_kernel<<<grid_for(d.classes, kF64Threads), kF64Threads, 0, s>>>(d);
+        f64_p1_kernel<<<(unsigned)(d.classes / ((long long)(d.N - 1) * (d.N - 2))), kF64Threads, sm, s>>>(d);
         CKF(cudaGetLastError());
         CKF(mark(1));
         CKF(launch_f64_dlap(d, s));
