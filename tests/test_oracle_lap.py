@@ -6,7 +6,16 @@
 * N!-enumeration: S is the minimum over all permutations, sigma attains it,
   and (u, v) is a dual certificate (M - u - v >= 0, zero on sigma,
   sum u + sum v = S) -- the LP duality of the assignment problem;
-* scipy.optimize.linear_sum_assignment optimum values for n up to 64.
+* scipy.optimize.linear_sum_assignment optimum values for n up to 64;
+* the exact duals: started from u = v = 0 the method ends at the optimal dual
+  with the largest v subject to v <= 0 (the minimum competitive prices
+  p = -v of the assignment market, which an exact ascending auction -- the
+  Hungarian method -- reaches whatever the order of the rows).  That dual is
+  computed independently: for any optimal assignment sigma (scipy), v_j is
+  the shortest distance to column j from a source joined to every column by a
+  0-weight edge, in the graph with an edge sigma(i) -> j of weight
+  M[i][j] - M[i][sigma(i)] (Bellman-Ford), and u_i = M[i][sigma(i)] -
+  v_sigma(i).  This pins (u, v) themselves, not only their optimality.
 """
 import itertools
 
@@ -96,3 +105,33 @@ def test_batch_equals_single(orc):
     for t in range(10):
         s1, g1, u1, v1, _ = orc.lap(Ms[t])
         assert s1 == S[t] and (g1 == sig[t]).all() and (u1 == u[t]).all() and (v1 == v[t]).all()
+
+
+def _minimum_price_duals(M):
+    n = M.shape[0]
+    r, c = linear_sum_assignment(M)
+    sig = np.empty(n, np.int64)
+    sig[r] = c
+    row_of = np.empty(n, np.int64)
+    row_of[c] = r
+    W = M[row_of, :] - M[row_of, np.arange(n)][:, None]   # W[k, j]: edge k -> j
+    d = np.zeros(n, np.int64)
+    for _ in range(n + 1):
+        nd = np.minimum(d, (d[:, None] + W).min(0))
+        if (nd == d).all():
+            break
+        d = nd
+    assert (nd == d).all()  # no negative cycle: sigma is optimal
+    return M[np.arange(n), sig] - d[sig], d
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12, 18, 28, 33])
+def test_duals_are_the_minimum_price_duals(orc, n):
+    rng = np.random.default_rng(700 + n)
+    Ms = np.concatenate([rng.integers(0, 3, size=(40, n, n)),         # heavy ties
+                         rng.integers(0, 20, size=(40, n, n)),
+                         rng.integers(0, 10**6, size=(20, n, n))])
+    S, sig, u, v, _ = orc.lap_batch(Ms)
+    for t in range(len(Ms)):
+        cu, cv = _minimum_price_duals(Ms[t])
+        assert (u[t] == cu).all() and (v[t] == cv).all(), t
