@@ -500,8 +500,16 @@ template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
 static cudaError_t dlap_fit(const Group &g, int &warps_per_sm)
 {
     const size_t smem = (size_t)WARPS * ((size_t)g.maxTS * 4 + 8);
+    // a CTA size whose tile buffers exceed a CTA's shared memory (large N:
+    // 16 warps from N = 61, 32 warps from N = 44) keeps no warp resident
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    warps_per_sm = 0;
+    if (smem > (size_t)optin) return cudaSuccess;
     auto k = dlap_kernel<NS, PACK, ONE, MODE, WARPS>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WARPS * 32, smem);
