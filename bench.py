@@ -33,10 +33,10 @@ ALU_LANES_PER_SM = 64    # integer ALU pipe: 16 lanes per scheduler, 4 scheduler
 # DRAM bytes per launch of the D->C and fused-pass kernels on the 30-facility
 # workload (tile store), from one ncu capture (profiles/dram_dlap_p1_clustered_n30.md);
 # reported only while the kernel's sources hash to the captured version.
-DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2714472704 + 2651894528,
+DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2714500096 + 2651857664,
                 "files": ("lap_kernels.cu", "device.cuh", "kernels.h"),
-                "sources_sha1": "8f72c099ba58a2d2388ce333a90eb70659637f27"}
-P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2740685568 + 2655290368,
+                "sources_sha1": "5cbf08ab80b8cebb8819b0dad2144aa00515209f"}
+P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2740532224 + 2655434496,
               "files": ("sweep_kernels.cu", "device.cuh", "kernels.h"),
               "sources_sha1": "0eafd798ec382b4ec2a33a9443f411e39707fa44"}
 
