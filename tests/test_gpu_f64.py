@@ -7,7 +7,9 @@ included):
   matrices, n = 1..64 (one and two column slots per lane), ragged counts;
 * the full state (B, C, D in the compact layouts), LB and work after every pass
   on the 8- and 12-facility workloads, small asymmetric instances with linear
-  terms and constants, and two passes of the 20-facility workload;
+  terms and constants, and two passes of the 20-facility workload; all 200
+  passes of that workload against the oracle's stored LB bit patterns and
+  state hashes;
 * RLT1 mode up to N = 40 (two column slots in C -> B and B -> LB);
 * the 30-facility workload (the benchmark's configuration) and N = 33 (D -> C
   LAPs on two column slots): the first pass on sampled entries of three
@@ -133,6 +135,30 @@ def test_n20_two_passes(gpu, orc):
             ctx.iterate(1)
             st.iterate()
             assert_same_state(ctx, st, "after pass %d" % (t + 1))
+
+
+def test_n20_against_golden_200_passes(gpu):
+    """All 200 passes of the 20-facility workload against the bit patterns of
+    the oracle's LB history and state hashes (tests/golden/lb_f64_clustered_n20.json,
+    written by tests/golden/make_golden.py --f64 from the oracle alone)."""
+    import json
+    import os
+    from tests.layout import state_hash
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "lb_f64_clustered_n20.json")))
+    F, D, iters = I.instance("clustered_n20")
+    N = 20
+    with rlt2.ContextF64(F, D) as ctx:
+        done = 0
+        for t in sorted(int(k) for k in gold["hash"]):
+            ctx.iterate(t - done)
+            done = t
+            h = gold["hash"][str(t)]
+            assert state_hash(bits(ctx.state(0))) == h["x"], "B after pass %d" % t
+            assert state_hash(bits(ctx.state(1))) == h["y"], "C after pass %d" % t
+            assert state_hash(bits(ctx.state(2).reshape(-1, N - 2, N - 2))) == h["z"], "D after pass %d" % t
+        assert done == iters
+        assert list(bits(ctx.history())) == gold["lb_bits"]
 
 
 def _first_pass_then_properties(orc, F, D, N, seed):
