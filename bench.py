@@ -400,6 +400,20 @@ def oracle_sample(F, D, budget_s, steps=None):
     return t_pass, len(slice_times), rest
 
 
+def oracle_all_cores(F, D):
+    """One full pass (pass 1, all seven operations) of the CPU oracle with its
+    operations over D split by facility over every host core
+    (State.iterate_threaded; the same result as the sequential pass)."""
+    from oracle import oracle as O
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    st = O.State(F, D)
+    t0 = time.perf_counter()
+    st.iterate_threaded(threads)
+    t = time.perf_counter() - t0
+    st.close()
+    return t, threads
+
+
 def reference_arm(args):
     """--impl reference: the CPU oracle as it stands, one sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -607,6 +621,11 @@ def main():
             "sample": "pass 1: spread/complementary and C/B operations in full (%.1f s), D->C "
                       "concentration on %d facility slices of %d LAPs each, extrapolated to %d "
                       "slices; single-threaded C oracle" % (rest, nslices, N * (N - 1) ** 2, N)}
+        t_all, threads = oracle_all_cores(F, D)
+        line["cpu_baseline_all_cores"] = {
+            "value": 1.0 / t_all, "unit": "iters/s", "cores": threads, "kind": "oracle",
+            "sample": "one full pass 1 (all seven operations, %.1f s), the operations over D split by "
+                      "facility over %d host threads; C oracle as it stands" % (t_all, threads)}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

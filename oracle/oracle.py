@@ -202,6 +202,29 @@ class State:
     def iterate(self):
         return int(lib().orc_iterate(self._h))
 
+    def iterate_threaded(self, threads):
+        """One pass of Algorithm 1, the three operations over D split by
+        facility (the oracle's _range functions) over `threads` host threads.
+        ctypes releases the GIL during each call, and the ranges of one
+        operation write disjoint entries (their own first facility, or for the
+        complementary transfer the classes of their smallest facility), so the
+        result is that of iterate(); the work counters are updated without
+        synchronisation and may undercount.  For timing on all host cores."""
+        from concurrent.futures import ThreadPoolExecutor
+        assert not self.paired, "the paired spread writes into other facilities' tiles"
+        N = self.N
+        lib().orc_spread_B_to_C(self._h)
+        if not self.rlt1_only:
+            with ThreadPoolExecutor(max_workers=threads) as ex:
+                for fn in (self.spread_C_to_D_range, self.complementary_D_range,
+                           self.concentrate_D_to_C_range):
+                    # one task per facility, the costliest (smallest i) first
+                    list(ex.map(lambda i: fn(i, i + 1), range(N)))
+        lib().orc_complementary_C(self._h)
+        lib().orc_concentrate_C_to_B(self._h)
+        self.add_LB(self.concentrate_B_to_LB())
+        return self.LB
+
     def run(self, k):
         hist = np.zeros(k, np.int64)
         lib().orc_run(self._h, k, _p64(hist))
