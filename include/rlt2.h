@@ -458,7 +458,7 @@ int rlt2_f64_stage_times(rlt2_f64_ctx *ctx, double out[4], int *passes);
  * n in 1..64.  Synchronises the stream.  Errors: RLT2_E_INVAL, RLT2_E_INTERNAL
  * (an invariant failed: a non-finite entry), RLT2_E_CUDA.
  */
-int rlt2_f64_lap_batch(double *M, int n, int count, double *S, int32_t *assign, double *u, double *v,
+int rlt2_f64_lap_batch(const double *M, int n, int count, double *S, int32_t *assign, double *u, double *v,
                        int64_t *work, void *stream);
 
 #ifdef __cplusplus

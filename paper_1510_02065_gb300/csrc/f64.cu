@@ -824,7 +824,7 @@ int rlt2_f64_stage_times(rlt2_f64_ctx *c, double out[4], int *passes)
     return RLT2_OK;
 }
 
-int rlt2_f64_lap_batch(double *M, int n, int count, double *S, int32_t *assign, double *u, double *v,
+int rlt2_f64_lap_batch(const double *M, int n, int count, double *S, int32_t *assign, double *u, double *v,
                        int64_t *work, void *stream)
 {
     if (n < 1 || n > 64 || count < 0 || (count > 0 && (!M || !S))) return RLT2_E_INVAL;
@@ -833,7 +833,9 @@ int rlt2_f64_lap_batch(double *M, int n, int count, double *S, int32_t *assign, 
     DevStatus *st = nullptr;
     CKF(cudaMallocAsync((void **)&st, sizeof(DevStatus), s));
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
-    if (e == cudaSuccess) e = launch_f64_lap(M, n, count, S, nullptr, assign, u, v, work, false, st, false, s);
+    // residual = false: the kernel only reads M
+    if (e == cudaSuccess)
+        e = launch_f64_lap(const_cast<double *>(M), n, count, S, nullptr, assign, u, v, work, false, st, false, s);
     int err = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &st->err, 4, cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(st, s);
