@@ -1,8 +1,8 @@
-"""The largest instances: N = 64 (the largest the library accepts) in the
-class-sum store (about 52 GB on the device; the tile store would need 258 GB),
-N = 48 in the tile store (45 GB) and in the pair store (23 GB), all beyond the
-sizes at which the D->C kernel's larger CTA shapes stop fitting in shared
-memory.
+"""Large instances, beyond the sizes at which the D->C kernel's larger CTA
+shapes stop fitting in shared memory and the fused pass moves fewer locations
+per chunk: N = 41, 44, 53 and 64 (the largest the library accepts; about 52 GB
+on the device) in the class-sum store, N = 44 and 48 in the tile store (45 GB
+at 48) and in the pair store.
 
 The oracle cannot hold D at N = 64 (N^6 dense entries), so the first pass is
 checked on sampled tiles (read from device memory): the D -> C input of a
@@ -145,9 +145,9 @@ def _d2h_int32(ptr, count):
 
 @pytest.mark.gpu
 @pytest.mark.slow
-def test_class_store_n64_first_pass_sampled(orc):
+@pytest.mark.parametrize("N", [41, 44, 53, 64])
+def test_class_store_large_first_pass_sampled(orc, N):
     rlt2 = _gpu()
-    N = 64
     F, D = I.clustered_euclid(N, seed=N)
     m, n = N - 1, N - 2
     W = rlt2.rlt2_row_stride(N)
@@ -182,9 +182,9 @@ def test_class_store_n64_first_pass_sampled(orc):
 
 @pytest.mark.gpu
 @pytest.mark.slow
-def test_tile_store_n48_first_pass_sampled(orc):
+@pytest.mark.parametrize("N", [44, 48])
+def test_tile_store_large_first_pass_sampled(orc, N):
     rlt2 = _gpu()
-    N = 48
     F, D = I.clustered_euclid(N, seed=N)
     m, n = N - 1, N - 2
     W = rlt2.rlt2_row_stride(N)
@@ -216,11 +216,11 @@ def test_tile_store_n48_first_pass_sampled(orc):
 
 @pytest.mark.gpu
 @pytest.mark.slow
-def test_pair_store_n48_first_pass_sampled(orc):
-    """The pair store (Sec. 6's complementary submatrices, reading R13) at
-    N = 48: pair tiles (i < k) indexed ((C(k,2) + i) N + j)(N-1) + n'."""
+@pytest.mark.parametrize("N", [44, 48])
+def test_pair_store_large_first_pass_sampled(orc, N):
+    """The pair store (Sec. 6's complementary submatrices, reading R13): pair
+    tiles (i < k) indexed ((C(k,2) + i) N + j)(N-1) + n'."""
     rlt2 = _gpu()
-    N = 48
     F, D = I.clustered_euclid(N, seed=N + 1)
     m, n = N - 1, N - 2
     W = rlt2.rlt2_row_stride(N)
