@@ -596,9 +596,12 @@ def main():
                        "includes": "rlt2_create (alloc, H2D, init) + per step rlt2_iterate(1) + "
                                    "rlt2_bound + rlt2_destroy"}
 
-    if args.batch_nodes > 0:
+    # the single-GPU measurements beside the metric run at N = 1 only (a
+    # multi-GPU run times the replicas and does not hold its GPUs longer)
+    solo = world == 1
+    if args.batch_nodes > 0 and solo:
         line["batch"] = batch_measure(rlt2, instances, torch, args.batch_nodes, args.batch_iters)
-    if args.n35_steps > 0:
+    if args.n35_steps > 0 and solo:
         line["n35"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_CLASSES)
         line["n35_tiles"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_TILES)
         # the paired dual ascent of Sec. 6's complementary submatrices (another
@@ -606,11 +609,11 @@ def main():
         line["pairs_n30"] = n35_measure(rlt2, instances, torch, 100, rlt2.RLT2_STORE_PAIRS,
                                         workload="clustered_n30")
         line["pairs_n35"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_PAIRS)
-    if args.fp64_steps > 0:
+    if args.fp64_steps > 0 and solo:
         line["fp64"] = fp64_measure(rlt2, instances, torch, args.fp64_steps, workload=args.workload)
-    if args.serve_requests > 0:
+    if args.serve_requests > 0 and solo:
         line["serve"] = serve_measure(instances, torch, args.serve_requests)
-    if args.batch_nodes > 0:
+    if args.batch_nodes > 0 and solo:
         line["bnb"] = bnb_measure(instances, torch)
         line["lap_methods"] = lap_methods_measure(rlt2, instances, torch)
 
