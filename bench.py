@@ -137,11 +137,11 @@ def n35_measure(rlt2, instances, torch, steps, store, warmup=3, workload="cluste
                 rlt2.rlt2_state_bytes(N, store=store) / 1e9)}
 
 
-# DRAM bytes of one f64_dlap_kernel launch at N=20 (profiles/f64_launches_dram_clustered_n20.md)
+# DRAM bytes of one f64_dlap_kernel launch at N=20 (profiles/f64_sections_clustered_n20.md)
 # per tile coefficient read (n x N per tile) and written (n x n), valid while
 # the FP64 sources hash to the captured version; other sizes scale by those units
-F64_DLAP_TRAFFIC = {"N": 20, "read": 417196544, "write": 355250688, "files": ("f64.cu", "device.cuh"),
-                    "sources_sha1": "f5aa7005c8fb1d0b9466a9a6bb85d7eb947e496e"}
+F64_DLAP_TRAFFIC = {"N": 20, "read": 417048832, "write": 358820864, "files": ("f64.cu", "device.cuh"),
+                    "sources_sha1": "a9a251ea0c9e19b67c34d7898250e55b81e934da"}
 
 
 def f64_traffic(N):
