@@ -381,8 +381,10 @@ int rlt2_lap_batch_auction(const int32_t *M, int n, int count, int64_t *S, int32
  * RLT2_LAP_STATIC_MAX_N is rejected with RLT2_E_INVAL.  The call allocates
  * nothing: no cudaMalloc, cudaFree or allocating library routine.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) for that device; make it before any stream
- *     capture on that device.
+ *     (cudaGetSymbolAddress) for that device and keeps it until the process
+ *     exits; make that call before any stream capture on the device, and do
+ *     not call this entry point on a device after cudaDeviceReset of it (the
+ *     reset unloads the library's device code, and the array may move).
  *   - Every call on a device reuses the same block and clears it first; two
  *     calls whose work overlaps on the GPU (different streams, or host threads
  *     calling at once) race on it, so serialise them.

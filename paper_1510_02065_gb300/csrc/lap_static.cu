@@ -31,7 +31,10 @@ rlt2::DevStatus *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_lap_scratch on the current device.  In host code the
 // symbol's name is only a host-side handle, so it is resolved once per device
-// (with that device current) by cudaGetSymbolAddress.
+// (with that device current) by cudaGetSymbolAddress and kept for the life of
+// the process.  cudaDeviceReset unloads the module and the array may come back
+// elsewhere, so a process that resets a device must not call this entry point
+// on that device afterwards.
 int scratch_on_current_device(rlt2::DevStatus **out)
 {
     int dev = 0;
