@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--batch-iters", type=int, default=100)
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving measurement (0: skip)")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="lanes per D->C LAP (4, 8, 16, 32); 0: autotuned")
+    ap.add_argument("--cta-warps", type=int, default=0, help="warps per D->C CTA; 0: chosen")
     ap.add_argument("--store", default="tiles", choices=["tiles", "classes"],
                     help="store of D for the headline run (results are identical)")
     ap.add_argument("--fp64-steps", type=int, default=10,
@@ -477,7 +480,7 @@ def main():
 
     store = rlt2.RLT2_STORE_CLASSES if args.store == "classes" else rlt2.RLT2_STORE_TILES
     ctx = rlt2.Context(F, D, profile=True, use_graph=True, max_iters=K + W + 16,
-                       stream=stream.cuda_stream, store=store)
+                       stream=stream.cuda_stream, store=store, lanes=args.lanes, cta_warps=args.cta_warps)
     ctx.iterate(W)
     torch.cuda.synchronize()
     rlt2.rlt2_reset_stage_times(ctx.ctx)

@@ -78,11 +78,33 @@ typedef struct {
     int store;            /* how D is kept: RLT2_STORE_TILES (default),
                              RLT2_STORE_CLASSES (identical results) or
                              RLT2_STORE_PAIRS (the paired dual ascent)          */
-    int lanes;            /* lanes per D->C LAP of instances with N <= 16: 32 (a
-                             warp each) or 16 (two per warp); 0 (default) =
-                             16 for a context or group, chosen by timing for
-                             rlt2_batch_bound; results are identical           */
+    int lanes;            /* lanes per D->C LAP (Sec. 4.1's concentration of D):
+                             32 (a warp per tile) or 16 (two tiles per warp, one
+                             per half-warp; needs N <= 16, tile or class-sum
+                             store); 0 (default): chosen (see "Autotuning"
+                             below).  Results are identical in every shape    */
+    int cta_warps;        /* warps per CTA of the whole-warp D->C kernel: 4, 16
+                             or 32 (it must fit the CTA's shared memory: 32 warps
+                             up to N = 43, 16 up to N = 60); 0 (default): chosen */
 } rlt2_opts;
+
+/*
+ * Autotuning of the D->C shape (opts.lanes = opts.cta_warps = 0).  The first
+ * passes of a context, group or batch are tuning passes: one unmeasured pass
+ * in the default shape (whole warps in the CTA size that keeps the most warps
+ * resident), then one pass per candidate -- the default, half-warps where the
+ * rows have at most 16 columns, whole warps in CTAs of 4, 16 and 32 warps
+ * where they fit (up to six passes in all) -- each timed by CUDA events and
+ * measured by the Hungarian's step counter.  A candidate replaces the default
+ * only if its time per step is at least 3% lower (a pass's time per step
+ * drifts by a percent or two from one pass to the next).  In a group or batch that holds instances with N <= 16 and
+ * larger ones, the two kinds form separate D->C ranges, each tuned on its own
+ * (the small one on a second stream beside the other after tuning).  Tuning
+ * passes are ordinary passes (every shape gives the same results), launched
+ * directly rather than from a graph, and each synchronises the stream.  The
+ * choice is remembered for the process per device, store and row width: later
+ * contexts and groups with the same key start with it and do not tune.
+ */
 
 /*
  * Stores of D.  RLT2_STORE_TILES keeps every reduced cost d_ijknpq in the tile
@@ -181,6 +203,13 @@ int rlt2_get_state(rlt2_ctx *ctx, int level, int32_t *host_buf, size_t count);
  * three counts for the D->C concentrations alone.
  */
 int rlt2_work(rlt2_ctx *ctx, int64_t out[6]);
+
+/*
+ * The context's D->C shape (see rlt2_opts.lanes and "Autotuning"): out[0]
+ * lanes per LAP, out[1] warps per CTA of its launches, out[2] 1 while tuning
+ * passes are still to come, else 0.  All 0 without D (RLT1 mode).
+ */
+int rlt2_dlap_shape(rlt2_ctx *ctx, int out[3]);
 
 /*
  * Stage times recorded while opts.profile was set (synchronises): out[s] =
@@ -304,14 +333,13 @@ int rlt2_subproblem(const int32_t *F, const int32_t *D, int N, int k, const int3
  *   lb_out    host, B int64: each node's LB (lb_const included)
  *   ms_out    (may be NULL) milliseconds of device work from the first
  *             initialisation to the last pass (CUDA events)
- *   opts      stream (NULL: a stream created for the call), store, lanes;
- *             rlt1_only must be 0
- *   lanes_out (may be NULL) lanes per D->C LAP used for the nodes with
- *             N - k <= 16 (32 when there are none)
- * Autotuning (opts->lanes == 0, iters >= 3): the first pass solves the small
- * nodes' D->C LAPs on whole warps, the second on half-warps, and the form with
- * the lower time per relaxation of the Hungarian runs the remaining passes
- * (the two forms give identical results).  Nodes of N' <= 16 are placed first
+ *   opts      stream (NULL: a stream created for the call), store, lanes,
+ *             cta_warps; rlt1_only must be 0
+ *   shape_out (may be NULL) int[4]: the D->C shape used after tuning, as
+ *             (lanes per LAP, warps per CTA) for the nodes with N - k > 16,
+ *             then for those with N - k <= 16 (0, 0 where there are none)
+ * opts->lanes = 0: the first passes are tuning passes (see "Autotuning"),
+ * the rest one captured graph.  Nodes of N' <= 16 are placed first
  * internally; lb_out keeps the caller's order.
  * One device allocation holds every node's state (about 4 B * N'^2 (N'-1)^2
  * (N'-2) * round_up(N',4) each) and is freed before returning; synchronises.
@@ -319,7 +347,7 @@ int rlt2_subproblem(const int32_t *F, const int32_t *D, int N, int k, const int3
  */
 int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node *nodes, int B,
                      int iters, const rlt2_opts *opts, int64_t *lb_out, double *ms_out,
-                     int *lanes_out);
+                     int *shape_out);
 
 /*
  * Batched linear assignment with the library's Hungarian kernel (the LAP of

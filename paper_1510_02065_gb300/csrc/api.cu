@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -62,9 +63,120 @@ int check_instance(const int32_t *F, const int32_t *D, int N, const int32_t *B_l
 
 long long n_triples(int N) { return (long long)N * (N - 1) * (N - 2) / 6; }
 
-// Largest instance whose D->C LAPs (width N <= 16 location columns) can run
-// on half-warps.
+// Instances with N <= kSmallN (rows of at most 16 location columns) form a
+// D->C range of their own in a group that also has larger ones, so that each
+// range gets the lanes per tile that suit its width.
 constexpr int kSmallN = 16;
+
+bool lanes_opt_ok(const rlt2_opts &o)
+{
+    return (o.lanes == 0 || o.lanes == 16 || o.lanes == 32) &&
+           (o.cta_warps == 0 || o.cta_warps == 4 || o.cta_warps == 16 || o.cta_warps == 32) &&
+           !(o.lanes == 16 && o.cta_warps != 0);
+}
+
+// D->C shapes that can solve rows of width W with tiles of tsp ints, in the
+// order the autotuner tries them, the default first (whole warps in the CTA
+// size that keeps the most warps resident): a CTA of whole warps needs warps
+// x (4 tsp + 8) bytes of shared memory, at most `optin` (a CTA of 32 warps
+// stops fitting at N = 44, one of 16 at N = 61).
+std::vector<DlapShape> shape_candidates(int W, bool paired, int tsp, int optin)
+{
+    std::vector<DlapShape> v;
+    for (DlapShape d : {DlapShape{32, 0}, DlapShape{16, 0}, DlapShape{32, 4}, DlapShape{32, 16}, DlapShape{32, 32}})
+        if (dlap_shape_fits(d, W, paired) && (d.warps == 0 || (long long)d.warps * (4LL * tsp + 8) <= optin))
+            v.push_back(d);
+    return v;
+}
+
+// Autotuner of a group's D->C shapes.  While active, each pass of the group is
+// a tuning pass: the D->C ranges run one after the other, each in its next
+// candidate shape, timed by CUDA events and measured by the device's
+// relaxation counter; after the last candidate, the fastest per relaxation of
+// each range becomes the group's shape (every shape gives identical results,
+// so the tuning passes are ordinary passes).  The choice is remembered per
+// device, store and row width, and later groups with the same key start with
+// it and skip tuning.  A candidate that does not fit in shared memory (a CTA
+// of many warps at large N) is skipped.
+struct DlapTuner {
+    std::vector<DlapShape> cand[2];
+    int W[2] = {0, 0};
+    int tried = -1, total = 0;  // tried = -1: the unmeasured first pass is still to come
+    double best[2] = {0.0, 0.0};
+    DlapShape bestS[2] = {{0, 0}, {0, 0}};
+    int key_store = 0;
+    bool active() const { return total > 0 && tried < total; }
+};
+
+constexpr int kMaxDev = 64;
+std::mutex g_tuned_mutex;
+DlapShape g_tuned[kMaxDev][3][65];  // per device, store kind, row width ({0, 0}: not yet)
+
+int store_kind(const Group &g) { return g.sym ? 1 : g.paired ? 2 : 0; }
+
+DlapShape tuned_shape(int store, int W)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || W < 0 || W > 64) return {0, 0};
+    std::lock_guard<std::mutex> lock(g_tuned_mutex);
+    return g_tuned[dev][store][W];
+}
+
+void remember_shape(int store, int W, DlapShape d)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || W < 0 || W > 64) return;
+    std::lock_guard<std::mutex> lock(g_tuned_mutex);
+    g_tuned[dev][store][W] = d;
+}
+
+int range_width(const Group &g, int which) { return which == 0 ? (g.maxN + 3) & ~3 : g.smallW; }
+
+bool range_empty(const Group &g, int which)
+{
+    return which == 0 ? g.dtiles <= g.small_tiles : g.small_tiles <= 0;
+}
+
+// The D->C shapes of a group from the options: forced (RLT2_E_INVAL if a
+// forced shape cannot solve a range's rows), or remembered, or the default
+// (whole warps in the CTA size that keeps the most warps resident) with the
+// tuner armed.  Without D there is no D->C.
+int setup_dshape(Group &g, const rlt2_opts &o, DlapTuner *tuner)
+{
+    if (tuner) *tuner = DlapTuner{};
+    for (int r = 0; r < 2; r++) {
+        g.dshape[r] = DlapShape{32, 0};
+        if (g.rlt1_only || range_empty(g, r)) continue;
+        const int W = range_width(g, r);
+        if (o.lanes != 0 || o.cta_warps != 0) {
+            DlapShape d{o.lanes ? o.lanes : 32, o.cta_warps};
+            if (o.lanes == 0 && W <= 16 && !g.paired && o.cta_warps == 0) d.lanes = 16;
+            if (!dlap_shape_fits(d, W, g.paired)) return RLT2_E_INVAL;
+            int dev = 0, optin = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+                return RLT2_E_CUDA;
+            if ((long long)d.warps * (4LL * (r == 0 ? g.maxTS : g.smallTS) + 8) > optin) return RLT2_E_INVAL;
+            g.dshape[r] = d;
+            continue;
+        }
+        const DlapShape known = tuned_shape(store_kind(g), W);
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return RLT2_E_CUDA;
+        const std::vector<DlapShape> cand =
+            shape_candidates(W, g.paired, r == 0 ? g.maxTS : g.smallTS, optin);
+        g.dshape[r] = known.lanes ? known : DlapShape{32, 0};
+        if (!known.lanes && tuner) {
+            tuner->cand[r] = cand;
+            tuner->W[r] = W;
+            tuner->total = std::max(tuner->total, (int)cand.size());
+        }
+    }
+    if (tuner) tuner->key_store = store_kind(g);
+    return RLT2_OK;
+}
 
 // Facility triples i < k < p ordered by p, then k, then i: the first C(N,3)
 // of the table for any larger N are exactly the triples of N.
@@ -156,8 +268,15 @@ struct StageRange {
     ~StageRange() { nvtxRangePop(); }
 };
 
+// A tuning pass's events before, between and after the two D->C ranges
+// (small instances first); the device work counters at those points are
+// copied to g.snap on the device, so the pass enqueues without waiting.
+struct TunePass {
+    cudaEvent_t te[3];
+};
+
 cudaError_t enqueue_pass(const Group &g, int sm_count, cudaStream_t s, cudaEvent_t *ev,
-                         const SideStream *side = nullptr)
+                         const SideStream *side = nullptr, TunePass *tp = nullptr)
 {
     cudaError_t e;
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
@@ -169,7 +288,18 @@ cudaError_t enqueue_pass(const Group &g, int sm_count, cudaStream_t s, cudaEvent
         }
         if ((e = mark(1)) != cudaSuccess) return e;
         StageRange r("rlt2: concentration D->C");
-        if ((e = launch_dlap(g, sm_count, s, side)) != cudaSuccess) return e;
+        if (!tp) {
+            if ((e = launch_dlap(g, sm_count, s, side)) != cudaSuccess) return e;
+        } else {
+            // the two ranges one after the other, measured
+            for (int k = 0; k < 3; k++) {
+                if ((e = cudaMemcpyAsync(g.snap + k, g.status, sizeof(DevStatus), cudaMemcpyDeviceToDevice, s)) !=
+                        cudaSuccess ||
+                    (e = cudaEventRecord(tp->te[k], s)) != cudaSuccess)
+                    return e;
+                if (k < 2 && (e = launch_dlap_range(g, 1 - k, sm_count, s)) != cudaSuccess) return e;
+            }
+        }
     } else if ((e = mark(1)) != cudaSuccess) {
         return e;
     }
@@ -199,6 +329,56 @@ cudaError_t capture_passes(const Group &g, int sm_count, cudaStream_t s, int pas
     return cudaGraphInstantiate(exec, *graph, 0);
 }
 
+// One pass of group g as a tuning pass of t (see DlapTuner); synchronises s.
+// The first is a plain pass in the group's default shape, unmeasured: pass 1
+// of a dual ascent does other work than later ones, and it loads the kernels.
+int tune_step(Group &g, DlapTuner &t, int sm_count, cudaStream_t s, cudaEvent_t *ev)
+{
+    if (t.tried < 0) {
+        CK(enqueue_pass(g, sm_count, s, ev));
+        t.tried = 0;
+        return RLT2_OK;
+    }
+    Group gt = g;
+    DlapShape tried[2] = {{0, 0}, {0, 0}};
+    for (int r = 0; r < 2; r++)
+        if (!t.cand[r].empty()) gt.dshape[r] = tried[r] = t.cand[r][t.tried % t.cand[r].size()];
+    TunePass tp{};
+    DevStatus st[3];
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; k++) e = cudaEventCreate(&tp.te[k]);
+    if (e == cudaSuccess) e = enqueue_pass(gt, sm_count, s, ev, nullptr, &tp);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st, g.snap, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms[2] = {0.f, 0.f};
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[1], tp.te[0], tp.te[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], tp.te[1], tp.te[2]);
+    for (cudaEvent_t ev2 : tp.te)
+        if (ev2) cudaEventDestroy(ev2);
+    if (e != cudaSuccess) return cuda_code(e);
+    // work of each range: Hungarian steps (a step costs the same instructions
+    // in every pass, while the relaxations per step change from pass to pass)
+    const double work[2] = {(double)(st[2].dsteps - st[1].dsteps), (double)(st[1].dsteps - st[0].dsteps)};
+    // the default (measured first) stays unless a candidate is clearly faster:
+    // one pass's time per step drifts by a percent or two from pass to pass
+    constexpr double kMargin = 0.97;
+    for (int r = 0; r < 2; r++) {
+        if (!tried[r].lanes || work[r] <= 0) continue;
+        const double per = ms[r] / work[r];
+        if (!t.bestS[r].lanes || per < kMargin * t.best[r]) {
+            t.best[r] = per;
+            t.bestS[r] = tried[r];
+        }
+    }
+    if (++t.tried == t.total)
+        for (int r = 0; r < 2; r++)
+            if (t.bestS[r].lanes) {
+                g.dshape[r] = t.bestS[r];
+                remember_shape(t.key_store, t.W[r], t.bestS[r]);
+            }
+    return RLT2_OK;
+}
+
 int group_status(const Group &g, cudaStream_t s)
 {
     int err = 0;
@@ -226,6 +406,7 @@ struct rlt2_ctx {
     // profiling: 5 events per pass, recorded on the stream between the stages
     std::vector<cudaEvent_t> events;
     size_t ev_used = 0;
+    DlapTuner tuner;       // D->C shape tuning on the first passes (opts.lanes = 0)
 };
 
 static void free_ctx(rlt2_ctx *c)
@@ -297,6 +478,7 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, int store, long long U, in
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
     const size_t o_cnt = a.take(8);
     const size_t o_st = a.take(sizeof(DevStatus));
+    const size_t o_snap = a.take(3 * sizeof(DevStatus));
     const size_t o_stage = a.take((size_t)3 * N * N * 4);
     cudaError_t e = cudaMalloc((void **)&c->mem, a.used);
     if (e != cudaSuccess) {
@@ -329,11 +511,15 @@ static int setup_ctx(rlt2_ctx *c, int N, bool with_d, int store, long long U, in
     g.sym = sym;
     g.paired = paired;
     g.dtiles = nd.dtiles;
-    // instances with N <= 16: D->C LAPs on half-warps unless opts ask for whole warps
-    g.small_tiles = with_d && !paired && N <= kSmallN && c->opts.lanes != 32 ? (int)nd.tiles : 0;
+    // one instance: one D->C range, its shape forced, remembered or tuned
+    g.small_tiles = 0;
     g.smallTS = nd.TS;
+    g.smallW = nd.W;
+    const int rc_shape = setup_dshape(g, c->opts, &c->tuner);
+    if (rc_shape != RLT2_OK) return rc_shape;
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
+    g.snap = reinterpret_cast<DevStatus *>(base + o_snap);
     g.triples = reinterpret_cast<const int4 *>(base + o_tri);
     g.first = nd;
     c->U = U;
@@ -409,7 +595,7 @@ int rlt2_create(const int32_t *F, const int32_t *D, int N, const int32_t *B_lin,
     int32_t *stage = nullptr;
     if ((c->opts.store != RLT2_STORE_TILES && c->opts.store != RLT2_STORE_CLASSES &&
          c->opts.store != RLT2_STORE_PAIRS) ||
-        (c->opts.lanes != 0 && c->opts.lanes != 16 && c->opts.lanes != 32)) {
+        !lanes_opt_ok(c->opts)) {
         free_ctx(c);
         return RLT2_E_INVAL;
     }
@@ -439,7 +625,7 @@ int rlt2_child(rlt2_ctx *par, int f, int l, const rlt2_opts *opts, rlt2_ctx **ou
     if (!c) return RLT2_E_OOM;
     c->opts.rlt1_only = pn.p.z == nullptr;
     c->opts.store = pn.paired ? RLT2_STORE_PAIRS : RLT2_STORE_TILES;
-    if (c->opts.lanes != 0 && c->opts.lanes != 16 && c->opts.lanes != 32) {
+    if (!lanes_opt_ok(c->opts)) {
         free_ctx(c);
         return RLT2_E_INVAL;
     }
@@ -534,7 +720,7 @@ int rlt2_load(const char *path, const rlt2_opts *opts, rlt2_ctx **out)
         }
         c->opts.rlt1_only = !h.with_d;
         c->opts.store = h.store;
-        if (h.iter > c->opts.max_iters) {  // the history must fit
+        if (h.iter > c->opts.max_iters || !lanes_opt_ok(c->opts)) {  // the history must fit
             rc = RLT2_E_INVAL;
             break;
         }
@@ -588,7 +774,10 @@ int rlt2_iterate(rlt2_ctx *c, int k)
             ev = &c->events[c->ev_used];
             c->ev_used += 5;
         }
-        if (c->opts.use_graph && !ev) {
+        if (c->tuner.active()) {
+            const int rc = tune_step(c->g, c->tuner, c->sm_count, c->stream, ev);
+            if (rc != RLT2_OK) return rc;
+        } else if (c->opts.use_graph && !ev) {
             if (!c->gexec) CK(capture_passes(c->g, c->sm_count, c->stream, 1, &c->graph, &c->gexec));
             CK(cudaGraphLaunch(c->gexec, c->stream));
         } else {
@@ -687,6 +876,16 @@ int rlt2_get_state(rlt2_ctx *c, int level, int32_t *host, size_t count)
     return RLT2_OK;
 }
 
+int rlt2_dlap_shape(rlt2_ctx *c, int out[3])
+{
+    if (!c || !out) return RLT2_E_INVAL;
+    const bool d = !c->g.rlt1_only;
+    out[0] = d ? c->g.dshape[0].lanes : 0;
+    out[1] = d ? dlap_cta_warps(c->g, 0) : 0;
+    out[2] = d && c->tuner.active() ? 1 : 0;
+    return RLT2_OK;
+}
+
 int rlt2_work(rlt2_ctx *c, int64_t out[6])
 {
     if (!c || !out) return RLT2_E_INVAL;
@@ -766,7 +965,8 @@ struct rlt2_group {
     cudaEvent_t done = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    SideStream side{};     // the half-warp D->C kernel beside the whole-warp one
+    SideStream side{};     // the small instances' D->C range beside the other one
+    DlapTuner tuner;       // D->C shape tuning on the first passes (opts.lanes = 0)
 };
 
 static int make_side(SideStream &sd)
@@ -806,10 +1006,15 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
 {
     if (!out || !ctxs || count < 1) return RLT2_E_INVAL;
     *out = nullptr;
-    for (int b = 0; b < count; b++)
+    for (int b = 0; b < count; b++) {
         if (!ctxs[b] || ctxs[b]->g.rlt1_only != ctxs[0]->g.rlt1_only || ctxs[b]->g.sym != ctxs[0]->g.sym ||
             ctxs[b]->g.paired != ctxs[0]->g.paired)
             return RLT2_E_INVAL;
+        // a context twice would give two descriptors of one state, whose
+        // passes in the same launches would race on it
+        for (int b2 = 0; b2 < b; b2++)
+            if (ctxs[b2] == ctxs[b]) return RLT2_E_INVAL;
+    }
     rlt2_group *gr = new (std::nothrow) rlt2_group();
     if (!gr) return RLT2_E_OOM;
     auto fail = [&](int code) {
@@ -841,24 +1046,23 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
     const size_t o_cnt = a.take(8);
     const size_t o_st = a.take(sizeof(DevStatus));
+    const size_t o_snap = a.take(3 * sizeof(DevStatus));
     cudaError_t e = cudaMalloc((void **)&gr->mem, a.used);
     if (e != cudaSuccess) {
         cudaGetLastError();
         gr->mem = nullptr;
         return fail(cuda_code(e));
     }
-    // instances with N <= 16 first: their tiles form the half-warp range of D->C
-    bool halves = !ctxs[0]->g.rlt1_only && !ctxs[0]->g.paired;
-    for (rlt2_ctx *c : gr->ctxs) halves = halves && c->opts.lanes != 32;
+    // instances with N <= 16 first: their D->C units form a range of their own
+    // when the group also has larger instances
     std::vector<int> order(count);
     for (int b = 0; b < count; b++) order[b] = b;
-    if (halves)
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-            return (gr->ctxs[x]->node.N <= kSmallN) > (gr->ctxs[y]->node.N <= kSmallN);
-        });
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (gr->ctxs[x]->node.N <= kSmallN) > (gr->ctxs[y]->node.N <= kSmallN);
+    });
     std::vector<NodeDesc> hn(count);
     long long tiles = 0, small_tiles = 0, dtiles = 0;
-    int ctas = 0, probs = 0, maxTS = 0, smallTS = 4;
+    int ctas = 0, probs = 0, maxTS = 0, smallTS = 4, smallW = 4;
     for (int b = 0; b < count; b++) {
         NodeDesc &nd = hn[b];
         nd = gr->ctxs[order[b]]->node;     // the context's own state, shared
@@ -873,15 +1077,17 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
         ctas += (int)(n_triples(nd.N) * nd.nchunks);
         probs += nd.N * nd.N;
         maxTS = std::max(maxTS, nd.TS);
-        if (halves && nd.N <= kSmallN) {
-            small_tiles += nd.tiles;
+        if (nd.N <= kSmallN) {
+            small_tiles += nd.dtiles;
             smallTS = std::max(smallTS, nd.TS);
+            smallW = std::max(smallW, nd.W);
         }
     }
     if (tiles >= (1LL << 31)) return fail(RLT2_E_INVAL);
     Group &g = gr->g;
-    g.small_tiles = (int)small_tiles;
+    g.small_tiles = small_tiles < dtiles ? (int)small_tiles : 0;
     g.smallTS = smallTS;
+    g.smallW = smallW;
     g.nodes = reinterpret_cast<const NodeDesc *>(gr->mem + o_nodes);
     g.B = count;
     g.tiles = tiles;
@@ -897,8 +1103,11 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     g.dtiles = dtiles;
     g.counter = reinterpret_cast<unsigned *>(gr->mem + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(gr->mem + o_st);
+    g.snap = reinterpret_cast<DevStatus *>(gr->mem + o_snap);
     g.triples = reinterpret_cast<const int4 *>(gr->mem + o_tri);
     g.first = hn[0];
+    const int rc_shape = setup_dshape(g, ctxs[0]->opts, &gr->tuner);
+    if (rc_shape != RLT2_OK) return fail(rc_shape);
     // the group's stream starts after every context's pending work
     for (rlt2_ctx *c : gr->ctxs) {
         if (cudaEventRecord(gr->done, c->stream) != cudaSuccess ||
@@ -924,8 +1133,14 @@ int rlt2_group_iterate(rlt2_group *gr, int k)
     for (rlt2_ctx *c : gr->ctxs)
         if ((long long)c->enqueued + k > c->opts.max_iters) return RLT2_E_STATE;
     if (k == 0) return RLT2_OK;
-    if (!gr->exec) CK(capture_passes(gr->g, gr->sm_count, gr->stream, 1, &gr->graph, &gr->exec, &gr->side));
-    for (int t = 0; t < k; t++) CK(cudaGraphLaunch(gr->exec, gr->stream));
+    int t = 0;
+    for (; t < k && gr->tuner.active(); t++) {
+        const int rc = tune_step(gr->g, gr->tuner, gr->sm_count, gr->stream, nullptr);
+        if (rc != RLT2_OK) return rc;
+    }
+    if (t < k && !gr->exec)
+        CK(capture_passes(gr->g, gr->sm_count, gr->stream, 1, &gr->graph, &gr->exec, &gr->side));
+    for (; t < k; t++) CK(cudaGraphLaunch(gr->exec, gr->stream));
     for (rlt2_ctx *c : gr->ctxs) c->enqueued += k;
     // every context's later work starts after the group's passes
     CK(cudaEventRecord(gr->done, gr->stream));
@@ -982,7 +1197,7 @@ int rlt2_subproblem(const int32_t *F, const int32_t *D, int N, int k, const int3
 }
 
 int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node *nodes, int B,
-                     int iters, const rlt2_opts *opts, int64_t *lb_out, double *ms_out, int *lanes_out)
+                     int iters, const rlt2_opts *opts, int64_t *lb_out, double *ms_out, int *shape_out)
 {
     if (!F || !D || N < RLT2_MIN_N || N > RLT2_MAX_N || !nodes || B < 1 || iters < 0 || !lb_out)
         return RLT2_E_INVAL;
@@ -990,7 +1205,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     if (opts) o = *opts;
     else rlt2_default_opts(&o);
     if (o.rlt1_only) return RLT2_E_INVAL;  // the batch runs the full RLT2 dual ascent
-    if (o.lanes != 0 && o.lanes != 16 && o.lanes != 32) return RLT2_E_INVAL;
+    if (!lanes_opt_ok(o)) return RLT2_E_INVAL;
     int dev = 0, sm_count = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -1039,6 +1254,7 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     const size_t o_tri = a.take(tri.size() * sizeof(int4));
     const size_t o_cnt = a.take(8);
     const size_t o_st = a.take(sizeof(DevStatus));
+    const size_t o_snap = a.take(3 * sizeof(DevStatus));
     const size_t o_stage = a.take((size_t)3 * maxN * maxN * 4 * B);
     // stream capture needs a stream other than the legacy default one
     cudaStream_t s = (cudaStream_t)o.stream;
@@ -1064,12 +1280,12 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
         if (own) cudaStreamDestroy(own);
         return RLT2_E_INVAL;
     }
-    // nodes with N' <= 16 first: their tiles form the half-warp range of D->C
+    // nodes with N' <= 16 first: their D->C units form a range of their own
     std::vector<int> order(B);
     for (int b = 0; b < B; b++) order[b] = b;
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return (in[x].Np <= kSmallN) > (in[y].Np <= kSmallN); });
-    int ctas = 0, probs = 0, maxTS = 0, smallTS = 4;
+    int ctas = 0, probs = 0, maxTS = 0, smallTS = 4, smallW = 4;
     long long small_tiles = 0, dtiles = 0;
     for (int b = 0; b < B; b++) {
         NodeDesc &nd = hn[b];
@@ -1078,9 +1294,10 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
         fill_node(nd, in[ob].Np, JC);
         nd.p = node_state(base, no[ob], hist_cap, o);
         encode_zmap(nd, JC);
-        if (nd.N <= kSmallN && !paired) {
-            small_tiles += nd.tiles;
+        if (nd.N <= kSmallN) {
+            small_tiles += nd.dtiles;
             smallTS = std::max(smallTS, nd.TS);
+            smallW = std::max(smallW, nd.W);
         }
         nd.tile_base = tiles;
         nd.dtile_base = dtiles;
@@ -1105,20 +1322,25 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     g.sym = sym;
     g.paired = paired;
     g.dtiles = dtiles;
-    g.small_tiles = 0;
+    g.small_tiles = small_tiles < dtiles ? (int)small_tiles : 0;
     g.smallTS = smallTS;
+    g.smallW = smallW;
     g.counter = reinterpret_cast<unsigned *>(base + o_cnt);
     g.status = reinterpret_cast<DevStatus *>(base + o_st);
+    g.snap = reinterpret_cast<DevStatus *>(base + o_snap);
     g.triples = reinterpret_cast<const int4 *>(base + o_tri);
     g.first = hn[0];
-    // D->C of the small nodes: whole warps (g) or half-warps (g16); opts.lanes
-    // forces one, 0 lets the first passes decide (below)
-    Group g16 = g;
-    g16.small_tiles = (int)small_tiles;
-    int lanes = small_tiles == 0 ? 32 : o.lanes;
+    // D->C shapes: opts.lanes / opts.cta_warps force the shape of both
+    // ranges, 0 lets the first passes decide (tuning passes, below)
+    DlapTuner tuner;
+    const int rc_shape = setup_dshape(g, o, &tuner);
+    if (rc_shape != RLT2_OK) {
+        cudaFree(base);
+        if (own) cudaStreamDestroy(own);
+        return rc_shape;
+    }
 
     cudaEvent_t t0 = nullptr, t1 = nullptr;
-    cudaEvent_t tev[10] = {};
     SideStream side{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1144,37 +1366,24 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
             e = init_node(hn[b], I.F.data(), I.D.data(), I.B.data(), I.cst, stage + (size_t)b * 3 * maxN * maxN, s);
         }
         if (e != cudaSuccess) break;
-        // Autotuning of the lanes per D->C LAP of the small nodes: the first
-        // two passes (real passes: both forms give identical results) run one
-        // with whole warps, one with half-warps; the D->C time per relaxation
-        // of the Hungarian decides the form of the remaining passes.
+        // tuning passes first (real passes), then every remaining pass of
+        // every node: one captured graph, one launch
         int done = 0;
-        if (lanes == 0 && iters >= 3) {
-            for (int k = 0; k < 10 && e == cudaSuccess; k++) e = cudaEventCreate(&tev[k]);
-            DevStatus st[3];
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&st[0], g.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = enqueue_pass(g, sm_count, s, tev, &side);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&st[1], g.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = enqueue_pass(g16, sm_count, s, tev + 5, &side);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&st[2], g.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) break;
-            float m32 = 0.f, m16 = 0.f;
-            if ((e = cudaEventElapsedTime(&m32, tev[1], tev[2])) != cudaSuccess) break;
-            if ((e = cudaEventElapsedTime(&m16, tev[6], tev[7])) != cudaSuccess) break;
-            const double r32 = (double)(st[1].drelax - st[0].drelax), r16 = (double)(st[2].drelax - st[1].drelax);
-            lanes = (r16 > 0 && r32 > 0 && m16 / r16 < m32 / r32) ? 16 : 32;
-            done = 2;
-        } else if (lanes == 0) {
-            lanes = 16;
+        for (; done < iters && tuner.active(); done++) {
+            rc = tune_step(g, tuner, sm_count, s, nullptr);
+            if (rc != RLT2_OK) break;
         }
-        const Group &gb = lanes == 16 ? g16 : g;
-        // all (remaining) passes of all nodes: one captured graph, one launch
+        if (rc != RLT2_OK) break;
         if (iters > done) {
-            if ((e = capture_passes(gb, sm_count, s, iters - done, &graph, &exec, &side)) != cudaSuccess) break;
+            if ((e = capture_passes(g, sm_count, s, iters - done, &graph, &exec, &side)) != cudaSuccess) break;
             if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
         }
-        if (lanes_out) *lanes_out = small_tiles == 0 ? 32 : lanes;
+        if (shape_out) {
+            for (int r = 0; r < 2; r++) {
+                shape_out[2 * r] = range_empty(g, r) ? 0 : g.dshape[r].lanes;
+                shape_out[2 * r + 1] = dlap_cta_warps(g, r);
+            }
+        }
         if ((e = cudaEventRecord(t1, s)) != cudaSuccess) break;
         rc = group_status(g, s);
         for (int b = 0; b < B && e == cudaSuccess; b++)
@@ -1192,8 +1401,6 @@ int rlt2_batch_bound(const int32_t *F, const int32_t *D, int N, const rlt2_node 
     if (graph) cudaGraphDestroy(graph);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
-    for (cudaEvent_t ev : tev)
-        if (ev) cudaEventDestroy(ev);
     free_side(side);
     cudaFree(base);
     if (own) cudaStreamDestroy(own);

@@ -165,6 +165,15 @@ inline void fill_node(NodeDesc &d, int N, int JC)
     d.fn = make_fastdiv(N - 2);
 }
 
+// How the D->C concentration solves a range of tiles: `lanes` lanes per tile
+// (32: a warp per tile, in CTAs of `warps` = 4, 16 or 32 warps, 0 for the
+// size that keeps the most warps resident; 16: two tiles per warp, one per
+// half-warp, for rows of at most 16 columns in the tile and class-sum
+// stores).  Every shape gives identical results.
+struct DlapShape {
+    int lanes, warps;
+};
+
 // A group of instances advanced together.
 struct Group {
     const NodeDesc *nodes;  // device array [B]
@@ -179,11 +188,13 @@ struct Group {
     bool sym;               // D in the class-sum store (every instance of the group)
     bool paired;            // D in the pair store (every instance of the group)
     long long dtiles;       // total D->C work units
-    int small_tiles;        // D->C: the first small_tiles tiles (instances with N <= 16, which
-                            // come first in the group) are solved two per warp, 16 lanes each
-    int smallTS;            // largest tile stride (ints) among those instances
-    unsigned *counter;      // D->C work counters: [0] one tile per warp, [1] pairs of small tiles
+    int small_tiles;        // D->C: the first small_tiles units (instances with N <= 16, which
+                            // come first in the group) form a range of their own
+    int smallTS, smallW;    // largest tile stride (ints) and row width among those instances
+    DlapShape dshape[2];    // D->C shape of the other units [0] and of the small ones [1]
+    unsigned *counter;      // D->C work counters: [0] the other units, [1] the small ones
     DevStatus *status;      // error bits and work counters of the group
+    DevStatus *snap;        // [3] copies of *status taken inside a tuning pass
     const int4 *triples;    // facility triples i<k<p ordered by p: the first C(N,3) serve N
     NodeDesc first;         // copy of nodes[0]: kernels of a group of one read it as a parameter
 };
@@ -215,6 +226,24 @@ struct SideStream {
     cudaEvent_t fork, join;
 };
 cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s, const SideStream *side = nullptr);
+// One range [lo, hi) of the group's D->C units, taken from *counter (reset to
+// 0 by the fused pass), tiles of at most tsp ints and maxW columns.
+struct DlapRange {
+    long long lo, hi;
+    unsigned *counter;
+    int tsp, maxW, lanes, warps;
+};
+// One of the group's two D->C ranges (0: the units from small_tiles on, 1:
+// the small instances' units) in its shape g.dshape[which].
+cudaError_t launch_dlap_range(const Group &g, int which, int sm_count, cudaStream_t s);
+// Warps per CTA that range `which` launches with (0 if it is empty).
+int dlap_cta_warps(const Group &g, int which);
+// Whether a shape can solve rows of width W (paired: the pair store).
+inline bool dlap_shape_fits(const DlapShape &d, int W, bool paired)
+{
+    if (d.lanes == 16) return W <= 16 && !paired && d.warps == 0;
+    return d.lanes == 32 && (d.warps == 0 || d.warps == 4 || d.warps == 16 || d.warps == 32);
+}
 cudaError_t launch_clap(const Group &g, cudaStream_t s);
 cudaError_t launch_xlap(const Group &g, cudaStream_t s);
 cudaError_t launch_lap_batch(const int32_t *M, int n, int count, int64_t *S, int32_t *assign,

@@ -11,6 +11,11 @@
 //   xlap_kernel   concentration B -> LB (one LAP of size N), LB += LB', history,
 //                 stopping rule of Algorithm 1.
 //   lap_batch_kernel  the same Hungarian on caller-supplied matrices.
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
+
 #include "device.cuh"
 #include "kernels.h"
 
@@ -187,14 +192,15 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
 // caps registers at 32 per thread (64 warps per SM).
 // MODE: 0 tile store, 1 class-sum store, 2 pair store (work units: its tiles).
 template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 64 / WARPS) dlap_kernel(Group g)
+__global__ void __launch_bounds__(WARPS * 32, 64 / WARPS)
+    dlap_kernel(Group g, long long lo, long long hi, unsigned *counter, int tsp)
 {
     constexpr bool SYM = MODE == 1, PAIR = MODE == 2;
     if (ONE && *g.first.p.stop) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * g.maxTS;
-    unsigned char *tail = smem + (size_t)WARPS * g.maxTS * 4;
+    int *buf = reinterpret_cast<int *>(smem) + (size_t)warp * tsp;
+    unsigned char *tail = smem + (size_t)WARPS * tsp * 4;
     uint64_t *bar = reinterpret_cast<uint64_t *>(tail) + warp;
 
     if (lane == 0) {
@@ -205,11 +211,11 @@ __global__ void __launch_bounds__(WARPS * 32, 64 / WARPS) dlap_kernel(Group g)
 
     unsigned parity = 0;
     unsigned steps = 0, relax = 0, laps = 0;
-    const unsigned ntiles = (unsigned)g.dtiles;  // < 2^31 for any group the host accepts
+    const unsigned ntiles = (unsigned)hi;  // < 2^31 for any group the host accepts
     int b = 0;
     for (;;) {
-        unsigned T = 0;  // units [0, small_tiles) are the half-warp kernel's
-        if (lane == 0) T = atomicAdd(g.counter, 1u) + (unsigned)g.small_tiles;
+        unsigned T = 0;
+        if (lane == 0) T = atomicAdd(counter, 1u) + (unsigned)lo;
         T = __shfl_sync(kFull, T, 0);
         if (T >= ntiles) break;
         bool ok;
@@ -244,18 +250,19 @@ __global__ void __launch_bounds__(WARPS * 32, 64 / WARPS) dlap_kernel(Group g)
     }
 }
 
-// Tiles of instances with N <= 16 (the group's first small_tiles tiles): two
-// per warp, one per half-warp (LAPs of width <= 16 on 16 lanes), from the
-// second work counter.  Two buffers of smallTS ints and two mbarriers per
-// warp; half h always uses buffer and barrier h.
+// Tiles of instances with N <= 16 (a range [lo, hi) of the group's units,
+// from its own counter): two per warp, one per half-warp (LAPs of width <= 16
+// on 16 lanes).  Two buffers of tsp ints and two mbarriers per warp; half h
+// always uses buffer and barrier h.
 template <bool PACK, bool ONE, bool SYM>
-__global__ void __launch_bounds__(kDlap16Warps * 32, 64 / kDlap16Warps) dlap16_kernel(Group g)
+__global__ void __launch_bounds__(kDlap16Warps * 32, 64 / kDlap16Warps)
+    dlap16_kernel(Group g, long long lo, long long hi, unsigned *counter, int tsp)
 {
     if (ONE && *g.first.p.stop) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
-    int *buf = reinterpret_cast<int *>(smem) + ((size_t)warp * 2 + half) * g.smallTS;
-    unsigned char *tail = smem + (size_t)kDlap16Warps * 2 * g.smallTS * 4;
+    int *buf = reinterpret_cast<int *>(smem) + ((size_t)warp * 2 + half) * tsp;
+    unsigned char *tail = smem + (size_t)kDlap16Warps * 2 * tsp * 4;
     uint64_t *bar = reinterpret_cast<uint64_t *>(tail) + warp * 2 + half;
 
     if (hl == 0) {
@@ -266,14 +273,14 @@ __global__ void __launch_bounds__(kDlap16Warps * 32, 64 / kDlap16Warps) dlap16_k
 
     unsigned parity = 0;
     unsigned steps = 0, relax = 0, laps = 0;
-    const unsigned small = (unsigned)g.small_tiles, units = (small + 1u) / 2u;
+    const unsigned small = (unsigned)hi, units = (unsigned)((hi - lo + 1) / 2);
     int b = 0;
     for (;;) {
         unsigned U = 0;
-        if (lane == 0) U = atomicAdd(g.counter + 1, 1u);
+        if (lane == 0) U = atomicAdd(counter, 1u);
         U = __shfl_sync(kFull, U, 0);
         if (U >= units) break;
-        const unsigned T = 2u * U + (unsigned)half;
+        const unsigned T = (unsigned)lo + 2u * U + (unsigned)half;
         bool ok = true;
         if (T < small) {
             if constexpr (ONE) {
@@ -495,120 +502,215 @@ cudaError_t launch_wait_selftest(DevStatus *status, unsigned limit, cudaStream_t
 
 // ---------------------------------------------------------------- launchers
 
-// Resident warps per SM of the D->C kernel with CTAs of WARPS warps.
-template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
-static cudaError_t dlap_fit(const Group &g, int &warps_per_sm)
+// Resident CTAs per SM of kernel k with `threads` threads and `smem` bytes of
+// dynamic shared memory on the current device, 0 when smem exceeds a CTA's
+// opt-in maximum.  The first query for a kernel raises its dynamic
+// shared-memory cap to that maximum (a cap only: occupancy follows the bytes
+// a launch asks for); answers are cached per kernel, device and size, so a
+// launch costs no driver queries after its first one.
+static cudaError_t ctas_per_sm(const void *k, int threads, size_t smem, int &per_sm)
 {
-    const size_t smem = (size_t)WARPS * ((size_t)g.maxTS * 4 + 8);
-    // a CTA size whose tile buffers exceed a CTA's shared memory (large N:
-    // 16 warps from N = 61, 32 warps from N = 44) keeps no warp resident
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, size_t>, int> cache;
+    static std::set<std::pair<const void *, int>> capped;
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    warps_per_sm = 0;
-    if (smem > (size_t)optin) return cudaSuccess;
-    auto k = dlap_kernel<NS, PACK, ONE, MODE, WARPS>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(k, dev, threads, smem);
+    const auto it = cache.find(key);
+    if (it != cache.end()) {
+        per_sm = it->second;
+        return cudaSuccess;
+    }
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    per_sm = 0;
+    if (smem <= (size_t)optin) {
+        if (!capped.count({k, dev})) {
+            if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess)
+                return e;
+            capped.insert({k, dev});
+        }
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem)) != cudaSuccess) return e;
+    }
+    cache[key] = per_sm;
+    return cudaSuccess;
+}
+
+// Resident warps per SM of the D->C kernel with CTAs of WARPS warps (0 when its
+// tile buffers exceed a CTA's shared memory: 16 warps from N = 61, 32 warps
+// from N = 44).
+template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
+static cudaError_t dlap_fit(const DlapRange &rg, int &warps_per_sm)
+{
+    const size_t smem = (size_t)WARPS * ((size_t)rg.tsp * 4 + 8);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WARPS * 32, smem);
+    const cudaError_t e =
+        ctas_per_sm(reinterpret_cast<const void *>(dlap_kernel<NS, PACK, ONE, MODE, WARPS>), WARPS * 32, smem, per_sm);
     warps_per_sm = per_sm * WARPS;
     return e;
 }
 
 template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
-static cudaError_t dlap_run(const Group &g, int sm_count, cudaStream_t s)
+static cudaError_t dlap_run(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
 {
-    const size_t smem = (size_t)WARPS * ((size_t)g.maxTS * 4 + 8);
+    const size_t smem = (size_t)WARPS * ((size_t)rg.tsp * 4 + 8);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dlap_kernel<NS, PACK, ONE, MODE, WARPS>,
-                                                                  WARPS * 32, smem);
+    cudaError_t e = ctas_per_sm(reinterpret_cast<const void *>(dlap_kernel<NS, PACK, ONE, MODE, WARPS>), WARPS * 32,
+                                smem, per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)per_sm * sm_count;
-    const long long need = (g.dtiles + WARPS - 1) / WARPS;
+    const long long need = (rg.hi - rg.lo + WARPS - 1) / WARPS;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    dlap_kernel<NS, PACK, ONE, MODE, WARPS><<<(unsigned)grid, WARPS * 32, smem, s>>>(g);
+    dlap_kernel<NS, PACK, ONE, MODE, WARPS><<<(unsigned)grid, WARPS * 32, smem, s>>>(g, rg.lo, rg.hi, rg.counter,
+                                                                                   rg.tsp);
     return cudaGetLastError();
 }
 
-// CTA size: the one of 4, 16 or 32 warps that keeps the most warps resident
-// (shared memory decides: at N = 30 two CTAs of 32 warps fit where fourteen
-// of 4 do), the smaller on a tie.
+// CTA size: rg.warps (4, 16 or 32) when given, else the one of those that
+// keeps the most warps resident (shared memory decides: at N = 30 two CTAs of
+// 32 warps fit where fourteen of 4 do), the smaller on a tie.
 template <int NS, bool PACK, bool ONE, int MODE>
-static cudaError_t dlap_go(const Group &g, int sm_count, cudaStream_t s)
+static cudaError_t dlap_go(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
 {
     int w4 = 0, w16 = 0, w32 = 0;
     cudaError_t e;
-    if ((e = dlap_fit<NS, PACK, ONE, MODE, 4>(g, w4)) != cudaSuccess) return e;
-    if ((e = dlap_fit<NS, PACK, ONE, MODE, 16>(g, w16)) != cudaSuccess) return e;
-    if ((e = dlap_fit<NS, PACK, ONE, MODE, 32>(g, w32)) != cudaSuccess) return e;
-    if (w32 > w4 && w32 > w16) return dlap_run<NS, PACK, ONE, MODE, 32>(g, sm_count, s);
-    if (w16 > w4) return dlap_run<NS, PACK, ONE, MODE, 16>(g, sm_count, s);
-    return dlap_run<NS, PACK, ONE, MODE, 4>(g, sm_count, s);
+    if ((e = dlap_fit<NS, PACK, ONE, MODE, 4>(rg, w4)) != cudaSuccess) return e;
+    if ((e = dlap_fit<NS, PACK, ONE, MODE, 16>(rg, w16)) != cudaSuccess) return e;
+    if ((e = dlap_fit<NS, PACK, ONE, MODE, 32>(rg, w32)) != cudaSuccess) return e;
+    int w = rg.warps;
+    if (w == 0) w = (w32 > w4 && w32 > w16) ? 32 : w16 > w4 ? 16 : 4;
+    if ((w == 4 && !w4) || (w == 16 && !w16) || (w == 32 && !w32)) return cudaErrorInvalidConfiguration;
+    if (w == 32) return dlap_run<NS, PACK, ONE, MODE, 32>(g, rg, sm_count, s);
+    if (w == 16) return dlap_run<NS, PACK, ONE, MODE, 16>(g, rg, sm_count, s);
+    if (w == 4) return dlap_run<NS, PACK, ONE, MODE, 4>(g, rg, sm_count, s);
+    return cudaErrorInvalidValue;
 }
 
 template <bool ONE, int MODE>
-static cudaError_t dlap_pick(const Group &g, int sm_count, cudaStream_t s)
+static cudaError_t dlap_pick(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
 {
-    if (g.maxN <= 32)
-        return g.pack ? dlap_go<1, true, ONE, MODE>(g, sm_count, s) : dlap_go<1, false, ONE, MODE>(g, sm_count, s);
-    return g.pack ? dlap_go<2, true, ONE, MODE>(g, sm_count, s) : dlap_go<2, false, ONE, MODE>(g, sm_count, s);
+    if (rg.maxW <= 32)
+        return g.pack ? dlap_go<1, true, ONE, MODE>(g, rg, sm_count, s) : dlap_go<1, false, ONE, MODE>(g, rg, sm_count, s);
+    return g.pack ? dlap_go<2, true, ONE, MODE>(g, rg, sm_count, s) : dlap_go<2, false, ONE, MODE>(g, rg, sm_count, s);
+}
+
+static cudaError_t dlap_warp(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
+{
+    if (g.sym) return g.B == 1 ? dlap_pick<true, 1>(g, rg, sm_count, s) : dlap_pick<false, 1>(g, rg, sm_count, s);
+    if (g.paired) return g.B == 1 ? dlap_pick<true, 2>(g, rg, sm_count, s) : dlap_pick<false, 2>(g, rg, sm_count, s);
+    return g.B == 1 ? dlap_pick<true, 0>(g, rg, sm_count, s) : dlap_pick<false, 0>(g, rg, sm_count, s);
 }
 
 template <bool PACK, bool ONE, bool SYM>
-static cudaError_t dlap16_go(const Group &g, int sm_count, cudaStream_t s)
+static cudaError_t dlap16_go(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
 {
-    const size_t smem = (size_t)kDlap16Warps * ((size_t)g.smallTS * 2 * 4 + 16);
+    const size_t smem = (size_t)kDlap16Warps * ((size_t)rg.tsp * 2 * 4 + 16);
     auto k = dlap16_kernel<PACK, ONE, SYM>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDlap16Warps * 32, smem);
+    cudaError_t e = ctas_per_sm(reinterpret_cast<const void *>(k), kDlap16Warps * 32, smem, per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)per_sm * sm_count;
-    const long long need = ((long long)g.small_tiles / 2 + 1 + kDlap16Warps - 1) / kDlap16Warps;
+    const long long need = ((rg.hi - rg.lo) / 2 + 1 + kDlap16Warps - 1) / kDlap16Warps;
     if (grid > need) grid = need;
-    k<<<(unsigned)grid, kDlap16Warps * 32, smem, s>>>(g);
+    k<<<(unsigned)grid, kDlap16Warps * 32, smem, s>>>(g, rg.lo, rg.hi, rg.counter, rg.tsp);
     return cudaGetLastError();
 }
 
 template <bool ONE, bool SYM>
-static cudaError_t dlap16_pick(const Group &g, int sm_count, cudaStream_t s)
+static cudaError_t dlap16_pick(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
 {
-    return g.pack ? dlap16_go<true, ONE, SYM>(g, sm_count, s) : dlap16_go<false, ONE, SYM>(g, sm_count, s);
+    return g.pack ? dlap16_go<true, ONE, SYM>(g, rg, sm_count, s) : dlap16_go<false, ONE, SYM>(g, rg, sm_count, s);
 }
 
-static cudaError_t dlap16_any(const Group &g, int sm_count, cudaStream_t s)
+static cudaError_t dlap_half(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
 {
-    if (g.sym) return g.B == 1 ? dlap16_pick<true, true>(g, sm_count, s) : dlap16_pick<false, true>(g, sm_count, s);
-    return g.B == 1 ? dlap16_pick<true, false>(g, sm_count, s) : dlap16_pick<false, false>(g, sm_count, s);
+    if (g.paired) return cudaErrorInvalidValue;  // the half-warp form serves the tile and class-sum stores
+    if (g.sym) return g.B == 1 ? dlap16_pick<true, true>(g, rg, sm_count, s) : dlap16_pick<false, true>(g, rg, sm_count, s);
+    return g.B == 1 ? dlap16_pick<true, false>(g, rg, sm_count, s) : dlap16_pick<false, false>(g, rg, sm_count, s);
 }
 
-static cudaError_t dlap_any(const Group &g, int sm_count, cudaStream_t s)
+// The group's two D->C ranges: [small_tiles, dtiles) (counter 0) and the
+// small instances' [0, small_tiles) (counter 1), each in its own shape.
+static DlapRange dlap_range(const Group &g, int which)
 {
-    if (g.sym) return g.B == 1 ? dlap_pick<true, 1>(g, sm_count, s) : dlap_pick<false, 1>(g, sm_count, s);
-    if (g.paired) return g.B == 1 ? dlap_pick<true, 2>(g, sm_count, s) : dlap_pick<false, 2>(g, sm_count, s);
-    return g.B == 1 ? dlap_pick<true, 0>(g, sm_count, s) : dlap_pick<false, 0>(g, sm_count, s);
+    DlapRange rg;
+    if (which == 0) {
+        rg.lo = g.small_tiles;
+        rg.hi = g.dtiles;
+        rg.counter = g.counter;
+        rg.tsp = g.maxTS;
+        rg.maxW = (g.maxN + 3) & ~3;
+    } else {
+        rg.lo = 0;
+        rg.hi = g.small_tiles;
+        rg.counter = g.counter + 1;
+        rg.tsp = g.smallTS;
+        rg.maxW = g.smallW;
+    }
+    rg.lanes = g.dshape[which].lanes;
+    rg.warps = g.dshape[which].warps;
+    return rg;
+}
+
+int dlap_cta_warps(const Group &g, int which)
+{
+    const DlapRange rg = dlap_range(g, which);
+    if (rg.hi <= rg.lo) return 0;
+    if (rg.lanes == 16) return kDlap16Warps;
+    if (rg.warps) return rg.warps;
+    // the choice of dlap_go: most warps resident, the smaller CTA on a tie
+    int w4 = 0, w16 = 0, w32 = 0;
+    cudaError_t e = cudaSuccess;
+    // (occupancy of the tile-store, one-instance kernel: the other forms use
+    // as many registers and the same shared memory, so they choose alike)
+    if (rg.maxW <= 32) {
+        if (g.pack) {
+            e = dlap_fit<1, true, true, 0, 4>(rg, w4);
+            if (e == cudaSuccess) e = dlap_fit<1, true, true, 0, 16>(rg, w16);
+            if (e == cudaSuccess) e = dlap_fit<1, true, true, 0, 32>(rg, w32);
+        } else {
+            e = dlap_fit<1, false, true, 0, 4>(rg, w4);
+            if (e == cudaSuccess) e = dlap_fit<1, false, true, 0, 16>(rg, w16);
+            if (e == cudaSuccess) e = dlap_fit<1, false, true, 0, 32>(rg, w32);
+        }
+    } else {
+        e = dlap_fit<2, true, true, 0, 4>(rg, w4);
+        if (e == cudaSuccess) e = dlap_fit<2, true, true, 0, 16>(rg, w16);
+        if (e == cudaSuccess) e = dlap_fit<2, true, true, 0, 32>(rg, w32);
+    }
+    if (e != cudaSuccess) return 0;
+    return (w32 > w4 && w32 > w16) ? 32 : w16 > w4 ? 16 : 4;
+}
+
+cudaError_t launch_dlap_range(const Group &g, int which, int sm_count, cudaStream_t s)
+{
+    const DlapRange rg = dlap_range(g, which);
+    if (rg.hi <= rg.lo) return cudaSuccess;
+    if (rg.lanes == 16) {
+        if (rg.maxW > 16) return cudaErrorInvalidValue;
+        return dlap_half(g, rg, sm_count, s);
+    }
+    return dlap_warp(g, rg, sm_count, s);
 }
 
 cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s, const SideStream *side)
 {
-    if (g.small_tiles <= 0) return dlap_any(g, sm_count, s);
-    if (g.small_tiles >= g.dtiles) return dlap16_any(g, sm_count, s);
+    if (g.small_tiles <= 0) return launch_dlap_range(g, 0, sm_count, s);
     cudaError_t e;
     if (!side) {
-        if ((e = dlap16_any(g, sm_count, s)) != cudaSuccess) return e;
-        return dlap_any(g, sm_count, s);
+        if ((e = launch_dlap_range(g, 1, sm_count, s)) != cudaSuccess) return e;
+        return launch_dlap_range(g, 0, sm_count, s);
     }
-    // fork: small tiles on the side stream, the rest here; join before returning
+    // fork: the small instances' range on the side stream, the rest here; join
+    // before returning
     if ((e = cudaEventRecord(side->fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(side->s2, side->fork, 0)) != cudaSuccess) return e;
-    if ((e = dlap16_any(g, sm_count, side->s2)) != cudaSuccess) return e;
-    if ((e = dlap_any(g, sm_count, s)) != cudaSuccess) return e;
+    if ((e = launch_dlap_range(g, 1, sm_count, side->s2)) != cudaSuccess) return e;
+    if ((e = launch_dlap_range(g, 0, sm_count, s)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(side->join, side->s2)) != cudaSuccess) return e;
     return cudaStreamWaitEvent(s, side->join, 0);
 }

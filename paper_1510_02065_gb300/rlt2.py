@@ -49,7 +49,8 @@ class rlt2_node(C.Structure):
 class rlt2_opts(C.Structure):
     _fields_ = [("rlt1_only", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
                 ("max_iters", C.c_int), ("ub", C.c_double), ("min_progress", C.c_double),
-                ("stream", C.c_void_p), ("store", C.c_int), ("lanes", C.c_int)]
+                ("stream", C.c_void_p), ("store", C.c_int), ("lanes", C.c_int),
+                ("cta_warps", C.c_int)]
 
 
 _lib = None
@@ -80,6 +81,7 @@ def lib():
         "rlt2_bound_history": (C.c_int, [_vp, _i64p, C.c_int, _intp]),
         "rlt2_get_state": (C.c_int, [_vp, C.c_int, _i32p, C.c_size_t]),
         "rlt2_work": (C.c_int, [_vp, _i64p]),
+        "rlt2_dlap_shape": (C.c_int, [_vp, _intp]),
         "rlt2_stage_times": (C.c_int, [_vp, _dblp, _intp]),
         "rlt2_reset_stage_times": (C.c_int, [_vp]),
         "rlt2_device_state": (_vp, [_vp, C.c_int]),
@@ -217,6 +219,13 @@ def rlt2_get_state(ctx, level: int, N: int):
     return out
 
 
+def rlt2_dlap_shape(ctx):
+    """(lanes per D->C LAP, warps per CTA, tuning passes still to come) of a context."""
+    out = (C.c_int * 3)()
+    _chk(lib().rlt2_dlap_shape(_vp(ctx), out), "rlt2_dlap_shape")
+    return out[0], out[1], bool(out[2])
+
+
 def rlt2_work(ctx):
     out = np.zeros(6, np.int64)
     _chk(lib().rlt2_work(_vp(ctx), _p64(out)), "rlt2_work")
@@ -313,9 +322,10 @@ def rlt2_subproblem(F, D, fac, loc):
 
 
 def rlt2_batch_bound(F, D, nodes, iters, stream=0, store=RLT2_STORE_TILES, lanes=0, return_lanes=False,
-                     ub=0.0):
+                     ub=0.0, cta_warps=0):
     """nodes: list of (fac, loc) arrays -> (LB per node as int64 array, device ms)
-    [, lanes per D->C LAP used for the nodes with N' <= 16]."""
+    [, D->C shapes used: ((lanes, CTA warps) for the nodes with N' > 16, the
+    same for those with N' <= 16), (0, 0) where there are none]."""
     F = np.ascontiguousarray(F, np.int32)
     D = np.ascontiguousarray(D, np.int32)
     keep = [(np.ascontiguousarray(f, np.int32), np.ascontiguousarray(l, np.int32)) for f, l in nodes]
@@ -328,13 +338,15 @@ def rlt2_batch_bound(F, D, nodes, iters, stream=0, store=RLT2_STORE_TILES, lanes
     o.stream = stream or None
     o.store = int(store)
     o.lanes = int(lanes)
+    o.cta_warps = int(cta_warps)
     o.ub = float(ub)
     out = np.zeros(len(keep), np.int64)
     ms = C.c_double()
-    used = C.c_int()
+    used = (C.c_int * 4)()
     _chk(lib().rlt2_batch_bound(_p32(F), _p32(D), F.shape[0], arr, len(keep), int(iters), C.byref(o),
-                                _p64(out), C.byref(ms), C.byref(used)), "rlt2_batch_bound")
-    return (out, ms.value, used.value) if return_lanes else (out, ms.value)
+                                _p64(out), C.byref(ms), used), "rlt2_batch_bound")
+    shapes = ((used[0], used[1]), (used[2], used[3]))
+    return (out, ms.value, shapes) if return_lanes else (out, ms.value)
 
 
 # ------------------------------------------------------------ convenience
@@ -344,17 +356,19 @@ class Context:
 
     def __init__(self, F, D, B_lin=None, lb_const=0, rlt1_only=False, use_graph=True,
                  profile=False, max_iters=65536, ub=0.0, min_progress=0.0, stream=0,
-                 store=RLT2_STORE_TILES, lanes=0):
-        o = self._opts(rlt1_only, use_graph, profile, max_iters, ub, min_progress, stream, store, lanes)
+                 store=RLT2_STORE_TILES, lanes=0, cta_warps=0):
+        o = self._opts(rlt1_only, use_graph, profile, max_iters, ub, min_progress, stream, store, lanes,
+                       cta_warps)
         self.N = int(np.asarray(F).shape[0])
         self.ctx = rlt2_create(F, D, self.N, B_lin, lb_const, o)
 
     @staticmethod
     def _opts(rlt1_only=False, use_graph=True, profile=False, max_iters=65536, ub=0.0,
-              min_progress=0.0, stream=0, store=RLT2_STORE_TILES, lanes=0):
+              min_progress=0.0, stream=0, store=RLT2_STORE_TILES, lanes=0, cta_warps=0):
         o = rlt2_default_opts()
         o.store = int(store)
         o.lanes = int(lanes)
+        o.cta_warps = int(cta_warps)
         o.rlt1_only = int(rlt1_only)
         o.use_graph = int(use_graph)
         o.profile = int(profile)
@@ -397,6 +411,9 @@ class Context:
 
     def work(self):
         return rlt2_work(self.ctx)
+
+    def dlap_shape(self):
+        return rlt2_dlap_shape(self.ctx)
 
     def stage_times(self):
         return rlt2_stage_times(self.ctx)

@@ -94,24 +94,29 @@ def test_batch_rejects_too_small_residual(gpu):
 
 
 @pytest.mark.gpu
-def test_batch_lanes_autotuned_and_forced_agree(gpu):
-    """Nodes with N' <= 16 and larger ones in one batch: the autotuned run (first
-    two passes time whole- and half-warp LAPs) and both forced forms give the
-    same bounds; the choice is reported."""
+def test_batch_shapes_autotuned_and_forced_agree(gpu):
+    """Nodes with N' <= 16 and larger ones in one batch (two D->C ranges): the
+    autotuned run (tuning passes first) and forced shapes give the same
+    bounds; the shapes used are reported per range."""
     F, D = I.clustered_euclid(20, seed=9)
     rng = np.random.default_rng(9)
     nodes = []
     for s in range(12):
-        k = int(rng.integers(1, 12))          # N' from 9 to 19: both forms present
+        k = int(rng.integers(1, 12))          # N' from 9 to 19: both ranges present
         nodes.append((rng.choice(20, size=k, replace=False), rng.choice(20, size=k, replace=False)))
     nodes.append((np.array([4]), np.array([7])))   # N' = 19
     nodes.append((np.arange(8), np.arange(8)[::-1].copy()))   # N' = 12
-    lb_auto, _, lanes = rlt2.rlt2_batch_bound(F, D, nodes, 5, return_lanes=True)
-    assert lanes in (16, 32)
-    lb16, _, l16 = rlt2.rlt2_batch_bound(F, D, nodes, 5, lanes=16, return_lanes=True)
-    lb32, _, l32 = rlt2.rlt2_batch_bound(F, D, nodes, 5, lanes=32, return_lanes=True)
-    assert (l16, l32) == (16, 32)
-    assert list(lb_auto) == list(lb16) == list(lb32)
+    lb_auto, _, shapes = rlt2.rlt2_batch_bound(F, D, nodes, 6, return_lanes=True)
+    (l0, w0), (l1, w1) = shapes
+    assert l0 == 32 and w0 in (4, 16, 32) and l1 in (16, 32) and w1 in (4, 16, 32)
+    for kw in (dict(lanes=32), dict(cta_warps=4), dict(cta_warps=16), dict(cta_warps=32)):
+        lb, _, got = rlt2.rlt2_batch_bound(F, D, nodes, 6, return_lanes=True, **kw)
+        assert list(lb) == list(lb_auto), kw
+        assert got[0][0] == got[1][0] == 32, (kw, got)
+        if "cta_warps" in kw:
+            assert got[0][1] == got[1][1] == kw["cta_warps"], (kw, got)
+    with pytest.raises(rlt2.Rlt2Error):       # half-warps do not cover the N' = 19 rows
+        rlt2.rlt2_batch_bound(F, D, nodes, 2, lanes=16)
     big = [(f, l) for f, l in nodes if 20 - len(f) > 16]
-    _, _, lanes_big = rlt2.rlt2_batch_bound(F, D, big, 3, return_lanes=True)
-    assert lanes_big == 32                    # no node small enough for half-warps
+    _, _, shapes_big = rlt2.rlt2_batch_bound(F, D, big, 5, return_lanes=True)
+    assert shapes_big[1] == (0, 0) and shapes_big[0][0] == 32

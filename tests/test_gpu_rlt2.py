@@ -322,32 +322,88 @@ def test_unknown_store_rejected(gpu):
     assert e.value.code == rlt2.RLT2_E_INVAL
 
 
-@pytest.mark.parametrize("store", STORES)
-@pytest.mark.parametrize("N", [5, 8, 13, 16])
-def test_half_warp_and_whole_warp_lanes_agree(gpu, orc, N, store):
-    """D->C LAPs of N <= 16 on half-warps (the default) and on whole warps give
-    the same state after every pass, equal to the oracle's."""
+def shapes_that_fit(N, store):
+    """D->C shapes (opts.lanes, opts.cta_warps) that can solve instances of size N."""
+    sh = [dict(lanes=32, cta_warps=w) for w in (4, 16, 32)]
+    if N <= 16 and store != rlt2.RLT2_STORE_PAIRS:
+        sh.insert(0, dict(lanes=16))
+    return sh
+
+
+@pytest.mark.parametrize("store", STORES + [rlt2.RLT2_STORE_PAIRS])
+@pytest.mark.parametrize("N", [5, 8, 13, 16, 17, 21])
+def test_every_dlap_shape_agrees(gpu, orc, N, store):
+    """D->C in every shape that fits (half-warps for N <= 16 in the tile and
+    class-sum stores; whole warps in CTAs of 4, 16 and 32 warps) and in the
+    autotuned one gives the same state after every pass, equal to the
+    oracle's, and the same Hungarian work counts (LAPs, steps, relaxations)."""
     F, D = I.clustered_euclid(N, seed=40 + N)
     Bl = np.random.default_rng(N).integers(0, 30, size=(N, N)).astype(np.int32)
-    st = orc.State(F, D, B_lin=Bl, lb_const=3)
-    with rlt2.Context(F, D, B_lin=Bl, lb_const=3, store=store, lanes=16) as a, \
-            rlt2.Context(F, D, B_lin=Bl, lb_const=3, store=store, lanes=32) as b:
-        for t in range(6):
-            a.iterate(1)
-            b.iterate(1)
+    paired = store == rlt2.RLT2_STORE_PAIRS
+    st = orc.State(F, D, B_lin=Bl, lb_const=3, paired=paired)
+    shapes = shapes_that_fit(N, store) + [dict()]
+    ctxs = [rlt2.Context(F, D, B_lin=Bl, lb_const=3, store=store, **kw) for kw in shapes]
+    try:
+        for t in range(6):   # an unmeasured pass and one per candidate shape: tuning is done
             st.iterate()
-            assert_same_state(a, st, "16 lanes, pass %d" % (t + 1))
-            assert_same_state(b, st, "32 lanes, pass %d" % (t + 1))
-        wa, wb = a.work(), b.work()
-        assert (wa["d_laps"], wa["d_steps"], wa["d_relaxations"]) == (wb["d_laps"], wb["d_steps"], wb["d_relaxations"])
+            for c, kw in zip(ctxs, shapes):
+                c.iterate(1)
+                if N <= 13:
+                    assert_same_state(c, st, "%s, pass %d" % (kw, t + 1))
+                else:
+                    assert c.bound()[1] == st.LB, kw
+                    assert (c.state(1) == compact_y(st.c)).all(), kw
+        ow = st.work()
+        ref = (ow["laps"], ow["steps"], ow["relaxations"])
+        for c, kw in zip(ctxs, shapes):
+            w = c.work()
+            assert (w["laps"], w["steps"], w["relaxations"]) == ref, kw
+            lanes, warps, tuning = c.dlap_shape()
+            assert not tuning and lanes in (16, 32) and warps in (4, 16, 32), (kw, lanes, warps)
+            if kw:
+                assert lanes == kw["lanes"] and warps == kw.get("cta_warps", 4), kw
+    finally:
+        for c in ctxs:
+            c.close()
 
 
-def test_unknown_lanes_rejected(gpu):
+@pytest.mark.parametrize("store", STORES)
+def test_dlap_shapes_agree_at_size(gpu, store):
+    """N = 30: every CTA shape of the whole-warp D->C kernel gives the same LB,
+    C and sampled D after each of three passes, and the same work counts
+    (pass 1 is checked against the oracle in test_headline_n30)."""
+    N = 30
+    F, D = I.clustered_euclid(N, seed=N + 5)
+    ref = None
+    for kw in shapes_that_fit(N, store):
+        with rlt2.Context(F, D, store=store, **kw) as c:
+            got = []
+            for t in range(3):
+                c.iterate(1)
+                z = c.state(2)
+                got.append((c.bound()[1], c.state(1).copy(), z[:: 1 + z.size // 500000].copy()))
+            w = c.work()
+            got.append((w["laps"], w["steps"], w["relaxations"]))
+        if ref is None:
+            ref = got
+            continue
+        for a_, b_ in zip(got[:-1], ref[:-1]):
+            assert a_[0] == b_[0], kw
+            assert (a_[1] == b_[1]).all() and (a_[2] == b_[2]).all(), kw
+        assert got[-1] == ref[-1], kw
+
+
+def test_unknown_shapes_rejected(gpu):
     F, D = I.uniform_symmetric(6, seed=1)
-    with pytest.raises(rlt2.Rlt2Error) as e:
-        rlt2.Context(F, D, lanes=8)
+    for kw in (dict(lanes=8), dict(lanes=12), dict(cta_warps=5), dict(cta_warps=-1),
+               dict(lanes=16, cta_warps=4), dict(lanes=16, store=rlt2.RLT2_STORE_PAIRS)):
+        with pytest.raises(rlt2.Rlt2Error) as e:
+            rlt2.Context(F, D, **kw)
+        assert e.value.code == rlt2.RLT2_E_INVAL, kw
+    F, D = I.uniform_symmetric(20, seed=1)
+    with pytest.raises(rlt2.Rlt2Error) as e:   # half-warps cover rows of at most 16 columns
+        rlt2.Context(F, D, lanes=16)
     assert e.value.code == rlt2.RLT2_E_INVAL
-
 
 
 # ------------------------------------------------------------ pair store
