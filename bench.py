@@ -28,10 +28,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RLT2 dual-ascent iters/sec at N=30"
-OPS_PER_RELAXATION = 9   # textbook int ops of one relaxation
+OPS_PER_RELAXATION = 9   # textbook int ops of one relaxation: 2 subtractions, compare with the
+                         # label, its 2 conditional updates, compare with the minimum, its 2
+                         # conditional updates, the label decrement
 ALU_LANES_PER_SM = 64    # integer ALU pipe: 16 lanes per scheduler, 4 schedulers
 # DRAM bytes per launch of the D->C and fused-pass kernels on the 30-facility
-# workload (tile store), from one ncu capture (profiles/dram_dlap_p1_clustered_n30.md);
+# workload (tile store), from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum;
 # reported only while the kernel's sources hash to the captured version.
 DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2714500096 + 2651857664,
                 "files": ("lap_kernels.cu", "device.cuh", "kernels.h"),
@@ -66,7 +68,7 @@ def parse():
     ap.add_argument("--batch-nodes", type=int, default=256,
                     help="B&B nodes of the batched-bounding measurement (0: skip)")
     ap.add_argument("--batch-iters", type=int, default=100)
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--serve-requests", type=int, default=1000,
                     help="requests of the serving measurement (0: skip)")
     ap.add_argument("--lanes", type=int, default=0,
                     help="lanes per D->C LAP (4, 8, 16, 32); 0: autotuned")
@@ -87,11 +89,12 @@ def serve_measure(instances, torch, count, passes=50, rate=50.0):
     is the clustered instance of size N_r uniform in [12, 30] with seed r, 50
     passes.  Admission by device memory (budget 64 GB).  If the measured
     throughput is below the offered rate (saturation), the stream is served
-    again at 0.8x the measured capacity and both runs are reported.
+    again at 0.8x the measured capacity (its first min(count, 500) requests)
+    and both runs are reported.
     """
     from paper_1510_02065_gb300.serve import BoundServer, Request
 
-    def run(r):
+    def run(r, count):
         arr, Ns = instances.poisson_requests(count, rate=r)
         reqs = []
         for rid in range(count):
@@ -103,11 +106,11 @@ def serve_measure(instances, torch, count, passes=50, rate=50.0):
         st["offered_rate"] = r
         return st
 
-    first = run(rate)
+    first = run(rate, count)
     out = {"metric": "served RLT2 bound requests", "unit": "requests/s", "passes": passes,
            "N_range": [12, 30], "offered": first}
     if first["throughput"] is not None and first["throughput"] < 0.95 * rate:
-        out["at_0.8_capacity"] = run(0.8 * first["throughput"])
+        out["at_0.8_capacity"] = run(0.8 * first["throughput"], min(count, 500))
     return out
 
 
@@ -140,7 +143,7 @@ def n35_measure(rlt2, instances, torch, steps, store, warmup=3, workload="cluste
                 rlt2.rlt2_state_bytes(N, store=store) / 1e9)}
 
 
-# DRAM bytes of one f64_dlap_kernel launch at N=20 (profiles/f64_sections_clustered_n20.md)
+# DRAM bytes of one f64_dlap_kernel launch at N=20 (one ncu capture of the DRAM byte counters)
 # per tile coefficient read (n x N per tile) and written (n x n), valid while
 # the FP64 sources hash to the captured version; other sizes scale by those units
 F64_DLAP_TRAFFIC = {"N": 20, "read": 417048832, "write": 358820864, "files": ("f64.cu", "device.cuh"),
@@ -261,34 +264,79 @@ def batch_measure(rlt2, instances, torch, nodes_count, iters):
 
     Nodes of one 25-facility clustered instance, node s fixing 1-15 random
     facilities (residual sizes 10-24), `iters` passes each.  Batched: one
-    rlt2_batch_bound call (one captured graph for all nodes and passes).
-    Plain: per node rlt2_subproblem, rlt2_create, rlt2_iterate, rlt2_bound,
-    rlt2_destroy.  Both wall-clock, both including every allocation and copy;
-    the bounds must be identical.
+    rlt2_batch_bound call (tuning passes, then one captured graph for all
+    nodes and the remaining passes).  Plain: per node rlt2_subproblem,
+    rlt2_create, rlt2_iterate, rlt2_bound, rlt2_destroy.  Both wall-clock,
+    both including every allocation and copy, both after an untimed warm-up
+    of their own on four nodes (module loading, first graph capture); the
+    bounds must be identical.  By residual size: the same two arms on the
+    nodes of each range of N' (batched: one call per range).
     """
     F, D = instances.clustered_euclid(25, seed=0)
     nodes = instances.subproblem_nodes(25, nodes_count)
+    s = torch.cuda.Stream()
+
+    def plain_one(fac, loc):
+        Fp, Dp, Bl, cst = rlt2.rlt2_subproblem(F, D, fac, loc)
+        with rlt2.Context(Fp, Dp, B_lin=Bl, lb_const=cst, max_iters=iters + 1, stream=s.cuda_stream) as c:
+            c.iterate(iters)
+            return c.bound()[1]
+
+    # untimed warm-up of both arms
+    rlt2.rlt2_batch_bound(F, D, nodes[:4], 3)
+    for fac, loc in nodes[:4]:
+        plain_one(fac, loc)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lbs, dev_ms, lanes = rlt2.rlt2_batch_bound(F, D, nodes, iters, return_lanes=True)
+    lbs, dev_ms, shapes = rlt2.rlt2_batch_bound(F, D, nodes, iters, return_lanes=True)
     t_batch = time.perf_counter() - t0
-    s = torch.cuda.Stream()
-    plain = []
+    plain, t_node = [], []
     t0 = time.perf_counter()
     for fac, loc in nodes:
-        Fp, Dp, Bl, cst = rlt2.rlt2_subproblem(F, D, fac, loc)
-        with rlt2.Context(Fp, Dp, B_lin=Bl, lb_const=cst, max_iters=iters + 1,
-                          stream=s.cuda_stream) as c:
-            c.iterate(iters)
-            plain.append(c.bound()[1])
+        t1 = time.perf_counter()
+        plain.append(plain_one(fac, loc))
+        t_node.append(time.perf_counter() - t1)
     t_plain = time.perf_counter() - t0
     sizes = [25 - len(f) for f, _ in nodes]
+    by_size = []
+    for lo, hi in ((10, 14), (15, 19), (20, 24)):
+        idx = [i for i, n in enumerate(sizes) if lo <= n <= hi]
+        if not idx:
+            continue
+        t0 = time.perf_counter()
+        rlt2.rlt2_batch_bound(F, D, [nodes[i] for i in idx], iters)
+        tb = time.perf_counter() - t0
+        tp = sum(t_node[i] for i in idx)
+        by_size.append({"residual_N": [lo, hi], "nodes": len(idx), "batched_nodes_per_s": len(idx) / tb,
+                        "plain_nodes_per_s": len(idx) / tp, "speedup": tp / tb})
     return {"metric": "batched B&B nodes/sec vs plain", "unit": "nodes/s",
             "batched": nodes_count / t_batch, "plain": nodes_count / t_plain,
             "speedup": t_plain / t_batch, "identical_bounds": list(plain) == [int(x) for x in lbs],
             "nodes": nodes_count, "iters": iters, "residual_N": [min(sizes), max(sizes)],
             "batched_device_ms": dev_ms, "graph_launches": 1,
-            "autotuned_lanes_per_lap_small_nodes": lanes,
+            "dlap_shape_after_tuning": {"N_gt_16": {"lanes": shapes[0][0], "cta_warps": shapes[0][1]},
+                                        "N_le_16": {"lanes": shapes[1][0], "cta_warps": shapes[1][1]}},
+            "by_residual_size": by_size,
+            "config": "clustered N=25 seed 0, node s fixes 1-15 pairs from default_rng(1000+s)"}
+
+
+def batch_sharded_measure(rlt2, instances, torch, dist, nodes_count, iters):
+    """The same nodes dealt round-robin over the ranks (one GPU each), each
+    rank bounding its share with one rlt2_batch_bound call; wall clock from a
+    barrier to the gathered bounds, the maximum over the ranks."""
+    from paper_1510_02065_gb300 import distributed
+    F, D = instances.clustered_euclid(25, seed=0)
+    nodes = instances.subproblem_nodes(25, nodes_count)
+    rlt2.rlt2_batch_bound(F, D, nodes[:4], 3)   # warm-up
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    lbs = distributed.bound_nodes_sharded(F, D, nodes, iters)
+    t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return {"metric": "batched B&B nodes/sec, nodes sharded over the ranks", "unit": "nodes/s",
+            "value": nodes_count / float(t.item()), "nodes": nodes_count, "iters": iters,
+            "ranks": dist.get_world_size(), "scaling": "strong", "lb_sum": int(sum(lbs)),
             "config": "clustered N=25 seed 0, node s fixes 1-15 pairs from default_rng(1000+s)"}
 
 
@@ -479,9 +527,15 @@ def main():
     props = torch.cuda.get_device_properties(local)
 
     store = rlt2.RLT2_STORE_CLASSES if args.store == "classes" else rlt2.RLT2_STORE_TILES
-    ctx = rlt2.Context(F, D, profile=True, use_graph=True, max_iters=K + W + 16,
+    ctx = rlt2.Context(F, D, profile=True, use_graph=True, max_iters=K + W + 24,
                        stream=stream.cuda_stream, store=store, lanes=args.lanes, cta_warps=args.cta_warps)
     ctx.iterate(W)
+    # the D->C shape is tuned on a context's first passes (see rlt2.h): should
+    # W be shorter than that, the remaining tuning passes run here, untimed
+    extra = 0
+    while ctx.dlap_shape()[2] and extra < 8:
+        ctx.iterate(1)
+        extra += 1
     torch.cuda.synchronize()
     rlt2.rlt2_reset_stage_times(ctx.ctx)
     w0 = ctx.work()
@@ -507,6 +561,7 @@ def main():
     stage_ms, passes = ctx.stage_times()
     w1 = ctx.work()
     lb, lb_exact, iters = ctx.bound()
+    shape = ctx.dlap_shape()
     ctx.close()
 
     ms_per_step = ms / K
@@ -573,6 +628,7 @@ def main():
                         "peak_kind": peaks_kind},
         "gpu_launches": 5 * K,
         "clocks": clk,
+        "dlap_shape": {"lanes": shape[0], "cta_warps": shape[1], "tuning_passes_after_warmup": extra},
     }
 
     # end to end through the public API with host buffers: create (H2D of F, D
@@ -604,6 +660,11 @@ def main():
     solo = world == 1
     if args.batch_nodes > 0 and solo:
         line["batch"] = batch_measure(rlt2, instances, torch, args.batch_nodes, args.batch_iters)
+    if args.batch_nodes > 0 and not solo:
+        # B&B nodes shard naturally: each rank bounds its share (no collective
+        # on the data path; the bounds are gathered once)
+        line["batch_sharded"] = batch_sharded_measure(rlt2, instances, torch, dist, args.batch_nodes,
+                                                      args.batch_iters)
     if args.n35_steps > 0 and solo:
         line["n35"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_CLASSES)
         line["n35_tiles"] = n35_measure(rlt2, instances, torch, args.n35_steps, rlt2.RLT2_STORE_TILES)

@@ -90,20 +90,24 @@ typedef struct {
 
 /*
  * Autotuning of the D->C shape (opts.lanes = opts.cta_warps = 0).  The first
- * passes of a context, group or batch are tuning passes: one unmeasured pass
+ * passes of a context or batch are tuning passes: one unmeasured pass
  * in the default shape (whole warps in the CTA size that keeps the most warps
  * resident), then one pass per candidate -- the default, half-warps where the
  * rows have at most 16 columns, whole warps in CTAs of 4, 16 and 32 warps
  * where they fit (up to six passes in all) -- each timed by CUDA events and
  * measured by the Hungarian's step counter.  A candidate replaces the default
  * only if its time per step is at least 3% lower (a pass's time per step
- * drifts by a percent or two from one pass to the next).  In a group or batch that holds instances with N <= 16 and
- * larger ones, the two kinds form separate D->C ranges, each tuned on its own
- * (the small one on a second stream beside the other after tuning).  Tuning
+ * drifts by a percent or two from one pass to the next).  In a group or
+ * batch that holds instances with N <= 16 and larger ones, the two kinds form
+ * separate D->C ranges, each with its own shape (a batch tunes each; after
+ * tuning the small one runs on a second stream beside the other).  Tuning
  * passes are ordinary passes (every shape gives the same results), launched
  * directly rather than from a graph, and each synchronises the stream.  The
  * choice is remembered for the process per device, store and row width: later
- * contexts and groups with the same key start with it and do not tune.
+ * contexts, groups and batches with the same key start with it and do not
+ * tune.  A group (rlt2_group_create) takes the remembered shape of its key,
+ * else the default, and never tunes (a server rebuilds its group whenever its
+ * membership changes, often sooner than tuning would end).
  */
 
 /*

@@ -25,6 +25,18 @@ facilities to locations.  This driver does the same on one GPU:
 
 Children are visited in increasing order of their bound.  With integer costs
 a node whose bound reaches the incumbent cannot contain a better solution.
+
+Several GPUs (one process each, as the paper runs one host thread per GPU
+with its own subtrees): with a torch.distributed process group, every rank
+expands the top of the tree the same way (deterministic: the bounds are bit
+for bit the same on every GPU) until there are at least `frontier_per_rank`
+subtrees per rank, deals them round-robin (distributed.shard) and searches
+its own on its own GPU.  Every `sync_every` nodes the ranks exchange the
+incumbent (an all-reduce of one integer, the minimum) and whether any of them
+has work left; nothing else crosses ranks, and no collective touches the
+bounding itself.  At the end the optimum, its permutation and the counters
+are gathered.
+
 All bounding runs through the C ABI (librlt2.so); this module only schedules.
 """
 from __future__ import annotations
@@ -74,7 +86,8 @@ class BranchAndBound:
 
     def __init__(self, F, D, iters: int = 12, root_iters: int = 30, strong_depth: int = 1,
                  strong_iters: int = 3, enum_size: int = 3, ub: Optional[int] = None,
-                 node_limit: int = 1_000_000, store: int = rlt2.RLT2_STORE_TILES, warm: bool = False):
+                 node_limit: int = 1_000_000, store: int = rlt2.RLT2_STORE_TILES, warm: bool = False,
+                 group=None, sync_every: int = 16, frontier_per_rank: int = 2):
         self.F = np.ascontiguousarray(F, np.int32)
         self.D = np.ascontiguousarray(D, np.int32)
         self.N = self.F.shape[0]
@@ -87,6 +100,9 @@ class BranchAndBound:
         self.store = store
         self.warm = warm
         self.ub0 = ub
+        self.group = group
+        self.sync_every = max(1, sync_every)
+        self.frontier_per_rank = max(1, frontier_per_rank)
         self.stats = dict(nodes_bounded=0, nodes_pruned=0, leaves_enumerated=0, batches=0,
                           strong_evaluations=0)
 
@@ -102,13 +118,20 @@ class BranchAndBound:
         """Children of the node held by ctx, warm-started from its dual state and
         advanced `iters` passes together; returns (bound, context) per location."""
         fl = free_facs.index(f)
-        kids = [ctx.child(fl, x, ub=float(self.ub), max_iters=self.iters + 1) for x in range(len(free_locs))]
-        grp = rlt2.rlt2_group_create([k.ctx for k in kids])
+        kids = []
         try:
-            rlt2.rlt2_group_iterate(grp, self.iters)
-            rlt2.rlt2_group_sync(grp)
-        finally:
-            rlt2.rlt2_group_destroy(grp)
+            for x in range(len(free_locs)):
+                kids.append(ctx.child(fl, x, ub=float(self.ub), max_iters=self.iters + 1))
+            grp = rlt2.rlt2_group_create([k.ctx for k in kids])
+            try:
+                rlt2.rlt2_group_iterate(grp, self.iters)
+                rlt2.rlt2_group_sync(grp)
+            finally:
+                rlt2.rlt2_group_destroy(grp)
+        except BaseException:
+            for k in kids:      # each holds a store of D on the device
+                k.close()
+            raise
         self.stats["batches"] += 1
         self.stats["nodes_bounded"] += len(kids)
         return [(k.bound()[1], k) for k in kids]
@@ -180,6 +203,8 @@ class BranchAndBound:
         return 1
 
     def solve(self) -> dict:
+        if self.group is not None:
+            return self._solve_distributed()
         t0 = time.perf_counter()
         if self.ub0 is not None:
             self.ub, self.best = int(self.ub0), None
@@ -211,3 +236,80 @@ class BranchAndBound:
         return dict(optimum=self.ub, perm=self.best, proven=not stack, root_lb=root_lb, warm=self.warm,
                     ub_initial=ub_initial, nodes_visited=visited, seconds=time.perf_counter() - t0,
                     **self.stats)
+
+    # -- several ranks ------------------------------------------------------
+    def _solve_distributed(self) -> dict:
+        """The search over the ranks of self.group (see the module docstring)."""
+        import torch
+        import torch.distributed as dist
+
+        from .distributed import shard
+
+        if self.warm:
+            raise ValueError("the distributed search starts every subtree cold")
+        t0 = time.perf_counter()
+        rank, world = dist.get_rank(self.group), dist.get_world_size(self.group)
+        if self.ub0 is not None:
+            self.ub, self.best = int(self.ub0), None
+        else:
+            self.ub, self.best = local_search_ub(self.F, self.D)   # the same on every rank
+        ub_initial = self.ub
+        with rlt2.Context(self.F, self.D, ub=float(self.ub), max_iters=self.root_iters + 1,
+                          store=self.store) as root:
+            root.iterate(self.root_iters)
+            root_lb = root.bound()[1]
+        # the top of the tree, expanded alike on every rank (breadth first)
+        frontier = [(root_lb, [], [], None)] if root_lb < self.ub else []
+        visited = 0
+        while frontier and len(frontier) < self.frontier_per_rank * world:
+            nxt = []
+            expandable = False
+            for lb, fac, loc, _ in frontier:
+                if self.N - len(fac) <= self.enum_size + 1:
+                    nxt.append((lb, fac, loc, None))
+                    continue
+                expandable = True
+                visited += self._expand(lb, fac, loc, None, nxt)
+            frontier = nxt
+            if not expandable:
+                break
+        frontier.sort(key=lambda x: (x[0], x[1], x[2]))
+        mine = [node for _, node in shard(frontier, rank, world)]
+        stack = sorted(mine, key=lambda x: -x[0])      # popped in increasing bound order
+        top = dict(self.stats)
+        for k in self.stats:
+            self.stats[k] = 0      # the search below counts this rank's own work
+        local = 0
+        buf = torch.zeros(2, dtype=torch.int64)
+        while True:
+            n = 0
+            while stack and n < self.sync_every and visited + local < self.node_limit:
+                lb, fac, loc, _ = stack.pop()
+                local += self._expand(lb, fac, loc, None, stack)
+                n += 1
+            # incumbent and remaining work across the ranks
+            buf[0] = self.ub
+            dist.all_reduce(buf[:1], op=dist.ReduceOp.MIN, group=self.group)
+            self.ub = min(self.ub, int(buf[0]))
+            buf[1] = 1 if (stack and visited + local < self.node_limit) else 0
+            dist.all_reduce(buf[1:], op=dist.ReduceOp.MAX, group=self.group)
+            if int(buf[1]) == 0:
+                break
+        parts = [None] * world
+        mine_best = None if self.best is None else [int(x) for x in self.best]
+        dist.all_gather_object(parts, dict(perm=mine_best, proven=not stack, nodes=local,
+                                           stats=dict(self.stats)), group=self.group)
+        # the incumbent (the minimum over the ranks after the last exchange) and
+        # a permutation of that cost found by some rank (none if it is ub0's)
+        perm = None
+        for part in parts:
+            if part["perm"] is not None and qap_cost(self.F, self.D, np.array(part["perm"])) == self.ub:
+                perm = np.array(part["perm"])
+                break
+        stats = {k: top[k] + sum(part["stats"][k] for part in parts) for k in top}
+        return dict(optimum=self.ub, perm=perm, proven=all(part["proven"] for part in parts),
+                    root_lb=root_lb, warm=False, ub_initial=ub_initial,
+                    nodes_visited=visited + sum(part["nodes"] for part in parts),
+                    seconds=time.perf_counter() - t0, ranks=world,
+                    nodes_per_rank=[part["nodes"] for part in parts], **stats)
+

@@ -966,7 +966,6 @@ struct rlt2_group {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     SideStream side{};     // the small instances' D->C range beside the other one
-    DlapTuner tuner;       // D->C shape tuning on the first passes (opts.lanes = 0)
 };
 
 static int make_side(SideStream &sd)
@@ -1106,7 +1105,10 @@ int rlt2_group_create(rlt2_ctx *const *ctxs, int count, void *stream, rlt2_group
     g.snap = reinterpret_cast<DevStatus *>(gr->mem + o_snap);
     g.triples = reinterpret_cast<const int4 *>(gr->mem + o_tri);
     g.first = hn[0];
-    const int rc_shape = setup_dshape(g, ctxs[0]->opts, &gr->tuner);
+    // groups take the remembered shape or the default and do not tune: a
+    // server rebuilds its group whenever membership changes, often sooner
+    // than tuning would end
+    const int rc_shape = setup_dshape(g, ctxs[0]->opts, nullptr);
     if (rc_shape != RLT2_OK) return fail(rc_shape);
     // the group's stream starts after every context's pending work
     for (rlt2_ctx *c : gr->ctxs) {
@@ -1133,14 +1135,8 @@ int rlt2_group_iterate(rlt2_group *gr, int k)
     for (rlt2_ctx *c : gr->ctxs)
         if ((long long)c->enqueued + k > c->opts.max_iters) return RLT2_E_STATE;
     if (k == 0) return RLT2_OK;
-    int t = 0;
-    for (; t < k && gr->tuner.active(); t++) {
-        const int rc = tune_step(gr->g, gr->tuner, gr->sm_count, gr->stream, nullptr);
-        if (rc != RLT2_OK) return rc;
-    }
-    if (t < k && !gr->exec)
-        CK(capture_passes(gr->g, gr->sm_count, gr->stream, 1, &gr->graph, &gr->exec, &gr->side));
-    for (; t < k; t++) CK(cudaGraphLaunch(gr->exec, gr->stream));
+    if (!gr->exec) CK(capture_passes(gr->g, gr->sm_count, gr->stream, 1, &gr->graph, &gr->exec, &gr->side));
+    for (int t = 0; t < k; t++) CK(cudaGraphLaunch(gr->exec, gr->stream));
     for (rlt2_ctx *c : gr->ctxs) c->enqueued += k;
     // every context's later work starts after the group's passes
     CK(cudaEventRecord(gr->done, gr->stream));

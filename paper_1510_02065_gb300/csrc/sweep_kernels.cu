@@ -261,53 +261,59 @@ __device__ __forceinline__ void p1_shares(const P1Layout &L, int N, int i, int k
     }
 }
 
-// One CTA per (instance, facility triple, location chunk) of the group; yS
-// holds c' (C plus the spread of B) per tile.  ONE (a group of one instance):
-// the instance is the kernel parameter g.first.
-template <int JC, bool ONE>
-__global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant__ Group g)
-{
-    if (blockIdx.x == 0 && threadIdx.x < 2) g.counter[threadIdx.x] = 0;  // work counters of the D -> C sweep
-    const NodeDesc &nd =
-        ONE ? g.first
-            : g.nodes[find_node(g.nodes, g.B, blockIdx.x, [](const NodeDesc &d) { return (long long)d.cta_base; })];
-    const PassState p = nd.p;
-    if (*p.stop) return;
-    const int N = nd.N, W = nd.W, nchunks = nd.nchunks;
-    const FastDiv fN = nd.fN, fn = nd.fn;
-    const int bid = blockIdx.x - nd.cta_base;
-    extern __shared__ __align__(128) int sm[];
-    const P1Layout L = p1_layout(N, W, JC, false);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t TS = (size_t)(N - 2) * W;
-    const int4 tr = g.triples[bid / nchunks];
-    const int i = tr.x, k = tr.y, pp = tr.z;
-    const int j0 = (bid % nchunks) * JC;
-    const int jc = min(JC, N - j0);
-    const int *__restrict__ yS = p.yS;
-    int *__restrict__ z = p.z;
-    const int NN = N * N;
+// One work unit of the fused pass over D in the tile store: an instance's
+// facility triple i < k < p and chunk of JC locations j0.. of i (jc of them
+// in the instance's last chunk).  ONE (a group of one instance): the instance
+// is the kernel parameter g.first.
+struct P1Unit {
+    const NodeDesc *nd;
+    int i, k, pp, j0, jc;
+    bool live;   // the instance's stopping rule has not fired
+};
 
-    // ---- loads, all in flight at once, completing on bar: every full row by
-    // one bulk copy; the JC-location pieces of kinds 4 and 6 by one tensor
-    // copy per kind (rows i of tiles (k,a,p,l), resp. (p,a,k,l), all a and l)
-    // where the map exists (JC = 4), else one aligned cp.async per piece
-    __shared__ __align__(8) uint64_t bar;
+template <int JC, bool ONE>
+__device__ __forceinline__ P1Unit p1_unit(const Group &g, int u)
+{
+    P1Unit w;
+    w.nd = ONE ? &g.first
+               : &g.nodes[find_node(g.nodes, g.B, u, [](const NodeDesc &d) { return (long long)d.cta_base; })];
+    const int bid = u - w.nd->cta_base, nchunks = w.nd->nchunks;
+    const int4 tr = g.triples[bid / nchunks];
+    w.i = tr.x;
+    w.k = tr.y;
+    w.pp = tr.z;
+    w.j0 = (bid % nchunks) * JC;
+    w.jc = min(JC, w.nd->N - w.j0);
+    w.live = !*w.nd->p.stop;
+    return w;
+}
+
+// Start every load of unit w into the layout at sm, all in flight at once:
+// every full row by one bulk copy and, where the map exists (JC = 4), the
+// JC-location pieces of kinds 4 and 6 by one tensor copy per kind (rows i of
+// tiles (k,a,p,l), resp. (p,a,k,l), all a and l), all completing on bar;
+// else one aligned cp.async per piece.  Then c' of every member tile (4-byte
+// cp.async into the H arrays).  The caller commits the cp.async group.
+template <int JC, bool ONE>
+__device__ __forceinline__ void p1_issue(const Group &g, const P1Unit &w, int *sm, uint64_t *bar)
+{
+    const NodeDesc &nd = *w.nd;
+    const int N = nd.N, W = nd.W, NN = N * N;
+    const FastDiv fN = nd.fN;
+    const P1Layout L = p1_layout(N, W, JC, false);
+    const size_t TS = (size_t)(N - 2) * W;
+    const int i = w.i, k = w.k, pp = w.pp, j0 = w.j0, jc = w.jc;
+    int *__restrict__ z = nd.p.z;
     const bool tma = JC == 4 && nd.zmap_ok;
     const void *zmap = &nd.zmap;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-        if (!ONE && tma) tensormap_acquire(zmap);
-    }
-    __syncthreads();
     const unsigned rowBytes = (unsigned)W * 4u;
     if (threadIdx.x == 0) {
+        if (!ONE && tma) tensormap_acquire(zmap);
         const unsigned pieceBytes = tma ? 2u * (unsigned)(N * L.P46) * 4u : 0u;
-        mbar_arrive_expect_tx(&bar, (unsigned)(4 * jc * (N - 1)) * rowBytes + pieceBytes);
+        mbar_arrive_expect_tx(bar, (unsigned)(4 * jc * (N - 1)) * rowBytes + pieceBytes);
         if (tma) {
-            tensor_load5(sm + L.A4, zmap, j0, i, 0, pp - 1, k * N, &bar);  // kind 4: tile (k,a,p,l), row i
-            tensor_load5(sm + L.A6, zmap, j0, i, 0, k, pp * N, &bar);      // kind 6: tile (p,a,k,l), row i
+            tensor_load5(sm + L.A4, zmap, j0, i, 0, pp - 1, k * N, bar);  // kind 4: tile (k,a,p,l), row i
+            tensor_load5(sm + L.A6, zmap, j0, i, 0, k, pp * N, bar);      // kind 6: tile (p,a,k,l), row i
         }
     }
     for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
         full_row(q, N, i, k, pp, j, x, t, row);
         const int base = q == 0 ? L.A1 : q == 1 ? L.A3 : q == 2 ? L.A2 : L.A5;
         const int pitch = q < 2 ? L.S13 : L.S25;
-        bulk_load_tx(sm + base + (jj * N + x) * pitch, z + t * TS + (size_t)row * W, rowBytes, &bar);
+        bulk_load_tx(sm + base + (jj * N + x) * pitch, z + t * TS + (size_t)row * W, rowBytes, bar);
     }
     for (int e = tma ? 2 * NN : threadIdx.x; e < 2 * NN; e += kP1Threads) {
         const int kind = e >= NN, r2 = e - kind * NN;
@@ -329,26 +335,24 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
         cp_async_piece<JC>(sm + (kind ? L.A6 : L.A4) + a * L.P46 + (l - (l > a)) * JC,
                            z + t * TS + (size_t)i * W + j0);
     }
+    p1_gather_c<JC, false>(L, N, i, k, pp, j0, jc, fN, nd.p.yS, nullptr, 0, sm);
+}
 
-    // ---- c' of every member tile, gathered while the copies fly (4-byte
-    // asynchronous copies into the H arrays, turned into shares below)
-    p1_gather_c<JC, false>(L, N, i, k, pp, j0, jc, fN, yS, nullptr, 0, sm);
-
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    if (__syncthreads_or(!mbar_wait(&bar, 0))) {
-        // give up: record it, let the copies in flight land (bounded), leave
-        if (threadIdx.x == 0) atomicOr(&g.status->err, kDevTimeout);
-        mbar_wait(&bar, 0);
-        __syncthreads();
-        return;
-    }
-    p1_shares<false>(L, N, i, k, pp, fn, sm);
+// Shares of c' and the split of every class {(i,j),(k,nn),(p,qq)}, j in the
+// chunk, in shared memory (the loads of unit w have landed and the CTA is
+// synchronised): one warp per nn, lanes over qq, each lane the JC classes of
+// its (nn, qq).  Their members of kinds 4 and 6 are exactly the pieces
+// (nn, qq) and (qq, nn), which move as one vector each.
+template <int JC>
+__device__ __forceinline__ void p1_split(const P1Unit &w, int *sm)
+{
+    const NodeDesc &nd = *w.nd;
+    const int N = nd.N;
+    const P1Layout L = p1_layout(N, nd.W, JC, false);
+    const int i = w.i, k = w.k, pp = w.pp, j0 = w.j0, jc = w.jc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    p1_shares<false>(L, N, i, k, pp, nd.fn, sm);
     __syncthreads();
-
-    // ---- split every class {(i,j),(k,nn),(p,qq)}, j in the chunk: one warp
-    // per nn, lanes over qq, each lane the JC classes of its (nn, qq).  Their
-    // members of kinds 4 and 6 are exactly the pieces (nn, qq) and (qq, nn),
-    // which move as one vector each.
     for (int nn = warp; nn < N; nn += kP1Warps) {
         const int *h4 = sm + L.H4 + nn * N, *h6 = sm + L.H6 + nn;
         for (int qq = lane; qq < N; qq += 32) {
@@ -380,11 +384,27 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
             store_piece<JC>(a6, p6);
         }
     }
+}
+
+// Write unit w back: whole rows by bulk stores (after the split's shared
+// writes are made visible to the async proxy), pieces by one tensor store
+// per kind or by vector stores; every thread commits its bulk stores as one
+// group.  The layout at sm stays in use until those groups have been read.
+template <int JC>
+__device__ __forceinline__ void p1_store(const P1Unit &w, int *sm)
+{
+    const NodeDesc &nd = *w.nd;
+    const int N = nd.N, W = nd.W, NN = N * N;
+    const FastDiv fN = nd.fN;
+    const P1Layout L = p1_layout(N, W, JC, false);
+    const size_t TS = (size_t)(N - 2) * W;
+    const int i = w.i, k = w.k, pp = w.pp, j0 = w.j0, jc = w.jc;
+    int *__restrict__ z = nd.p.z;
+    const bool tma = JC == 4 && nd.zmap_ok;
+    const void *zmap = &nd.zmap;
+    const unsigned rowBytes = (unsigned)W * 4u;
     fence_proxy_async_smem();
     __syncthreads();
-
-    // ---- write back: whole rows by bulk stores (after the split's shared
-    // writes are made visible to the async proxy), pieces by 16-byte stores
     for (int e = threadIdx.x; e < 4 * JC * N; e += kP1Threads) {
         const int qj = (int)fdiv((unsigned)e, fN), x = e - qj * N;
         const int q = qj / JC, jj = qj % JC, j = j0 + jj;
@@ -408,6 +428,35 @@ __global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant
         copy_piece<JC>(z + t * TS + (size_t)i * W + j0,
                        sm + (kind ? L.A6 : L.A4) + a * L.P46 + (l - (l > a)) * JC);
     }
+}
+
+// One CTA per unit of the group; yS holds c' (C plus the spread of B) per
+// tile.  The loads, the split and the stores of a CTA follow one another;
+// two CTAs per SM overlap them.
+template <int JC, bool ONE>
+__global__ void __launch_bounds__(kP1Threads, 2) p1_kernel(const __grid_constant__ Group g)
+{
+    if (blockIdx.x == 0 && threadIdx.x < 2) g.counter[threadIdx.x] = 0;  // work counters of the D -> C sweep
+    const P1Unit w = p1_unit<JC, ONE>(g, blockIdx.x);
+    if (!w.live) return;
+    extern __shared__ __align__(128) int sm[];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    p1_issue<JC, ONE>(g, w, sm, &bar);
+    cp_async_wait_all();
+    if (__syncthreads_or(!mbar_wait(&bar, 0))) {
+        // give up: record it, let the copies in flight land (bounded), leave
+        if (threadIdx.x == 0) atomicOr(&g.status->err, kDevTimeout);
+        mbar_wait(&bar, 0);
+        __syncthreads();
+        return;
+    }
+    p1_split<JC>(w, sm);
+    p1_store<JC>(w, sm);
     bulk_wait_read_all();  // shared memory stays valid until the bulk stores have read it
 }
 

@@ -2,7 +2,9 @@
 
 Branch-and-bound nodes and bound requests are independent units: rank r of
 W bounds units r, r+W, r+2W, ...; no collective touches the data path, and
-the per-unit results are gathered once at the end.
+the per-unit results are gathered once at the end.  Users: bound_nodes_sharded
+below (a batch of B&B nodes), bnb.BranchAndBound(group=...) (subtrees, with
+the incumbent exchanged between rounds) and serve.serve_sharded (requests).
 """
 from __future__ import annotations
 
@@ -29,3 +31,20 @@ def gather_results(local: List[Tuple[int, int]], total: int, group=None) -> List
     if any(v is None for v in out):
         raise RuntimeError("a unit was bounded by no rank")
     return out
+
+
+def bound_nodes_sharded(F, D, nodes, iters: int, group=None, **kw) -> List[int]:
+    """Bounds of B&B nodes (fac, loc) of one instance: this rank's share by
+    one rlt2_batch_bound call on its GPU, every node's bound gathered on every
+    rank in the original order.  kw: rlt2_batch_bound options."""
+    import torch.distributed as dist
+
+    from . import rlt2
+
+    mine = shard(nodes, dist.get_rank(group), dist.get_world_size(group))
+    local = []
+    if mine:
+        lbs, _ = rlt2.rlt2_batch_bound(F, D, [n for _, n in mine], iters, **kw)
+        local = [(i, int(v)) for (i, _), v in zip(mine, lbs)]
+    return gather_results(local, len(nodes), group)
+

@@ -185,3 +185,23 @@ class BoundServer:
             "mean_resident": self.slot_rounds / self.rounds if self.rounds else 0.0,
             "peak_bytes": self.peak_bytes, "rounds": self.rounds,
         }
+
+
+def serve_sharded(server: "BoundServer", requests: List[Request], group=None, realtime: bool = True) -> dict:
+    """One server per rank (one process per GPU): this rank serves its
+    round-robin share of `requests` (distributed.shard by position) with
+    `server`, and every request's result, (LB, error), is gathered on every
+    rank in the original order.  The requests are independent, so no
+    collective touches the bounding; the gather is the only exchange."""
+    import torch.distributed as dist
+
+    from .distributed import gather_results, shard
+
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    mine = shard(requests, rank, world)
+    stats = server.serve([r for _, r in mine], realtime=realtime)
+    local = [(i, (r.lb, r.error)) for i, r in mine]
+    results = gather_results(local, len(requests), group)
+    parts = [None] * world
+    dist.all_gather_object(parts, stats, group=group)
+    return {"results": results, "per_rank": parts, "ranks": world}

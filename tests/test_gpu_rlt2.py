@@ -406,6 +406,17 @@ def test_unknown_shapes_rejected(gpu):
     assert e.value.code == rlt2.RLT2_E_INVAL
 
 
+def test_group_rejects_a_context_twice(gpu):
+    """Two descriptors of one dual state would race in the same launches."""
+    F, D = I.uniform_symmetric(6, seed=1)
+    with rlt2.Context(F, D) as a, rlt2.Context(F, D) as b:
+        with pytest.raises(rlt2.Rlt2Error) as e:
+            rlt2.rlt2_group_create([a.ctx, b.ctx, a.ctx])
+        assert e.value.code == rlt2.RLT2_E_INVAL
+        g = rlt2.rlt2_group_create([a.ctx, b.ctx])
+        rlt2.rlt2_group_destroy(g)
+
+
 # ------------------------------------------------------------ pair store
 
 PAIRS = rlt2.RLT2_STORE_PAIRS
