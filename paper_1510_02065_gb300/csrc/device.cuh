@@ -284,14 +284,26 @@ __device__ __forceinline__ long long seg_sum64(long long x, unsigned mask)
 // latest when every column is labelled, and an augmenting path is at most as
 // long as the phase.  If an invariant fails (it cannot for entries in range)
 // the function stops and returns false instead of spinning.
-template <int NS, bool PACK, int SEG = 32>
+//
+// SENT (width <= 32 NS - 1): the last column slot, lane 31 of slot NS - 1,
+// holds no column and serves as a sentinel: never matched (its row stays -1),
+// its key above every key a column can have (PACK: the largest distance a
+// packed key allows; keys of real columns are below it or tie with a smaller
+// column) yet below a labelled column's.  A phase in which every real column
+// got labelled then also ends on a free column -- the sentinel -- so a step
+// tests only for a free column, and reaching the sentinel reports the
+// invariant failure.
+template <int NS, bool PACK, int SEG = 32, bool SENT = false>
 __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld, int n, int width,
                                                int dead0, int dead1, int (&rowOf)[NS],
                                                int (&uM)[NS], int (&v)[NS],
                                                unsigned &steps_out, unsigned &relax_out)
 {
     static_assert(SEG == 32 || (SEG == 16 && NS == 1), "a half-warp LAP has one column per lane");
+    static_assert(!SENT || SEG == 32, "the sentinel is lane 31 of a whole warp");
     constexpr unsigned kDone = 0x80000000u;  // key of a labelled (or absent) column
+    constexpr int kSentCol = 32 * NS - 1;
+    constexpr unsigned kSentKey = PACK ? ((((1u << 25) - 1u) << 6) | (unsigned)kSentCol) : 0x7fffffffu;
     const Seg<SEG> g;
     const int lane = g.sl;  // the lane's place in its segment
     bool valid[NS];
@@ -318,6 +330,9 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
         // labels a new column or ends the phase: at most n + 1 steps.
 #pragma unroll
         for (int s = 0; s < NS; ++s) key[s] = valid[s] ? 0x7fffffffu : kDone;
+        if constexpr (SENT) {
+            if (lane == 31) key[NS - 1] = kSentKey;
+        }
         int i0 = r;   // row scanned at this step
         int j0 = -1;  // column through which i0 was reached (-1: the new row)
         int c0 = 0;   // u(i0) - D before this step
@@ -356,7 +371,11 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
             const int src = j1 & 31, sl = j1 >> 5;
             const int rj = __shfl_sync(g.mask, pick<NS>(rowOf, sl), g.base + src);
             const int uj = __shfl_sync(g.mask, pick<NS>(uM, sl), g.base + src);
-            if (rj < 0 || mm == kDone) break;  // free column: augmenting path found
+            if constexpr (SENT) {
+                if (rj < 0) break;  // free column (or the sentinel): augmenting path found
+            } else {
+                if (rj < 0 || mm == kDone) break;  // free column: augmenting path found
+            }
             if (lane == src) {
                 put<NS>(key, sl, kDone);
                 put<NS>(dlab, sl, Dk);
@@ -365,7 +384,7 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
             j0 = j1;
             c0 = uj - Dk;
         }
-        if (mm == kDone) return false;  // every column labelled: cannot happen
+        if (SENT ? j1 == kSentCol : mm == kDone) return false;  // every column labelled: cannot happen
         const int jf = j1, Dend = Dk;
 
         // lazy potential updates of the columns labelled in this phase

@@ -231,7 +231,7 @@ cudaError_t launch_dlap(const Group &g, int sm_count, cudaStream_t s, const Side
 struct DlapRange {
     long long lo, hi;
     unsigned *counter;
-    int tsp, maxW, lanes, warps;
+    int tsp, maxW, maxN, lanes, warps;
 };
 // One of the group's two D->C ranges (0: the units from small_tiles on, 1:
 // the small instances' units) in its shape g.dshape[which].

@@ -21,6 +21,14 @@
 
 namespace rlt2 {
 
+// D->C LAPs with one column slot per lane use the Hungarian's sentinel column
+// (a build can turn it off for comparison with -DRLT2_NO_SENTINEL)
+#ifdef RLT2_NO_SENTINEL
+constexpr bool kSentinel = false;
+#else
+constexpr bool kSentinel = true;
+#endif
+
 constexpr int kClapWarps = 4;
 constexpr int kDlap16Warps = 4;
 constexpr int kXlapWarps = 4;
@@ -76,7 +84,8 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
     }
     const int nl = nn + (nn >= j);
     int rowOf[NS], uM[NS], v[NS];
-    if (!warp_hungarian<NS, PACK, SEG>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
+    if (!warp_hungarian<NS, PACK, SEG, kSentinel && SEG == 32 && NS == 1>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) &&
+        lane == 0)
         atomicOr(&status->err, kDevInternal);
     // u of every row goes to the row's column j, which holds no coefficient
     scatter_rows<NS, SEG>(n, N, j, nl, rowOf, uM, buf + j, nullptr, W);
@@ -165,7 +174,8 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
     }
     __syncwarp(sg.mask);
     int rowOf[NS], uM[NS], v[NS];
-    if (!warp_hungarian<NS, PACK, SEG>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) && lane == 0)
+    if (!warp_hungarian<NS, PACK, SEG, kSentinel && SEG == 32 && NS == 1>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) &&
+        lane == 0)
         atomicOr(&status->err, kDevInternal);
     scatter_rows<NS, SEG>(n, N, j, nl, rowOf, uM, buf + j, nullptr, W);  // u to the free column j
     __syncwarp(sg.mask);
@@ -589,10 +599,12 @@ static cudaError_t dlap_go(const Group &g, const DlapRange &rg, int sm_count, cu
     return cudaErrorInvalidValue;
 }
 
+// One column slot per lane (with the sentinel column in lane 31) up to N = 31,
+// two from N = 32.
 template <bool ONE, int MODE>
 static cudaError_t dlap_pick(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
 {
-    if (rg.maxW <= 32)
+    if (rg.maxN <= 31)
         return g.pack ? dlap_go<1, true, ONE, MODE>(g, rg, sm_count, s) : dlap_go<1, false, ONE, MODE>(g, rg, sm_count, s);
     return g.pack ? dlap_go<2, true, ONE, MODE>(g, rg, sm_count, s) : dlap_go<2, false, ONE, MODE>(g, rg, sm_count, s);
 }
@@ -644,12 +656,14 @@ static DlapRange dlap_range(const Group &g, int which)
         rg.counter = g.counter;
         rg.tsp = g.maxTS;
         rg.maxW = (g.maxN + 3) & ~3;
+        rg.maxN = g.maxN;
     } else {
         rg.lo = 0;
         rg.hi = g.small_tiles;
         rg.counter = g.counter + 1;
         rg.tsp = g.smallTS;
         rg.maxW = g.smallW;
+        rg.maxN = g.smallW;   // N <= W <= 16
     }
     rg.lanes = g.dshape[which].lanes;
     rg.warps = g.dshape[which].warps;
@@ -667,7 +681,7 @@ int dlap_cta_warps(const Group &g, int which)
     cudaError_t e = cudaSuccess;
     // (occupancy of the tile-store, one-instance kernel: the other forms use
     // as many registers and the same shared memory, so they choose alike)
-    if (rg.maxW <= 32) {
+    if (rg.maxN <= 31) {
         if (g.pack) {
             e = dlap_fit<1, true, true, 0, 4>(rg, w4);
             if (e == cudaSuccess) e = dlap_fit<1, true, true, 0, 16>(rg, w16);
