@@ -368,7 +368,9 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
                     j1 = b0 ? __ffs(b0) - 1 : 31 + __ffs(b1);
                 }
             }
-            const int src = j1 & 31, sl = j1 >> 5;
+            // one slot per lane on a whole warp: j1 < 32 is the lane itself
+            constexpr bool kOne = NS == 1 && SEG == 32;
+            const int src = kOne ? j1 : j1 & 31, sl = kOne ? 0 : j1 >> 5;
             const int rj = __shfl_sync(g.mask, pick<NS>(rowOf, sl), g.base + src);
             const int uj = __shfl_sync(g.mask, pick<NS>(uM, sl), g.base + src);
             if constexpr (SENT) {
@@ -403,13 +405,16 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
         sumK2 += K * K;
 
         // augment: each column on the path takes the row of its predecessor
+        // (one slot per lane on a whole warp: columns are lanes, and a shuffle
+        // from lane -1 reads lane 31, whose values a predecessor -1 ignores)
+        constexpr bool kOne = NS == 1 && SEG == 32;
         int c = jf;
         for (int hop = 0;; ++hop) {
             if (hop > K) return false;
-            const int cs = c >> 5, cl = c & 31;
+            const int cs = kOne ? 0 : c >> 5, cl = kOne ? c : c & 31;
             const int w = __shfl_sync(g.mask, pick<NS>(way, cs), g.base + cl);
             int nr = r, nu = Dend;
-            const int ws = (w < 0 ? 0 : w) >> 5, wl = (w < 0 ? 0 : w) & 31;
+            const int ws = kOne ? 0 : (w < 0 ? 0 : w) >> 5, wl = kOne ? w : (w < 0 ? 0 : w) & 31;
             const int pr = __shfl_sync(g.mask, pick<NS>(rowOf, ws), g.base + wl);
             const int pu = __shfl_sync(g.mask, pick<NS>(uM, ws), g.base + wl);
             if (w >= 0) {
