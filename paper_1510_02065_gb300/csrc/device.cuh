@@ -301,18 +301,27 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
 {
     static_assert(SEG == 32 || (SEG == 16 && NS == 1), "a half-warp LAP has one column per lane");
     static_assert(!SENT || SEG == 32, "the sentinel is lane 31 of a whole warp");
-    constexpr unsigned kDone = 0x80000000u;  // key of a labelled (or absent) column
+    // A labelled column's key is kDone = INT_MIN: as a signed value no
+    // candidate is below it, so no relaxation touches it (whatever the data),
+    // and as an unsigned value it is above every unlabelled key, so no
+    // reduction picks it while an unlabelled column remains.  Each step
+    // therefore labels a new column or ends the phase: at most n + 1 steps.
+    // A column outside the LAP has key kNone (never relaxed, never picked
+    // before kDone, told apart from a labelled column).
+    constexpr unsigned kDone = 0x80000000u;  // key of a labelled column
+    constexpr unsigned kNone = 0xffffffffu;  // key of a column outside the LAP
     constexpr int kSentCol = 32 * NS - 1;
     constexpr unsigned kSentKey = PACK ? ((((1u << 25) - 1u) << 6) | (unsigned)kSentCol) : 0x7fffffffu;
     const Seg<SEG> g;
     const int lane = g.sl;  // the lane's place in its segment
     bool valid[NS];
     int way[NS], dlab[NS];
-    unsigned key[NS];
+    unsigned key[NS], key0[NS];  // key0: the key a column starts every row with
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const int c = lane + 32 * s;
         valid[s] = c < width && c != dead0 && c != dead1;
+        key0[s] = valid[s] ? 0x7fffffffu : (SENT && c == kSentCol) ? kSentKey : kNone;
         rowOf[s] = -1;
         uM[s] = 0;
         v[s] = 0;
@@ -323,16 +332,9 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
 
     for (int r = 0; r < n; ++r) {
         // key = distance label (+ D of its last update), packed with the column
-        // when PACK; kDone = INT_MIN marks labelled columns: as a signed value no
-        // candidate is below it, so no relaxation touches it (whatever the data),
-        // and as an unsigned value it is above every valid key, so no reduction
-        // picks it while an unlabelled column remains.  Each step therefore
-        // labels a new column or ends the phase: at most n + 1 steps.
+        // when PACK
 #pragma unroll
-        for (int s = 0; s < NS; ++s) key[s] = valid[s] ? 0x7fffffffu : kDone;
-        if constexpr (SENT) {
-            if (lane == 31) key[NS - 1] = kSentKey;
-        }
+        for (int s = 0; s < NS; ++s) key[s] = key0[s];
         int i0 = r;   // row scanned at this step
         int j0 = -1;  // column through which i0 was reached (-1: the new row)
         int c0 = 0;   // u(i0) - D before this step
@@ -393,7 +395,7 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
         int K = 1;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const bool lab = valid[s] && key[s] == kDone;
+            const bool lab = key[s] == kDone;
             K += __popc(__ballot_sync(g.mask, lab));
             if (lab) {
                 const int dd = Dend - dlab[s];
