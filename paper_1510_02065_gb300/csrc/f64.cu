@@ -142,7 +142,8 @@ __device__ bool hungarian_f64(const double *M, int ld, int n, int width, int dea
             }
             next = warp_argmin(best, bc);
             if (next == INT_MAX) return false;
-            const int src = next & 31, sl = next >> 5;
+            // one slot per lane: the column is the lane itself
+            const int src = NS == 1 ? next : next & 31, sl = NS == 1 ? 0 : next >> 5;
             const double delta = __shfl_sync(kFull, pick<NS>(dist, sl), src);
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
@@ -170,9 +171,11 @@ __device__ bool hungarian_f64(const double *M, int ld, int n, int width, int dea
         int c = next;
         for (int hop = 0;; ++hop) {
             if (hop > n) return false;
-            const int cs = c >> 5, cl = c & 31;
+            // (one slot per lane: columns are lanes; a shuffle from lane -1
+            // reads lane 31, whose values a predecessor -1 ignores)
+            const int cs = NS == 1 ? 0 : c >> 5, cl = NS == 1 ? c : c & 31;
             const int w = __shfl_sync(kFull, pick<NS>(way, cs), cl);
-            const int ws = (w < 0 ? 0 : w) >> 5, wl = (w < 0 ? 0 : w) & 31;
+            const int ws = NS == 1 ? 0 : (w < 0 ? 0 : w) >> 5, wl = NS == 1 ? w : (w < 0 ? 0 : w) & 31;
             const int pr = __shfl_sync(kFull, pick<NS>(rowOf, ws), wl);
             const double pu = __shfl_sync(kFull, pick<NS>(uM, ws), wl);
             if (lane == cl) {
