@@ -35,12 +35,12 @@ ALU_LANES_PER_SM = 64    # integer ALU pipe: 16 lanes per scheduler, 4 scheduler
 # DRAM bytes per launch of the D->C and fused-pass kernels on the 30-facility
 # workload (tile store), from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum;
 # reported only while the kernel's sources hash to the captured version.
-DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2716721920 + 2655284992,
+DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2715261952 + 2655528448,
                 "files": ("lap_kernels.cu", "device.cuh", "kernels.h"),
-                "sources_sha1": "2c8556334b31e2a46bbbbe0f70541f03e65a5bba"}
-P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2740582400 + 2655439360,
+                "sources_sha1": "7749aca6aad028f2d3a29eafdba0c72a6418fd69"}
+P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2740663552 + 2655432704,
               "files": ("sweep_kernels.cu", "device.cuh", "kernels.h"),
-              "sources_sha1": "159813edd0e0411e888f7d6a89890f38e6336e25"}
+              "sources_sha1": "f34c97e3f759ec7ffd746f3ca5b4785b39f1fd9e"}
 
 
 def captured_traffic(rec, workload, store):
