@@ -332,7 +332,7 @@ def batch_sharded_measure(rlt2, instances, torch, dist, nodes_count, iters):
     dist.barrier()
     t0 = time.perf_counter()
     lbs = distributed.bound_nodes_sharded(F, D, nodes, iters)
-    t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64)
+    t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")   # NCCL: device tensors
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return {"metric": "batched B&B nodes/sec, nodes sharded over the ranks", "unit": "nodes/s",
             "value": nodes_count / float(t.item()), "nodes": nodes_count, "iters": iters,

@@ -280,7 +280,9 @@ class BranchAndBound:
         for k in self.stats:
             self.stats[k] = 0      # the search below counts this rank's own work
         local = 0
-        buf = torch.zeros(2, dtype=torch.int64)
+        # the incumbent exchange: NCCL reduces device tensors, gloo host ones
+        dev = "cuda" if dist.get_backend(self.group) == "nccl" else "cpu"
+        buf = torch.zeros(2, dtype=torch.int64, device=dev)
         while True:
             n = 0
             while stack and n < self.sync_every and visited + local < self.node_limit:
