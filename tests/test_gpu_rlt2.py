@@ -393,6 +393,27 @@ def test_dlap_shapes_agree_at_size(gpu, store):
         assert got[-1] == ref[-1], kw
 
 
+def test_tuned_shape_is_remembered(gpu):
+    """A context tunes its D->C shape on its first passes and reports it; a
+    later context of the same store and row width starts in that shape with
+    no tuning passes; a forced shape never tunes."""
+    F, D = I.clustered_euclid(19, seed=2)          # W = 20: a width no other test of this module tunes
+    with rlt2.Context(F, D, store=rlt2.RLT2_STORE_PAIRS) as a:
+        first = a.dlap_shape()
+        passes = 0
+        while a.dlap_shape()[2] and passes < 8:
+            a.iterate(1)
+            passes += 1
+        assert not a.dlap_shape()[2] and passes <= 6
+        tuned = a.dlap_shape()
+    F2, D2 = I.clustered_euclid(18, seed=3)        # N = 18: the same row width
+    with rlt2.Context(F2, D2, store=rlt2.RLT2_STORE_PAIRS) as b:
+        assert b.dlap_shape() == tuned
+    with rlt2.Context(F2, D2, store=rlt2.RLT2_STORE_PAIRS, lanes=32, cta_warps=16) as c:
+        assert c.dlap_shape() == (32, 16, False)
+    assert first[2] or first == tuned
+
+
 def test_unknown_shapes_rejected(gpu):
     F, D = I.uniform_symmetric(6, seed=1)
     for kw in (dict(lanes=8), dict(lanes=12), dict(cta_warps=5), dict(cta_warps=-1),
