@@ -214,13 +214,6 @@ __device__ __forceinline__ void decode_tile(const F64Dev &d, long long t, int &i
     n = nn + (nn >= j);
 }
 
-__device__ __forceinline__ size_t zaddr(const F64Dev &d, int i, int j, int k, int n, int p, int q)
-{
-    const long long t = ((long long)(i * d.N + j) * d.m + (k - (k > i))) * d.m + (n - (n > j));
-    const int r = p - (p > i) - (p > k);
-    return (size_t)t * d.TS + (size_t)r * d.N + q;
-}
-
 __global__ void f64_init_kernel(F64Dev d)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < d.tiles;

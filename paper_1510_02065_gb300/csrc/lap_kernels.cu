@@ -201,8 +201,20 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
 // parameter space, and the stopping rule is checked once.  Every CTA size
 // caps registers at 32 per thread (64 warps per SM).
 // MODE: 0 tile store, 1 class-sum store, 2 pair store (work units: its tiles).
+// Resident warps per SM each D->C form is compiled for, i.e. its register
+// budget (65536 / 32 / warps).  A group of one reads its instance from kernel
+// parameters and fits 32 registers (64 warps).  A larger group holds its
+// instances' fields in registers: with the tile or pair store and one column
+// slot per lane it would take 38-43 and spills 32-48 bytes per thread at 32,
+// which measured faster at 64 warps than 48 warps without spills (C4 batch:
+// 28.0 vs 27.5 nodes/s); with the class-sum store's gather or two column
+// slots per lane it takes up to 64 and spilled 64-184 bytes, so those forms
+// get 64 registers (32 warps).
+template <int NS, bool ONE, int MODE>
+constexpr int kDlapWarpsPerSM = ONE ? 64 : (MODE == 1 || NS == 2) ? 32 : 64;
+
 template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 64 / WARPS)
+__global__ void __launch_bounds__(WARPS * 32, kDlapWarpsPerSM<NS, ONE, MODE> / WARPS)
     dlap_kernel(Group g, long long lo, long long hi, unsigned *counter, int tsp)
 {
     constexpr bool SYM = MODE == 1, PAIR = MODE == 2;
@@ -264,8 +276,10 @@ __global__ void __launch_bounds__(WARPS * 32, 64 / WARPS)
 // from its own counter): two per warp, one per half-warp (LAPs of width <= 16
 // on 16 lanes).  Two buffers of tsp ints and two mbarriers per warp; half h
 // always uses buffer and barrier h.
+// (register budget as above: 39-44 registers with the tile store, more than
+// 64 with the class-sum store)
 template <bool PACK, bool ONE, bool SYM>
-__global__ void __launch_bounds__(kDlap16Warps * 32, 64 / kDlap16Warps)
+__global__ void __launch_bounds__(kDlap16Warps * 32, (SYM ? 24 : 40) / kDlap16Warps)
     dlap16_kernel(Group g, long long lo, long long hi, unsigned *counter, int tsp)
 {
     if (ONE && *g.first.p.stop) return;
@@ -582,8 +596,10 @@ static cudaError_t dlap_run(const Group &g, const DlapRange &rg, int sm_count, c
 // CTA size: rg.warps (4, 16 or 32) when given, else the one of those that
 // keeps the most warps resident (shared memory decides: at N = 30 two CTAs of
 // 32 warps fit where fourteen of 4 do), the smaller on a tie.
+// chosen != null: report the CTA size in *chosen and launch nothing.
 template <int NS, bool PACK, bool ONE, int MODE>
-static cudaError_t dlap_go(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
+static cudaError_t dlap_go(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s,
+                           int *chosen = nullptr)
 {
     int w4 = 0, w16 = 0, w32 = 0;
     cudaError_t e;
@@ -593,6 +609,10 @@ static cudaError_t dlap_go(const Group &g, const DlapRange &rg, int sm_count, cu
     int w = rg.warps;
     if (w == 0) w = (w32 > w4 && w32 > w16) ? 32 : w16 > w4 ? 16 : 4;
     if ((w == 4 && !w4) || (w == 16 && !w16) || (w == 32 && !w32)) return cudaErrorInvalidConfiguration;
+    if (chosen) {
+        *chosen = w;
+        return cudaSuccess;
+    }
     if (w == 32) return dlap_run<NS, PACK, ONE, MODE, 32>(g, rg, sm_count, s);
     if (w == 16) return dlap_run<NS, PACK, ONE, MODE, 16>(g, rg, sm_count, s);
     if (w == 4) return dlap_run<NS, PACK, ONE, MODE, 4>(g, rg, sm_count, s);
@@ -602,18 +622,23 @@ static cudaError_t dlap_go(const Group &g, const DlapRange &rg, int sm_count, cu
 // One column slot per lane (with the sentinel column in lane 31) up to N = 31,
 // two from N = 32.
 template <bool ONE, int MODE>
-static cudaError_t dlap_pick(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
+static cudaError_t dlap_pick(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s, int *chosen)
 {
     if (rg.maxN <= 31)
-        return g.pack ? dlap_go<1, true, ONE, MODE>(g, rg, sm_count, s) : dlap_go<1, false, ONE, MODE>(g, rg, sm_count, s);
-    return g.pack ? dlap_go<2, true, ONE, MODE>(g, rg, sm_count, s) : dlap_go<2, false, ONE, MODE>(g, rg, sm_count, s);
+        return g.pack ? dlap_go<1, true, ONE, MODE>(g, rg, sm_count, s, chosen)
+                      : dlap_go<1, false, ONE, MODE>(g, rg, sm_count, s, chosen);
+    return g.pack ? dlap_go<2, true, ONE, MODE>(g, rg, sm_count, s, chosen)
+                  : dlap_go<2, false, ONE, MODE>(g, rg, sm_count, s, chosen);
 }
 
-static cudaError_t dlap_warp(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s)
+static cudaError_t dlap_warp(const Group &g, const DlapRange &rg, int sm_count, cudaStream_t s,
+                             int *chosen = nullptr)
 {
-    if (g.sym) return g.B == 1 ? dlap_pick<true, 1>(g, rg, sm_count, s) : dlap_pick<false, 1>(g, rg, sm_count, s);
-    if (g.paired) return g.B == 1 ? dlap_pick<true, 2>(g, rg, sm_count, s) : dlap_pick<false, 2>(g, rg, sm_count, s);
-    return g.B == 1 ? dlap_pick<true, 0>(g, rg, sm_count, s) : dlap_pick<false, 0>(g, rg, sm_count, s);
+    if (g.sym)
+        return g.B == 1 ? dlap_pick<true, 1>(g, rg, sm_count, s, chosen) : dlap_pick<false, 1>(g, rg, sm_count, s, chosen);
+    if (g.paired)
+        return g.B == 1 ? dlap_pick<true, 2>(g, rg, sm_count, s, chosen) : dlap_pick<false, 2>(g, rg, sm_count, s, chosen);
+    return g.B == 1 ? dlap_pick<true, 0>(g, rg, sm_count, s, chosen) : dlap_pick<false, 0>(g, rg, sm_count, s, chosen);
 }
 
 template <bool PACK, bool ONE, bool SYM>
@@ -675,29 +700,8 @@ int dlap_cta_warps(const Group &g, int which)
     const DlapRange rg = dlap_range(g, which);
     if (rg.hi <= rg.lo) return 0;
     if (rg.lanes == 16) return kDlap16Warps;
-    if (rg.warps) return rg.warps;
-    // the choice of dlap_go: most warps resident, the smaller CTA on a tie
-    int w4 = 0, w16 = 0, w32 = 0;
-    cudaError_t e = cudaSuccess;
-    // (occupancy of the tile-store, one-instance kernel: the other forms use
-    // as many registers and the same shared memory, so they choose alike)
-    if (rg.maxN <= 31) {
-        if (g.pack) {
-            e = dlap_fit<1, true, true, 0, 4>(rg, w4);
-            if (e == cudaSuccess) e = dlap_fit<1, true, true, 0, 16>(rg, w16);
-            if (e == cudaSuccess) e = dlap_fit<1, true, true, 0, 32>(rg, w32);
-        } else {
-            e = dlap_fit<1, false, true, 0, 4>(rg, w4);
-            if (e == cudaSuccess) e = dlap_fit<1, false, true, 0, 16>(rg, w16);
-            if (e == cudaSuccess) e = dlap_fit<1, false, true, 0, 32>(rg, w32);
-        }
-    } else {
-        e = dlap_fit<2, true, true, 0, 4>(rg, w4);
-        if (e == cudaSuccess) e = dlap_fit<2, true, true, 0, 16>(rg, w16);
-        if (e == cudaSuccess) e = dlap_fit<2, true, true, 0, 32>(rg, w32);
-    }
-    if (e != cudaSuccess) return 0;
-    return (w32 > w4 && w32 > w16) ? 32 : w16 > w4 ? 16 : 4;
+    int w = 0;
+    return dlap_warp(g, rg, 0, nullptr, &w) == cudaSuccess ? w : 0;
 }
 
 cudaError_t launch_dlap_range(const Group &g, int which, int sm_count, cudaStream_t s)
