@@ -35,9 +35,9 @@ ALU_LANES_PER_SM = 64    # integer ALU pipe: 16 lanes per scheduler, 4 scheduler
 # DRAM bytes per launch of the D->C and fused-pass kernels on the 30-facility
 # workload (tile store), from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum;
 # reported only while the kernel's sources hash to the captured version.
-DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2715261952 + 2655528448,
+DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2715341056 + 2655610624,
                 "files": ("lap_kernels.cu", "device.cuh", "kernels.h"),
-                "sources_sha1": "7749aca6aad028f2d3a29eafdba0c72a6418fd69"}
+                "sources_sha1": "4c7393575b79e41eba006b5892d21f5ebc28478e"}
 P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2740663552 + 2655432704,
               "files": ("sweep_kernels.cu", "device.cuh", "kernels.h"),
               "sources_sha1": "f34c97e3f759ec7ffd746f3ca5b4785b39f1fd9e"}
@@ -146,8 +146,8 @@ def n35_measure(rlt2, instances, torch, steps, store, warmup=3, workload="cluste
 # DRAM bytes of one f64_dlap_kernel launch at N=20 (one ncu capture of the DRAM byte counters)
 # per tile coefficient read (n x N per tile) and written (n x n), valid while
 # the FP64 sources hash to the captured version; other sizes scale by those units
-F64_DLAP_TRAFFIC = {"N": 20, "read": 417017088, "write": 357810944, "files": ("f64.cu", "device.cuh"),
-                    "sources_sha1": "8386bb3a69222410c58725a5b5420cf0dcb2ae86"}
+F64_DLAP_TRAFFIC = {"N": 20, "read": 417197568, "write": 358193408, "files": ("f64.cu", "device.cuh"),
+                    "sources_sha1": "91bf6c61e0f3d040e73651a652d8da11a1a2e0ef"}
 
 
 def f64_traffic(N):
