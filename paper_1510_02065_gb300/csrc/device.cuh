@@ -293,6 +293,100 @@ __device__ __forceinline__ long long seg_sum64(long long x, unsigned mask)
 // got labelled then also ends on a free column -- the sentinel -- so a step
 // tests only for a free column, and reaching the sentinel reports the
 // invariant failure.
+//
+// One column per lane of a whole warp with packed keys and the sentinel
+// (NS = 1, SEG = 32, PACK, SENT) goes to warp_hungarian_lane: the same method
+// in a representation that takes fewer instructions per step.
+//
+// warp_hungarian_lane: lane c owns column c (width <= 31, lane 31 the
+// sentinel).  Each lane keeps two words, both modulo 2^32:
+//   ruM = 64 uM + rowOf + 1   (its matched row and that row's potential)
+//   wv  = lane - 64 v         (its column potential)
+// A relaxation forms the packed key 64 x + wv - q = 64 (x - v - c0) + lane
+// directly (q = 64 c0), which is, modulo 2^32, the value the general form gets
+// by shifting the candidate, so every comparison and every result is the
+// same.  The winning column's lane hands over the next row and offset in one
+// word, z = ruM - key + lane = 64 (uM - Dk) + rowOf + 1: its low six bits are
+// the row + 1 (0: a free column, the augmenting path's end), the rest is q.
+// A labelled column keeps its key of labelling in dlab (64 Dk + column), and
+// the lazy updates move ruM and wv by 64 (Dend - Dk); augmenting moves one
+// word per column.
+__device__ __forceinline__ bool warp_hungarian_lane(const int *__restrict__ M, int ld, int n, int width,
+                                                    int dead0, int dead1, int &rowOf_out, int &uM_out,
+                                                    int &v_out, unsigned &steps_out, unsigned &relax_out)
+{
+    constexpr unsigned kDone = 0x80000000u;  // key of a labelled column
+    constexpr unsigned kNone = 0xffffffffu;  // key of a column outside the LAP
+    constexpr unsigned kSentKey = (((1u << 25) - 1u) << 6) | 31u;
+    const int lane = threadIdx.x & 31;
+    const bool valid = lane < width && lane != dead0 && lane != dead1;
+    const unsigned key0 = valid ? 0x7fffffffu : lane == 31 ? kSentKey : kNone;
+    unsigned ruM = 0u, wv = (unsigned)lane, dlab = 0u;
+    int way = -1;  // packed key of the column through which the column was reached (-1: the new row)
+    int sumK = 0, sumK2 = 0;
+    const int off = lane - ld;  // row i at M + (i + 1) * ld + off
+
+    for (int r = 0; r < n; ++r) {
+        unsigned key = key0, r1 = (unsigned)r + 1u, q = 0u, mm;
+        int j0 = -1;
+        for (;;) {
+            const int x = M[(int)r1 * ld + off];
+            if (valid) {
+                const unsigned ck = (unsigned)x * 64u + (wv - q);
+                if ((int)ck < (int)key) {
+                    key = ck;
+                    way = j0;
+                }
+            }
+            const unsigned z = ruM - key + (unsigned)lane;
+            mm = __reduce_min_sync(kFull, key);
+            const unsigned zw = __shfl_sync(kFull, z, (int)mm);  // from the lane of column mm % 64 (< 32)
+            r1 = zw & 63u;
+            if (r1 == 0u) break;  // free column (or the sentinel): augmenting path found
+            if (key == mm) {
+                dlab = key;
+                key = kDone;
+            }
+            q = zw & ~63u;
+            j0 = (int)mm;
+        }
+        const int jf = (int)(mm & 63u);
+        if (jf == 31) return false;  // the sentinel: every column labelled, cannot happen
+        const unsigned Dend6 = mm & ~63u;
+
+        // lazy potential updates of the columns labelled in this phase
+        const bool lab = key == kDone;
+        const int K = 1 + __popc(__ballot_sync(kFull, lab));
+        if (lab) {
+            const unsigned dd = Dend6 - (dlab & ~63u);
+            wv += dd;
+            ruM += dd;
+        }
+        sumK += K;
+        sumK2 += K * K;
+
+        // augment: each column on the path takes the row (and its potential)
+        // of its predecessor, the first one the new row with u = Dend (a
+        // shuffle from lane -1 reads lane 31, whose word a predecessor -1 ignores)
+        const unsigned root = Dend6 + (unsigned)r + 1u;
+        int c = jf;
+        for (int hop = 0;; ++hop) {
+            if (hop > K) return false;
+            const int w = __shfl_sync(kFull, way, c);
+            const unsigned p = __shfl_sync(kFull, ruM, w);
+            if (lane == c) ruM = w >= 0 ? p : root;
+            if (w < 0) break;
+            c = w & 63;
+        }
+    }
+    rowOf_out = (int)(ruM & 63u) - 1;
+    uM_out = (int)(ruM & ~63u) >> 6;
+    v_out = (int)((unsigned)lane - wv) >> 6;
+    steps_out += (unsigned)sumK;
+    relax_out += (unsigned)(n * sumK - (sumK2 - sumK) / 2);
+    return true;
+}
+
 template <int NS, bool PACK, int SEG = 32, bool SENT = false>
 __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld, int n, int width,
                                                int dead0, int dead1, int (&rowOf)[NS],
@@ -301,6 +395,8 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
 {
     static_assert(SEG == 32 || (SEG == 16 && NS == 1), "a half-warp LAP has one column per lane");
     static_assert(!SENT || SEG == 32, "the sentinel is lane 31 of a whole warp");
+    if constexpr (NS == 1 && SEG == 32 && PACK && SENT)
+        return warp_hungarian_lane(M, ld, n, width, dead0, dead1, rowOf[0], uM[0], v[0], steps_out, relax_out);
     // A labelled column's key is kDone = INT_MIN: as a signed value no
     // candidate is below it, so no relaxation touches it (whatever the data),
     // and as an unsigned value it is above every unlabelled key, so no
