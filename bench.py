@@ -35,12 +35,12 @@ ALU_LANES_PER_SM = 64    # integer ALU pipe: 16 lanes per scheduler, 4 scheduler
 # DRAM bytes per launch of the D->C and fused-pass kernels on the 30-facility
 # workload (tile store), from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum;
 # reported only while the kernel's sources hash to the captured version.
-DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2715341056 + 2655610624,
+DLAP_TRAFFIC = {"workload": "clustered_n30", "bytes": 2713529600 + 2654458624,
                 "files": ("lap_kernels.cu", "device.cuh", "kernels.h"),
-                "sources_sha1": "4c7393575b79e41eba006b5892d21f5ebc28478e"}
-P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2740663552 + 2655432704,
+                "sources_sha1": "eed19020147e72a9c5d3269774b4da331ab575e7"}
+P1_TRAFFIC = {"workload": "clustered_n30", "bytes": 2741044736 + 2655430400,
               "files": ("sweep_kernels.cu", "device.cuh", "kernels.h"),
-              "sources_sha1": "f34c97e3f759ec7ffd746f3ca5b4785b39f1fd9e"}
+              "sources_sha1": "7effb6ceb3bb7a07c31ea1e7936c36abb2fcd5ea"}
 
 
 def captured_traffic(rec, workload, store):
@@ -146,8 +146,8 @@ def n35_measure(rlt2, instances, torch, steps, store, warmup=3, workload="cluste
 # DRAM bytes of one f64_dlap_kernel launch at N=20 (one ncu capture of the DRAM byte counters)
 # per tile coefficient read (n x N per tile) and written (n x n), valid while
 # the FP64 sources hash to the captured version; other sizes scale by those units
-F64_DLAP_TRAFFIC = {"N": 20, "read": 417197568, "write": 358193408, "files": ("f64.cu", "device.cuh"),
-                    "sources_sha1": "91bf6c61e0f3d040e73651a652d8da11a1a2e0ef"}
+F64_DLAP_TRAFFIC = {"N": 20, "read": 417091840, "write": 358182400, "files": ("f64.cu", "device.cuh"),
+                    "sources_sha1": "852ad019743ca0a1dda6930a9a37adf640d44899"}
 
 
 def f64_traffic(N):

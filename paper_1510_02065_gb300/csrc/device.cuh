@@ -285,7 +285,9 @@ __device__ __forceinline__ long long seg_sum64(long long x, unsigned mask)
 // long as the phase.  If an invariant fails (it cannot for entries in range)
 // the function stops and returns false instead of spinning.
 //
-// SENT (width <= 32 NS - 1): the last column slot, lane 31 of slot NS - 1,
+// SENT: with packed keys (PACK) on a whole warp, see warp_hungarian_lane
+// below (dead0 must be a column < width).  Otherwise (width <= 32 NS - 1) the
+// last column slot, lane 31 of slot NS - 1,
 // holds no column and serves as a sentinel: never matched (its row stays -1),
 // its key above every key a column can have (PACK: the largest distance a
 // packed key allows; keys of real columns are below it or tie with a smaller
@@ -294,73 +296,114 @@ __device__ __forceinline__ long long seg_sum64(long long x, unsigned mask)
 // tests only for a free column, and reaching the sentinel reports the
 // invariant failure.
 //
-// One column per lane of a whole warp with packed keys and the sentinel
-// (NS = 1, SEG = 32, PACK, SENT) goes to warp_hungarian_lane: the same method
-// in a representation that takes fewer instructions per step.
+// A whole warp with packed keys and a sentinel (SEG = 32, PACK, SENT) goes to
+// warp_hungarian_lane: the same method in a representation that takes fewer
+// instructions per step, with the LAP's dead column dead0 as its sentinel.
 //
-// warp_hungarian_lane: lane c owns column c (width <= 31, lane 31 the
-// sentinel).  Each lane keeps two words, both modulo 2^32:
+// warp_hungarian_lane: lane c % 32, slot c / 32 owns column c.  Each column
+// keeps two words, both modulo 2^32:
 //   ruM = 64 uM + rowOf + 1   (its matched row and that row's potential)
-//   wv  = lane - 64 v         (its column potential)
-// A relaxation forms the packed key 64 x + wv - q = 64 (x - v - c0) + lane
-// directly (q = 64 c0), which is, modulo 2^32, the value the general form gets
-// by shifting the candidate, so every comparison and every result is the
+//   wv  = c - 64 v            (its potential)
+// A relaxation forms the packed key 64 x + wv - q = 64 (x - v - c0) + c
+// directly (q = 64 c0), which is, modulo 2^32, the value the general form
+// gets by shifting the candidate, so every comparison and every result is the
 // same.  The winning column's lane hands over the next row and offset in one
-// word, z = ruM - key + lane = 64 (uM - Dk) + rowOf + 1: its low six bits are
-// the row + 1 (0: a free column, the augmenting path's end), the rest is q.
-// A labelled column keeps its key of labelling in dlab (64 Dk + column), and
-// the lazy updates move ruM and wv by 64 (Dend - Dk); augmenting moves one
-// word per column.
+// word, z = ruM - key + c = 64 (uM - Dk) + rowOf + 1: its low six bits are the
+// row + 1 (0: a free column, the augmenting path's end), the rest is q.
+// Labelling sets the key's top bit and keeps its value (64 Dk + c) for the
+// lazy update, which moves ruM and wv by 64 (Dend - Dk); augmenting moves one
+// word per column.  (rowOf + 1 < 64: n <= 62.)
+//
+// The sentinel is column sent, one outside the LAP (dead0, or a slot c >=
+// width, c < 32 NS): its key is the largest distance a packed key allows (real
+// keys stay at least one below it) and it is never matched, so a phase in
+// which every real column got labelled ends on it and reports the invariant
+// failure.
+// Columns outside the LAP are never relaxed and keep the key 0x7fffffff,
+// above the sentinel's.
+//
+// Bounded on any data: a labelled key is negative as a signed value and a
+// relaxation only replaces a key by a smaller one, so it stays labelled (on
+// data in range no relaxation reaches it: a labelled column's candidate is its
+// reduced cost plus its label, >= 0); every step that does not end the phase
+// labels the least unlabelled key, so after at most one step per column the
+// sentinel is the least key and ends the phase.
+template <int NS>
 __device__ __forceinline__ bool warp_hungarian_lane(const int *__restrict__ M, int ld, int n, int width,
-                                                    int dead0, int dead1, int &rowOf_out, int &uM_out,
-                                                    int &v_out, unsigned &steps_out, unsigned &relax_out)
+                                                    int dead0, int dead1, int sent, int (&rowOf)[NS],
+                                                    int (&uM)[NS], int (&v)[NS], unsigned &steps_out,
+                                                    unsigned &relax_out)
 {
-    constexpr unsigned kDone = 0x80000000u;  // key of a labelled column
-    constexpr unsigned kNone = 0xffffffffu;  // key of a column outside the LAP
-    constexpr unsigned kSentKey = (((1u << 25) - 1u) << 6) | 31u;
+    constexpr unsigned kLab = 0x80000000u;   // set on the key of a labelled column
+    constexpr unsigned kNone = 0x7fffffffu;  // key of a column outside the LAP
+    constexpr unsigned kSentBase = ((1u << 25) - 1u) << 6;
     const int lane = threadIdx.x & 31;
-    const bool valid = lane < width && lane != dead0 && lane != dead1;
-    const unsigned key0 = valid ? 0x7fffffffu : lane == 31 ? kSentKey : kNone;
-    unsigned ruM = 0u, wv = (unsigned)lane, dlab = 0u;
-    int way = -1;  // packed key of the column through which the column was reached (-1: the new row)
+    bool valid[NS];
+    unsigned key0[NS], key[NS], ruM[NS], wv[NS];
+    int way[NS];  // packed key of the column through which the column was reached (-1: the new row)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int c = lane + 32 * s;
+        valid[s] = c < width && c != dead0 && c != dead1;
+        key0[s] = c == sent ? kSentBase | (unsigned)c : kNone;
+        ruM[s] = 0u;
+        wv[s] = (unsigned)c;
+        way[s] = -1;
+    }
     int sumK = 0, sumK2 = 0;
     const int off = lane - ld;  // row i at M + (i + 1) * ld + off
 
     for (int r = 0; r < n; ++r) {
-        unsigned key = key0, r1 = (unsigned)r + 1u, q = 0u, mm;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) key[s] = key0[s];
+        unsigned r1 = (unsigned)r + 1u, q = 0u, mm;
         int j0 = -1;
         for (;;) {
-            const int x = M[(int)r1 * ld + off];
-            if (valid) {
-                const unsigned ck = (unsigned)x * 64u + (wv - q);
-                if ((int)ck < (int)key) {
-                    key = ck;
-                    way = j0;
+            const int *row = M + ((int)r1 * ld + off);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                if (valid[s]) {
+                    const unsigned ck = (unsigned)row[32 * s] * 64u + (wv[s] - q);
+                    if ((int)ck < (int)key[s]) {
+                        key[s] = ck;
+                        way[s] = j0;
+                    }
                 }
             }
-            const unsigned z = ruM - key + (unsigned)lane;
-            mm = __reduce_min_sync(kFull, key);
-            const unsigned zw = __shfl_sync(kFull, z, (int)mm);  // from the lane of column mm % 64 (< 32)
+            unsigned lmin, z;
+            if constexpr (NS == 1) {
+                lmin = key[0];
+                z = ruM[0] - key[0] + (unsigned)lane;
+            } else {
+                const bool hi = key[1] < key[0];
+                lmin = hi ? key[1] : key[0];
+                z = (hi ? ruM[1] : ruM[0]) - lmin + (unsigned)(hi ? lane + 32 : lane);
+            }
+            mm = __reduce_min_sync(kFull, lmin);
+            const unsigned zw = __shfl_sync(kFull, z, (int)mm);  // from the lane of column mm % 64
             r1 = zw & 63u;
             if (r1 == 0u) break;  // free column (or the sentinel): augmenting path found
-            if (key == mm) {
-                dlab = key;
-                key = kDone;
-            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+                if (key[s] == mm) key[s] |= kLab;
             q = zw & ~63u;
             j0 = (int)mm;
         }
         const int jf = (int)(mm & 63u);
-        if (jf == 31) return false;  // the sentinel: every column labelled, cannot happen
+        if (jf == sent) return false;  // the sentinel: every column labelled, cannot happen
         const unsigned Dend6 = mm & ~63u;
 
         // lazy potential updates of the columns labelled in this phase
-        const bool lab = key == kDone;
-        const int K = 1 + __popc(__ballot_sync(kFull, lab));
-        if (lab) {
-            const unsigned dd = Dend6 - (dlab & ~63u);
-            wv += dd;
-            ruM += dd;
+        int K = 1;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const bool lab = (int)key[s] < 0;
+            K += __popc(__ballot_sync(kFull, lab));
+            if (lab) {
+                const unsigned dd = Dend6 - (key[s] & (kLab - 64u));
+                wv[s] += dd;
+                ruM[s] += dd;
+            }
         }
         sumK += K;
         sumK2 += K * K;
@@ -372,16 +415,19 @@ __device__ __forceinline__ bool warp_hungarian_lane(const int *__restrict__ M, i
         int c = jf;
         for (int hop = 0;; ++hop) {
             if (hop > K) return false;
-            const int w = __shfl_sync(kFull, way, c);
-            const unsigned p = __shfl_sync(kFull, ruM, w);
-            if (lane == c) ruM = w >= 0 ? p : root;
+            const int w = __shfl_sync(kFull, pick<NS>(way, NS == 1 ? 0 : c >> 5), c);
+            const unsigned p = __shfl_sync(kFull, pick<NS>(ruM, NS == 1 ? 0 : (w >> 5) & 1), w);
+            if (NS == 1 ? lane == c : lane == (c & 31)) put<NS>(ruM, NS == 1 ? 0 : c >> 5, w >= 0 ? p : root);
             if (w < 0) break;
             c = w & 63;
         }
     }
-    rowOf_out = (int)(ruM & 63u) - 1;
-    uM_out = (int)(ruM & ~63u) >> 6;
-    v_out = (int)((unsigned)lane - wv) >> 6;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        rowOf[s] = (int)(ruM[s] & 63u) - 1;
+        uM[s] = (int)(ruM[s] & ~63u) >> 6;
+        v[s] = (int)((unsigned)(lane + 32 * s) - wv[s]) >> 6;
+    }
     steps_out += (unsigned)sumK;
     relax_out += (unsigned)(n * sumK - (sumK2 - sumK) / 2);
     return true;
@@ -395,8 +441,9 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
 {
     static_assert(SEG == 32 || (SEG == 16 && NS == 1), "a half-warp LAP has one column per lane");
     static_assert(!SENT || SEG == 32, "the sentinel is lane 31 of a whole warp");
-    if constexpr (NS == 1 && SEG == 32 && PACK && SENT)
-        return warp_hungarian_lane(M, ld, n, width, dead0, dead1, rowOf[0], uM[0], v[0], steps_out, relax_out);
+    if constexpr (SEG == 32 && PACK && SENT)
+        return warp_hungarian_lane<NS>(M, ld, n, width, dead0, dead1, dead0, rowOf, uM, v, steps_out,
+                                       relax_out);
     // A labelled column's key is kDone = INT_MIN: as a signed value no
     // candidate is below it, so no relaxation touches it (whatever the data),
     // and as an unsigned value it is above every unlabelled key, so no
@@ -530,6 +577,20 @@ __device__ __forceinline__ bool warp_hungarian(const int *__restrict__ M, int ld
     steps_out += (unsigned)sumK;
     relax_out += (unsigned)(n * sumK - (sumK2 - sumK) / 2);
     return true;
+}
+
+// A full n x n LAP (no dead columns, width n): the lane words when keys pack
+// and a column slot is free for the sentinel (n < 32 NS), else the general form.
+template <int NS, bool PACK>
+__device__ __forceinline__ bool warp_hungarian_full(const int *__restrict__ M, int ld, int n, int (&rowOf)[NS],
+                                                    int (&uM)[NS], int (&v)[NS], unsigned &steps_out,
+                                                    unsigned &relax_out)
+{
+    if constexpr (PACK) {
+        if (n < 32 * NS)
+            return warp_hungarian_lane<NS>(M, ld, n, n, -1, -1, 32 * NS - 1, rowOf, uM, v, steps_out, relax_out);
+    }
+    return warp_hungarian<NS, PACK>(M, ld, n, n, -1, -1, rowOf, uM, v, steps_out, relax_out);
 }
 
 // S = sum of the row and column potentials = cost of the assignment.

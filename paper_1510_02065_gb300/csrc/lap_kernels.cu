@@ -21,8 +21,10 @@
 
 namespace rlt2 {
 
-// D->C LAPs with one column slot per lane use the Hungarian's sentinel column
-// (a build can turn it off for comparison with -DRLT2_NO_SENTINEL)
+// D->C LAPs on whole warps use the Hungarian's sentinel column: with packed
+// keys the tile's dead column j (and the packed lane words), otherwise lane 31
+// with one column slot per lane (a build can turn both off for comparison
+// with -DRLT2_NO_SENTINEL)
 #ifdef RLT2_NO_SENTINEL
 constexpr bool kSentinel = false;
 #else
@@ -84,7 +86,7 @@ __device__ __forceinline__ bool dlap_tile(const NodeDesc &nd, unsigned t, int *b
     }
     const int nl = nn + (nn >= j);
     int rowOf[NS], uM[NS], v[NS];
-    if (!warp_hungarian<NS, PACK, SEG, kSentinel && SEG == 32 && NS == 1>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) &&
+    if (!warp_hungarian<NS, PACK, SEG, kSentinel && SEG == 32 && (NS == 1 || PACK)>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) &&
         lane == 0)
         atomicOr(&status->err, kDevInternal);
     // u of every row goes to the row's column j, which holds no coefficient
@@ -174,7 +176,7 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
     }
     __syncwarp(sg.mask);
     int rowOf[NS], uM[NS], v[NS];
-    if (!warp_hungarian<NS, PACK, SEG, kSentinel && SEG == 32 && NS == 1>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) &&
+    if (!warp_hungarian<NS, PACK, SEG, kSentinel && SEG == 32 && (NS == 1 || PACK)>(buf, W, n, N, j, nl, rowOf, uM, v, steps, relax) &&
         lane == 0)
         atomicOr(&status->err, kDevInternal);
     scatter_rows<NS, SEG>(n, N, j, nl, rowOf, uM, buf + j, nullptr, W);  // u to the free column j
@@ -198,20 +200,20 @@ __device__ __forceinline__ bool dlap_tile_sym(const NodeDesc &nd, unsigned t, in
 // Tiles of one instance are consecutive in the group-wide order, so the
 // instance found for the previous tile is tried first.  ONE (a group of one
 // instance): the instance is the kernel parameter g.first, read from
-// parameter space, and the stopping rule is checked once.  Every CTA size
-// caps registers at 32 per thread (64 warps per SM).
+// parameter space, and the stopping rule is checked once.
 // MODE: 0 tile store, 1 class-sum store, 2 pair store (work units: its tiles).
 // Resident warps per SM each D->C form is compiled for, i.e. its register
-// budget (65536 / 32 / warps).  A group of one reads its instance from kernel
-// parameters and fits 32 registers (64 warps).  A larger group holds its
-// instances' fields in registers: with the tile or pair store and one column
-// slot per lane it would take 38-43 and spills 32-48 bytes per thread at 32,
-// which measured faster at 64 warps than 48 warps without spills (C4 batch:
-// 28.0 vs 27.5 nodes/s); with the class-sum store's gather or two column
-// slots per lane it takes up to 64 and spilled 64-184 bytes, so those forms
-// get 64 registers (32 warps).
+// budget (65536 / 32 / warps).  Two column slots per lane (N >= 32): a tile
+// buffer of at least 7.7 KB per warp keeps fewer than 30 warps resident, so
+// these forms get 64 registers (32 warps) and never spill.  One slot: a group
+// of one reads its instance from kernel parameters and fits 32 registers (64
+// warps).  A larger group holds its instances' fields in registers: with the
+// tile or pair store it would take 38-43 and spills 40-56 bytes per thread at
+// 32, which measured faster at 64 warps than 48 warps without spills (C4
+// batch: 28.0 vs 27.5 nodes/s); with the class-sum store's gather it takes up
+// to 64 (64 registers, 32 warps; 16 bytes spilled).
 template <int NS, bool ONE, int MODE>
-constexpr int kDlapWarpsPerSM = ONE ? 64 : (MODE == 1 || NS == 2) ? 32 : 64;
+constexpr int kDlapWarpsPerSM = NS == 2 ? 32 : ONE ? 64 : MODE == 1 ? 32 : 64;
 
 template <int NS, bool PACK, bool ONE, int MODE, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, kDlapWarpsPerSM<NS, ONE, MODE> / WARPS)
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(kClapWarps * 32) clap_kernel(Group g, int pitc
         }
         __syncwarp();
         int rowOf[NS], uM[NS], v[NS];
-        if (!warp_hungarian<NS, PACK>(buf, m, m, m, -1, -1, rowOf, uM, v, steps, relax) && lane == 0)
+        if (!warp_hungarian_full<NS, PACK>(buf, m, m, rowOf, uM, v, steps, relax) && lane == 0)
             atomicOr(&g.status->err, kDevInternal);
         scatter_rows<NS>(m, m, -1, -1, rowOf, uM, uRow, nullptr);
         __syncwarp();
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(kXlapWarps * 32) xlap_kernel(Group g, int pitc
     __syncwarp();
     unsigned steps = 0, relax = 0;
     int rowOf[NS], uM[NS], v[NS];
-    if (!warp_hungarian<NS, PACK>(buf, N, N, N, -1, -1, rowOf, uM, v, steps, relax) && lane == 0)
+    if (!warp_hungarian_full<NS, PACK>(buf, N, N, rowOf, uM, v, steps, relax) && lane == 0)
         atomicOr(&g.status->err, kDevInternal);
     scatter_rows<NS>(N, N, -1, -1, rowOf, uM, uRow, nullptr);
     __syncwarp();
@@ -475,8 +477,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32)
         unsigned steps = 0, relax = 0;
         int rowOf[NS], uM[NS], v[NS];
         const bool fine = mx < (1 << 25) / 3
-                              ? warp_hungarian<NS, true>(buf, n, n, n, -1, -1, rowOf, uM, v, steps, relax)
-                              : warp_hungarian<NS, false>(buf, n, n, n, -1, -1, rowOf, uM, v, steps, relax);
+                              ? warp_hungarian_full<NS, true>(buf, n, n, rowOf, uM, v, steps, relax)
+                              : warp_hungarian_full<NS, false>(buf, n, n, rowOf, uM, v, steps, relax);
         if (!fine && lane == 0) atomicOr(&status->err, kDevInternal);
         scatter_rows<NS>(n, n, -1, -1, rowOf, uM, uRow, colOf);
         __syncwarp();

@@ -86,6 +86,30 @@ def test_lap_extreme_values(torch, orc):
         assert (S == S0).all() and (A == A0).all() and (U == U0).all() and (V == V0).all()
 
 
+def test_lap_packing_limit(torch, orc):
+    """Entries at the largest value the packed keys take (a batch whose largest
+    entry is below 2^25 / 3) and one above it (the unpacked keys), for sizes
+    with a free column slot (the sentinel of the packed lane form) and without."""
+    lim = (1 << 25) // 3 - 1
+    rng = np.random.default_rng(11)
+    for top in (lim, lim + 1):
+        for n in (2, 5, 31, 32, 33, 63, 64):
+            M = np.empty((6, n, n), np.int64)
+            M[0] = top
+            M[1] = rng.integers(0, top + 1, size=(n, n))
+            M[2] = rng.integers(top - 3, top + 1, size=(n, n))
+            M[3] = np.arange(n)[None, :] * (top // max(n - 1, 1))
+            M[4] = (rng.random((n, n)) < 0.5) * top
+            M[5] = top - np.add.outer(np.arange(n), np.arange(n)) % 7
+            M = M.astype(np.int32)
+            rc, S, A, U, V, W = gpu_lap(torch, M)
+            assert rc == 0, rlt2.rlt2_strerror(rc)
+            S0, A0, U0, V0, W0 = orc.lap_batch(M)
+            assert (S == S0).all() and (A == A0).all(), (top, n)
+            assert (U == U0).all() and (V == V0).all(), (top, n)
+            assert (W[:, 0] == W0[:, 0]).all() and (W[:, 1] == W0[:, 1]).all(), (top, n)
+
+
 def test_lap_empty_batch(torch):
     rc = rlt2.rlt2_lap_batch(0, 4, 0, 0)
     assert rc == 0

@@ -489,6 +489,61 @@ def test_pairs_headline_n30(gpu, orc):
     _first_pass_then_properties(orc, F, D, 30, 31, PAIRS)
 
 
+def _sliced_first_pass_then_properties(orc, F, D, N, store, seed):
+    """The oracle's spreading and complementary operations in full and its
+    D -> C concentration on three facility slices; 10^6 sampled D entries of
+    those slices after the first pass must agree, then three passes are checked
+    through properties."""
+    paired = store == PAIRS
+    rng = np.random.default_rng(seed)
+    perms = [rng.permutation(N) for _ in range(100)]
+    st = orc.State(F, D, paired=paired)
+    st.spread_B_to_C()
+    st.spread_C_to_D()
+    st.complementary_D()
+    slices = (0, N // 2, N - 2 if paired else N - 1)
+    for a in slices:
+        st.concentrate_D_to_C_range(a, a + 1)
+    with rlt2.Context(F, D, store=store) as ctx:
+        ctx.iterate(1)
+        z = ctx.state(2)
+        i, j, k, n = [a.astype(np.int64) for a in tile_indices(N)]
+        per = N * (N - 1) ** 2
+        for a in slices:
+            sel = a * per + rng.integers(0, per, size=1000000)
+            rr = rng.integers(0, N - 2, size=sel.size)
+            ss = rng.integers(0, N - 2, size=sel.size)
+            lo, hi = np.minimum(i[sel], k[sel]), np.maximum(i[sel], k[sel])
+            p = rr + (rr >= lo)
+            p = p + (p >= hi)
+            lo, hi = np.minimum(j[sel], n[sel]), np.maximum(j[sel], n[sel])
+            q = ss + (ss >= lo)
+            q = q + (q >= hi)
+            ref = st.d[i[sel], j[sel], k[sel], n[sel], p, q]
+            got = z[(sel * (N - 2) + rr) * (N - 2) + ss]
+            assert (got == ref).all(), "D differs in slice i = %d" % a
+        st.close()
+        hist = [ctx.bound()[1]]
+        for t in range(3):
+            ctx.iterate(1)
+            hist.append(ctx.bound()[1])
+        x, y, z = ctx.state(0), ctx.state(1), ctx.state(2)
+        assert x.min() >= 0 and y.min() >= 0 and z.min() >= 0
+        assert all(a <= b for a, b in zip(hist, hist[1:]))
+        assert _conservation_sample(F, D, N, hist[-1], x, y, z, perms) == 0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("N,store", [(31, rlt2.RLT2_STORE_TILES), (31, rlt2.RLT2_STORE_CLASSES),
+                                     (32, rlt2.RLT2_STORE_TILES), (32, PAIRS)])
+def test_column_slot_boundary(gpu, orc, N, store):
+    """N = 31: the widest D -> C tiles with one column slot per lane (31
+    columns, the LAP's dead column as the sentinel of the packed Hungarian);
+    N = 32: the narrowest with two (32 columns, no free lane)."""
+    F, D = I.clustered_euclid(N, seed=N + 2)
+    _sliced_first_pass_then_properties(orc, F, D, N, store, N)
+
+
 @pytest.mark.slow
 def test_pairs_n34_two_column_slots(gpu, orc):
     """N = 34 in the pair store: two column slots per lane in the LAPs (the
