@@ -75,6 +75,26 @@ def test_batch_equals_single_contexts_and_oracle(gpu, orc, store):
 
 
 @pytest.mark.gpu
+@pytest.mark.slow
+@pytest.mark.parametrize("store", [rlt2.RLT2_STORE_TILES, rlt2.RLT2_STORE_CLASSES, rlt2.RLT2_STORE_PAIRS])
+def test_batch_two_column_slots(gpu, store):
+    """Nodes of a 34-facility instance with N' = 34, 33, 32 (two column slots
+    per lane in the group's D->C kernel) and one with N' = 30 in the same
+    range: the batch gives every node the bound of its own single context."""
+    N = 34
+    F, D = I.clustered_euclid(N, seed=12)
+    nodes = [(np.array([], np.int32), np.array([], np.int32)), (np.array([5]), np.array([9])),
+             (np.array([0, 17]), np.array([33, 2])), (np.array([1, 2, 3, 4]), np.array([8, 6, 4, 2]))]
+    iters = 3
+    lbs, _ = rlt2.rlt2_batch_bound(F, D, nodes, iters, store=store)
+    for b, (fac, loc) in enumerate(nodes):
+        Fp, Dp, Bl, cst = rlt2.rlt2_subproblem(F, D, fac, loc)
+        with rlt2.Context(Fp, Dp, B_lin=Bl, lb_const=cst, store=store) as ctx:
+            ctx.iterate(iters)
+            assert ctx.bound()[1] == lbs[b], (b, N - len(fac))
+
+
+@pytest.mark.gpu
 def test_batch_of_one_and_zero_passes(gpu):
     F, D = I.uniform_symmetric(9, seed=2)
     lbs, _ = rlt2.rlt2_batch_bound(F, D, [(np.array([], np.int32), np.array([], np.int32))], 4)
